@@ -1,0 +1,110 @@
+"""Pins of the step-by-step gridding-NFFT oracle.
+
+- window Fourier transforms phihat against numerical quadrature of phi
+  (exact for the Gaussian; within the O(exp(-b m)) truncation term for the
+  Kaiser-Bessel window, whose I0 formula transforms the untruncated function);
+- the approximation error against the direct NDFT (Eq. 9) obeys the
+  textbook exponential decay bounds for the Gaussian and Kaiser-Bessel
+  windows and shrinks with m;
+- the NFFT and its inverse procedure are exact transposes (adjoint identity
+  to rounding, independent of the window error);
+- the oversampled size rule.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate
+
+from oracle import ndft, nfft_steps as S
+from paper_2001_01583_gb300 import inputs
+
+
+@pytest.mark.parametrize("window,m,N,n", [(S.GAUSSIAN, 4, 32, 64), (S.GAUSSIAN, 6, 16, 40),
+                                          (S.KAISER_BESSEL, 4, 32, 64), (S.KAISER_BESSEL, 3, 20, 30)])
+def test_phi_hat_matches_quadrature(window, m, N, n):
+    # phihat(k) = int phi(x) exp(-2 pi i k x) dx; phi is even so the cosine part suffices
+    lim = m / n if window == S.KAISER_BESSEL else 12.0 * math.sqrt(S.shape_param(window, m, n, N)) / n
+    for k in (0, 1, N // 4, N // 2 - 1, -N // 2):
+        val, _ = scipy.integrate.quad(lambda x: float(S.phi(window, np.array([n * x]), m, n, N)[0])
+                                      * math.cos(2 * math.pi * k * x), -lim, lim, limit=400,
+                                      epsabs=1e-15, epsrel=1e-13)
+        ref = float(S.phi_hat(window, k, m, n, N))
+        if window == S.GAUSSIAN:
+            assert abs(val - ref) <= 1e-10 * abs(ref)
+        else:
+            # the I0 formula is the transform of the untruncated Kaiser-Bessel
+            # function; cutting it at |u| = m changes the transform by a
+            # amount of order exp(-b m) relative to the peak phihat(0)
+            b = S.shape_param(window, m, n, N)
+            peak = float(S.phi_hat(window, 0, m, n, N))
+            assert abs(val - ref) <= (2.0 * math.exp(-b * m) + 1e-12) * peak
+
+
+def test_oversampled_size_rule():
+    assert S.oversampled_size(64, 2.0, 4) == 128
+    assert S.oversampled_size(100, 1.25, 4) == 126      # 125 is odd -> 126 = 2 * 3^2 * 7
+    assert S.oversampled_size(256, 1.5, 4) == 384
+    with pytest.raises(ValueError):
+        S.oversampled_size(4, 2.0, 6)                    # n = 8 < 2m + 2
+
+
+def _gauss_bound(m, sigma):
+    # Steidl (1998): E_inf <= 4 exp(-m pi (1 - 1/(2 sigma - 1)))
+    return 4.0 * math.exp(-m * math.pi * (1.0 - 1.0 / (2.0 * sigma - 1.0)))
+
+
+def _kb_bound(m, sigma):
+    # Potts & Steidl: E_inf <= 4 pi (sqrt(m) + m) (1 - 1/sigma)^(1/4) exp(-2 pi m sqrt(1 - 1/sigma))
+    s = 1.0 - 1.0 / sigma
+    return 4.0 * math.pi * (math.sqrt(m) + m) * s ** 0.25 * math.exp(-2.0 * math.pi * m * math.sqrt(s))
+
+
+@pytest.mark.parametrize("window,bound", [(S.GAUSSIAN, _gauss_bound), (S.KAISER_BESSEL, _kb_bound)])
+def test_error_within_textbook_bound_and_decreasing(window, bound):
+    N = (64,)
+    M = 400
+    x = inputs.uniform_points(M, 1, seed=21)
+    f = inputs.complex_normal(M, seed=22)
+    exact = ndft.adjoint(x, f, N)
+    errs = []
+    for m in (2, 3, 4, 5, 6):
+        approx = S.adjoint(x, f, N, 2.0, m, window)
+        e = ndft.rel_l2(approx, exact)
+        assert e < bound(m, 2.0), (m, e)
+        errs.append(e)
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+@pytest.mark.parametrize("d,N", [(1, (32,)), (2, (12, 16)), (3, (8, 8, 6))])
+@pytest.mark.parametrize("window", [S.GAUSSIAN, S.KAISER_BESSEL])
+def test_nfft_pair_is_exact_transpose(d, N, window):
+    M = 120
+    x = inputs.uniform_points(M, d, seed=31)
+    f = inputs.complex_normal(M, seed=32)
+    g = inputs.complex_normal(N, seed=33)
+    lhs = np.vdot(S.forward(x, g, N, 2.0, 3, window), f)
+    rhs = np.vdot(g, S.adjoint(x, f, N, 2.0, 3, window))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_forward_error_3d_kaiser_bessel():
+    N = (16, 16, 16)
+    M = 800
+    x = inputs.uniform_points(M, 3, seed=41)
+    fh = inputs.complex_normal(N, seed=42)
+    e = ndft.rel_l2(S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL), ndft.forward(x, fh, N))
+    assert e < _kb_bound(4, 2.0)
+    assert e < 1e-6
+
+
+def test_points_on_cell_boundaries_and_wrap():
+    # a point at x = -1/2 and one at x = +1/2 are the same point (Eq. 5 is
+    # 1-periodic); both must give the same NFFT output
+    N = (16,)
+    f = np.array([1.0 + 0.5j])
+    a = S.adjoint(np.array([[-0.5]]), f, N, 2.0, 4, S.KAISER_BESSEL)
+    b = S.adjoint(np.array([[0.5]]), f, N, 2.0, 4, S.KAISER_BESSEL)
+    assert np.max(np.abs(a - b)) < 1e-14
+    exact = ndft.adjoint(np.array([[-0.5]]), f, N)
+    assert ndft.rel_l2(a, exact) < 1e-6
