@@ -1,0 +1,184 @@
+/*
+ * gbnfft: the gridding NFFT of the HP-NFFT paper on one GB300 GPU.
+ *
+ * C ABI.  All functions return an nfft_status (0 = success, < 0 = error)
+ * unless stated otherwise; none throws.  Pointers named *_dev are device
+ * pointers the caller owns (for example PyTorch tensors); the library never
+ * frees them and never copies them to the host.  Work is queued on the plan's
+ * CUDA stream and is asynchronous: argument errors are returned at once,
+ * errors found on the device (non-finite points) are returned by nfft_sync.
+ * A plan is not thread-safe; distinct plans may be used from distinct threads.
+ *
+ * Notation (paper, Section 1):
+ *   I_N = { k in Z^d : -N_t/2 <= k_t < N_t/2 },  N_t even, d in {1, 2, 3}
+ *   Eq. 5 (adjoint):  fhat(k) = sum_{j<M} f(x_j) exp(-2 pi i k.x_j),  k in I_N
+ *   Eq. 6 (forward):  f(x_j)  = sum_{k in I_N} fhat(k) exp(+2 pi i k.x_j)
+ * Eq. 6 is the transpose A^H of Eq. 5's matrix A, which the paper calls the
+ * "inverse NDFT"; this library calls it the forward transform.
+ *
+ * Both transforms are computed by the gridding method of Section 2 on the
+ * oversampled grid I_n, n_t = sigma N_t rounded up to an even 2,3,5,7-smooth
+ * integer: spreading with a window phi, FFT, scaling by c_k(phi~) (Fig. 1,
+ * Algorithm 2) and subdividing, inverse FFT, interpolating (Fig. 2,
+ * Algorithm 5).  Each point reaches 2m + 2 cells per dimension (the
+ * Kaiser-Bessel window is zero on two of them, which the kernels skip).
+ *
+ * Layouts
+ *   x      M x d doubles, point-major: x[j*d + t] is coordinate t of point j,
+ *          paired with N_t.  Any finite value (Eq. 5 is 1-periodic in x).
+ *   f      R x M complex, right-hand side r at f + r*M.
+ *   fhat   R x |I_N| complex, each in C order over (k_0, ..., k_{d-1}) with
+ *          every k_t ascending from -N_t/2 (the last index varies fastest).
+ *   complex = interleaved (re, im): double for NFFT_FP64, float for
+ *          NFFT_FP32_MIXED.
+ */
+#ifndef GBNFFT_H
+#define GBNFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nfft_plan nfft_plan;
+
+/* Window functions named in Section 4 (formulas: the standard NFFT windows). */
+typedef enum {
+  NFFT_GAUSSIAN = 0,
+  NFFT_KAISER_BESSEL = 1
+} nfft_window;
+
+/* NFFT_FP64: FP64 points, weights, grid and FFT (the plain form).
+ * NFFT_FP32_MIXED: FP64 argument reduction of n x_j and FP64 scaling factors,
+ * FP32 window weights, FP32 spreading / interpolation with FP32 accumulation,
+ * FP32 FFT. */
+typedef enum {
+  NFFT_FP64 = 0,
+  NFFT_FP32_MIXED = 1
+} nfft_precision;
+
+typedef enum {
+  NFFT_OK = 0,
+  NFFT_ERR_INVALID_ARG = -1,  /* bad size, null pointer, odd N, sigma < 1, ... */
+  NFFT_ERR_DOMAIN = -2,       /* a point coordinate was NaN or infinite */
+  NFFT_ERR_OOM = -3,          /* device allocation failed */
+  NFFT_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+  NFFT_ERR_CUFFT = -5,        /* a cuFFT call failed */
+  NFFT_ERR_NOT_READY = -6,    /* transform requested before nfft_set_points */
+  NFFT_ERR_TIMEOUT = -7,      /* a bounded device wait gave up */
+  NFFT_ERR_UNSUPPORTED = -8   /* valid request outside what this build supports */
+} nfft_status;
+
+/* Spreading / interpolation kernels. */
+typedef enum {
+  NFFT_METHOD_AUTO = 0,   /* tiled if the tile fits in shared memory, else global */
+  NFFT_METHOD_TILED = 1,  /* bin-sorted points, per-subproblem shared-memory tile */
+  NFFT_METHOD_GLOBAL = 2  /* one thread per point, atomics straight into the grid
+                             (the paper's spread kernel, Section 3) */
+} nfft_method;
+
+/* Options for nfft_set_option. */
+typedef enum {
+  NFFT_OPT_METHOD = 0,          /* nfft_method */
+  NFFT_OPT_BIN_0 = 1,           /* bin edge in cells along dimension 0 (0 = default) */
+  NFFT_OPT_BIN_1 = 2,
+  NFFT_OPT_BIN_2 = 3,
+  NFFT_OPT_MAX_SUBPROBLEM = 4,  /* points per subproblem (0 = default) */
+  NFFT_OPT_RHS_CAPACITY = 5,    /* grids kept for right-hand sides processed together */
+  NFFT_OPT_PROFILE = 6,         /* 1: record CUDA events around every stage */
+  NFFT_OPT_THREADS = 7          /* threads per block of the point kernels (0 = default) */
+} nfft_option;
+
+/* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
+typedef enum {
+  NFFT_STAGE_SORT = 0,      /* nfft_set_points: wrap, cell, bin-sort, subproblems */
+  NFFT_STAGE_SPREAD = 1,    /* adjoint step 1 */
+  NFFT_STAGE_FFT = 2,       /* adjoint step 2 (forward cuFFT) */
+  NFFT_STAGE_DECONV = 3,    /* adjoint step 3 (scale + crop) */
+  NFFT_STAGE_PAD = 4,       /* forward step 1 (subdivide: scale + zero pad) */
+  NFFT_STAGE_IFFT = 5,      /* forward step 2 (inverse cuFFT) */
+  NFFT_STAGE_INTERP = 6,    /* forward step 3 */
+  NFFT_STAGE_COUNT = 7
+} nfft_stage;
+
+typedef struct {
+  int d;
+  int64_t N[3];
+  int64_t n[3];              /* oversampled grid */
+  int64_t M;
+  int m;                     /* cut-off parameter */
+  int taps;                  /* nonzero window taps per dimension the kernels visit */
+  int window;
+  int precision;
+  int method;                /* the method in use (never AUTO) */
+  int bin[3];                /* bin edges in cells */
+  int64_t n_bins;
+  int rhs_capacity;
+  int threads;               /* threads per block of the point kernels */
+  int64_t device_bytes;      /* device memory held by the plan (grids, sort buffers, tables) */
+  double sigma[3];           /* actual n_t / N_t */
+} nfft_plan_info;
+
+/* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling
+ * sigma >= 1, cut-off m >= 1, window, precision).  N points to d int64 values,
+ * each even and >= 2.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  Allocates all device memory the transforms need; no later call
+ * allocates unless NFFT_OPT_RHS_CAPACITY, a bin size or the method changes.
+ * On error *out is NULL. */
+int nfft_plan_create(nfft_plan** out, int d, const int64_t* N, int64_t M, double sigma, int m,
+                     int window, int precision, void* cuda_stream);
+
+/* Free the plan and everything it holds (waits for its stream first). NULL is ignored. */
+int nfft_plan_destroy(nfft_plan* plan);
+
+/* Set the M points (x_dev: M*d doubles on the device, layout above).  Wraps
+ * each coordinate into [-1/2, 1/2) (exact: Eq. 5 is 1-periodic), reduces
+ * u = n_t x_t to a cell index and an in-cell offset in FP64, and bin-sorts the
+ * points by spatial tile (the on-device form of the paper's subcells,
+ * Eqs. 7-8).  x_dev is read during the call's kernels only and may be freed or
+ * reused once the stream passes them.  A NaN/Inf coordinate sets the plan's
+ * device error flag (reported by nfft_sync as NFFT_ERR_DOMAIN); such a point
+ * is treated as x = 0. */
+int nfft_set_points(nfft_plan* plan, const double* x_dev);
+
+/* Eq. 5 for R right-hand sides (Fig. 1, Algorithm 2): fhat_dev[r] = A f_dev[r].
+ * f_dev: R x M complex, fhat_dev: R x |I_N| complex (precision's type). */
+int nfft_adjoint(nfft_plan* plan, const void* f_dev, void* fhat_dev, int R);
+
+/* Eq. 6 for R right-hand sides (Fig. 2, Algorithm 5): f_dev[r] = A^H fhat_dev[r]. */
+int nfft_forward(nfft_plan* plan, const void* fhat_dev, void* f_dev, int R);
+
+/* Wait for the plan's stream, then report (and clear) the device error flag. */
+int nfft_sync(nfft_plan* plan);
+
+/* Change the stream later calls queue on (NULL = legacy default stream). */
+int nfft_set_stream(nfft_plan* plan, void* cuda_stream);
+
+/* Set a tuning option (nfft_option).  Bins, method and subproblem size take
+ * effect at the next nfft_set_points, which must follow. */
+int nfft_set_option(nfft_plan* plan, int option, int64_t value);
+
+int nfft_get_info(const nfft_plan* plan, nfft_plan_info* info);
+
+/* With NFFT_OPT_PROFILE on: waits for the stream, then writes into
+ * ms[NFFT_STAGE_COUNT] the milliseconds and into launches[NFFT_STAGE_COUNT]
+ * (may be NULL) the number of timed calls accumulated per stage since the
+ * last reset; reset != 0 clears the totals afterwards. */
+int nfft_stage_times(nfft_plan* plan, double* ms, int64_t* launches, int reset);
+
+/* Host-only parameter rule (no device needed): the oversampled size n_t for
+ * each of the d bandwidths and the number of window taps per dimension. */
+int nfft_plan_params(int d, const int64_t* N, double sigma, int m, int window, int64_t* n_out, int* taps_out);
+
+/* Human-readable name of a status code (static string). */
+const char* nfft_status_string(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int nfft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBNFFT_H */

@@ -1,0 +1,125 @@
+// Shared device definitions of the gbnfft CUDA library.
+//
+// Grid storage: the oversampled grid I_n is stored with cell l_t at array
+// index l_t mod n_t, C order (dimension d-1 fastest).  With that layout the
+// centred DFTs of Section 2 are plain cuFFT transforms.
+//
+// Points: after nfft_set_points every point j is described, in sorted order,
+// by its original index perm[p], its in-bin cell offsets (packed) and its
+// in-cell offsets delta_t = u_t - floor(u_t), u_t = n_t (x_t mod 1).  The
+// subproblem list cuts every non-empty bin into runs of at most P points.
+//
+// Window taps: a point in cell c reaches cells c - m + s + i, i = 0..W-1,
+// where (s, W) = (0, 2m+2) for the Gaussian and (1, 2m) for the Kaiser-Bessel
+// window (whose weight is exactly zero at the two outer cells of the 2m + 2
+// the method defines).  The distance u - l of tap i is delta + (m - s) - i.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbnfft {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxTaps = 32;
+
+template <typename Real> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cmake(double re, double im);
+template <> __device__ __forceinline__ float2 cmake<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> __device__ __forceinline__ double2 cmake<double2>(double re, double im) { return make_double2(re, im); }
+
+// Window parameters, normalised so that psi(0) = 1 (the constant phi(0) is
+// moved into the FP64 scaling factors on the host).  The shape parameter
+// depends on sigma_t = n_t / N_t, so it is kept per dimension.
+struct WindowDev {
+  int kind;                 // 0 Gaussian, 1 Kaiser-Bessel
+  int m;                    // cut-off
+  int shift;                // s: first tap is c - m + s
+  int taps;                 // W
+  double b[kMaxDim];        // shape parameter per dimension
+  double kb_norm[kMaxDim];  // 1 / (1 - exp(-2 b m)) per dimension
+};
+
+// psi(u) = phi(u / n) / phi(0) for the distance u (in cells).
+//   Gaussian:       exp(-u^2 / b)
+//   Kaiser-Bessel:  sinh(b z) / z * m / sinh(b m),  z = sqrt(m^2 - u^2), |u| < m
+// The Kaiser-Bessel form is evaluated as
+//   exp(-b u^2 / (z + m)) * m * (-expm1(-2 b z) / z) * kb_norm
+// so the large exponent b m cancels exactly instead of in floating point.
+template <typename Real>
+__device__ __forceinline__ Real window_psi(const WindowDev& w, int t, Real u);
+
+template <>
+__device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, float u) {
+  const float b = (float)w.b[t];
+  if (w.kind == 0) return expf(-(u * u) / b);
+  const float m = (float)w.m;
+  const float u2 = u * u;
+  const float m2 = m * m;
+  if (!(u2 < m2)) return 0.0f;
+  const float z = sqrtf(m2 - u2);
+  const float e = expf(-b * u2 / (z + m));
+  const float s = -expm1f(-2.0f * b * z) / z;
+  return e * m * s * (float)w.kb_norm[t];
+}
+
+template <>
+__device__ __forceinline__ double window_psi<double>(const WindowDev& w, int t, double u) {
+  const double b = w.b[t];
+  if (w.kind == 0) return exp(-(u * u) / b);
+  const double m = (double)w.m;
+  const double u2 = u * u;
+  const double m2 = m * m;
+  if (!(u2 < m2)) return 0.0;
+  const double z = sqrt(m2 - u2);
+  const double e = exp(-b * u2 / (z + m));
+  const double s = -expm1(-2.0 * b * z) / z;
+  return e * m * s * w.kb_norm[t];
+}
+
+// One subproblem: a run of sorted points inside one bin.
+struct SubProblem {
+  int bin;
+  int start;
+  int count;
+  int pad_;
+};
+
+// Point data after sorting (all arrays indexed by sorted position).
+template <typename Real>
+struct SortedPoints {
+  const int* perm;           // sorted position -> original point index
+  const uint32_t* local;     // packed in-bin cell offsets
+  const Real* delta[kMaxDim];
+  const SubProblem* subs;
+  const int* num_subs;       // device scalar
+};
+
+struct GridGeom {
+  int d;
+  int n[kMaxDim];            // oversampled sizes (unused dims = 1)
+  int bin[kMaxDim];          // bin edges (unused dims = 1)
+  int nbins[kMaxDim];        // bins per dimension
+  int tile[kMaxDim];         // bin + W - 1 (unused dims = 1)
+  int64_t grid_cells;        // prod n
+  int tile_cells;            // prod tile
+};
+
+// Pack / unpack of in-bin offsets: 32 bits split evenly over d dimensions.
+__host__ __device__ __forceinline__ int local_bits(int d) { return d == 1 ? 32 : (d == 2 ? 16 : 10); }
+
+__device__ __forceinline__ int unpack_local(uint32_t v, int d, int t) {
+  if (d == 1) return (int)v;
+  const int bits = local_bits(d);
+  return (int)((v >> (bits * t)) & ((1u << bits) - 1u));
+}
+
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+}  // namespace gbnfft

@@ -1,0 +1,185 @@
+// nfft_set_points kernels: argument reduction and counting sort of the points
+// by spatial bin.  The bins are the on-device form of the paper's subcells
+// (Section 3, Eqs. 7-8): a transform is the sum of the sub-transforms of any
+// partition of the points, so every bin can be spread independently.
+#include "kernels.h"
+
+namespace gbnfft {
+
+namespace {
+
+// Reduce one coordinate: x -> x - floor(x) in [0, 1] (exact for Eq. 5, which
+// is 1-periodic), u = n x, cell c = floor(u) in [0, n), offset u - c in FP64,
+// then rounded once to Real.  An offset that rounds up to 1 moves to the next
+// cell with offset 0 (the same position).
+template <typename Real>
+__device__ __forceinline__ void reduce_coord(double x, int n, int& c, Real& delta) {
+  const double xw = x - floor(x);
+  const double u = (double)n * xw;
+  const double cf = floor(u);
+  int ci = (int)cf;
+  Real dr = (Real)(u - cf);
+  if (dr >= (Real)1) {
+    dr = (Real)0;
+    ci += 1;
+  }
+  if (ci >= n) ci -= n;
+  c = ci;
+  delta = dr;
+}
+
+__device__ __forceinline__ double load_coord(const double* x, int64_t j, int d, int t, bool& bad) {
+  const double v = x[j * d + t];
+  if (!isfinite(v)) {
+    bad = true;
+    return 0.0;
+  }
+  return v;
+}
+
+template <typename Real>
+__global__ void k_bin_count(const double* __restrict__ x, int64_t M, GridGeom g, int* __restrict__ bin_count,
+                            int2* __restrict__ bin_rank, int* __restrict__ err) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = j < M;
+  int bin = -1;
+  if (valid) {
+    bool bad = false;
+    bin = 0;
+    for (int t = 0; t < g.d; ++t) {
+      int c;
+      Real dl;
+      reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
+      bin = bin * g.nbins[t] + c / g.bin[t];
+    }
+    if (bad) atomicOr(err, 1);
+  }
+  // warp-aggregated rank: lanes with the same bin share one atomic
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (valid) bin_rank[j] = make_int2(bin, base + __popc(peers & ((1u << lane) - 1u)));
+}
+
+template <typename Real>
+__global__ void k_scatter(const double* __restrict__ x, int64_t M, GridGeom g, const int* __restrict__ bin_start,
+                          const int2* __restrict__ bin_rank, int* __restrict__ perm, uint32_t* __restrict__ local,
+                          Real* d0, Real* d1, Real* d2) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int2 br = bin_rank[j];
+  const int pos = bin_start[br.x] + br.y;
+  bool bad = false;
+  uint32_t packed = 0;
+  const int bits = local_bits(g.d);
+  Real* dst[3] = {d0, d1, d2};
+  for (int t = 0; t < g.d; ++t) {
+    int c;
+    Real dl;
+    reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
+    const uint32_t lc = (uint32_t)(c % g.bin[t]);
+    packed |= (g.d == 1) ? lc : (lc << (bits * t));
+    dst[t][pos] = dl;
+  }
+  perm[pos] = (int)j;
+  local[pos] = packed;
+}
+
+// Exclusive scan of n ints with one block of 1024 threads: each thread scans a
+// contiguous chunk sequentially, the chunk totals are scanned in shared memory.
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* __restrict__ out, int n,
+                                                int* __restrict__ total) {
+  __shared__ int part[1024];
+  const int T = blockDim.x;
+  const int chunk = (n + T - 1) / T;
+  const int lo = min(n, threadIdx.x * chunk);
+  const int hi = min(n, lo + chunk);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the chunk totals
+  for (int off = 1; off < T; off <<= 1) {
+    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int i = lo; i < hi; ++i) {
+    const int v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (total && threadIdx.x == T - 1) *total = part[T - 1];
+}
+
+__global__ void k_sub_count(const int* __restrict__ bin_count, int nbins, int P, int* __restrict__ sub_count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nbins) sub_count[b] = (bin_count[b] + P - 1) / P;
+}
+
+__global__ void k_sub_fill(const int* __restrict__ bin_count, const int* __restrict__ bin_start,
+                           const int* __restrict__ sub_start, int nbins, int P, SubProblem* __restrict__ subs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const int cnt = bin_count[b];
+  const int s0 = sub_start[b];
+  for (int s = 0, off = 0; off < cnt; ++s, off += P) {
+    SubProblem sp;
+    sp.bin = b;
+    sp.start = bin_start[b] + off;
+    sp.count = min(P, cnt - off);
+    sp.pad_ = 0;
+    subs[s0 + s] = sp;
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+template <typename Real>
+cudaError_t launch_bin_count(const double* x, int64_t M, const GridGeom& g, int* bin_count, int2* bin_rank, int* err,
+                             cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_bin_count<Real><<<blocks_for(M, 256), 256, 0, st>>>(x, M, g, bin_count, bin_rank, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int* in, int* out, int n, int* total, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(in, out, n, total);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_scatter(const double* x, int64_t M, const GridGeom& g, const int* bin_start, const int2* bin_rank,
+                           int* perm, uint32_t* local, Real* const* delta, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_scatter<Real><<<blocks_for(M, 256), 256, 0, st>>>(x, M, g, bin_start, bin_rank, perm, local, delta[0], delta[1],
+                                                      delta[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subproblem_count(const int* bin_count, int nbins, int P, int* sub_count, cudaStream_t st) {
+  k_sub_count<<<blocks_for(nbins, 256), 256, 0, st>>>(bin_count, nbins, P, sub_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subproblem_fill(const int* bin_count, const int* bin_start, const int* sub_start, int nbins, int P,
+                                   SubProblem* subs, cudaStream_t st) {
+  k_sub_fill<<<blocks_for(nbins, 256), 256, 0, st>>>(bin_count, bin_start, sub_start, nbins, P, subs);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_bin_count<float>(const double*, int64_t, const GridGeom&, int*, int2*, int*, cudaStream_t);
+template cudaError_t launch_bin_count<double>(const double*, int64_t, const GridGeom&, int*, int2*, int*, cudaStream_t);
+template cudaError_t launch_scatter<float>(const double*, int64_t, const GridGeom&, const int*, const int2*, int*,
+                                           uint32_t*, float* const*, cudaStream_t);
+template cudaError_t launch_scatter<double>(const double*, int64_t, const GridGeom&, const int*, const int2*, int*,
+                                            uint32_t*, double* const*, cudaStream_t);
+
+}  // namespace gbnfft

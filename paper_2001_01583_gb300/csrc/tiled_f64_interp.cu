@@ -1,0 +1,21 @@
+// Instantiations of the tiled interp kernel for double (one translation unit per
+// kernel and precision so the build compiles them in parallel).
+#include "points_tiled.cuh"
+
+namespace gbnfft {
+
+#define GBNFFT_CASE(D, W, R) \
+  case (D) * 100 + (W):      \
+    return reinterpret_cast<const void*>(&k_interp_tiled<D, W, R>);
+
+const void* interp_tiled_kernel_f64(int d, int taps) {
+  switch (d * 100 + taps) {
+    GBNFFT_TAPS_1_2(GBNFFT_CASE, 1, double)
+    GBNFFT_TAPS_1_2(GBNFFT_CASE, 2, double)
+    GBNFFT_TAPS_3(GBNFFT_CASE, 3, double)
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace gbnfft

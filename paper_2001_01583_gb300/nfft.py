@@ -1,0 +1,145 @@
+"""Python front end of the gbnfft C ABI, on PyTorch tensors.
+
+PyTorch provides device memory and streams only; every transform step runs in
+libgbnfft.so.  Tensors on the GPU are used in place.  Tensors on the host are
+copied to the GPU on the plan's stream first and the result is copied back
+(the end-to-end path a caller with host data uses).
+
+Names follow the paper (Section 1): N bandwidths (I_N), M points x_j,
+adjoint = Eq. 5 (fhat(k) = sum_j f(x_j) exp(-2 pi i k.x_j)),
+forward = Eq. 6 (f(x_j) = sum_k fhat(k) exp(+2 pi i k.x_j)).
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An NFFT plan: bandwidth N (d even ints), M points, oversampling sigma,
+    cut-off m, window ("kaiser_bessel" or "gaussian"), precision ("fp32" for
+    the mixed FP32 form, "fp64" for the plain FP64 form)."""
+
+    def __init__(self, N, M, sigma=2.0, m=4, window="kaiser_bessel", precision="fp32", stream=None):
+        self._lib = _lib.load()
+        self.N = tuple(int(v) for v in N)
+        self.d = len(self.N)
+        self.M = int(M)
+        self.window = _lib.WINDOWS[window] if isinstance(window, str) else int(window)
+        self.precision = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.cdtype = torch.complex128 if self.precision == _lib.FP64 else torch.complex64
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        Narr = (ctypes.c_int64 * self.d)(*self.N)
+        _lib.check(self._lib.nfft_plan_create(ctypes.byref(h), self.d, Narr, self.M, float(sigma), int(m),
+                                              self.window, self.precision, _stream_handle(self.stream)),
+                   "nfft_plan_create")
+        self._h = h
+        self._x = None
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.nfft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers -----------------------------------------------------------------
+    def _to_device(self, t, dtype):
+        if t.device.type != "cuda":
+            with torch.cuda.stream(self.stream):
+                return t.to(device=self.device, dtype=dtype, non_blocking=True).contiguous(), True
+        if t.dtype != dtype:
+            raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+        return t.contiguous(), False
+
+    # -- C ABI calls ---------------------------------------------------------------
+    def set_points(self, x):
+        """x: (M, d) float64, any finite values (wrapped into [-1/2, 1/2)^d)."""
+        if tuple(x.shape) != (self.M, self.d):
+            raise ValueError("points must have shape (%d, %d)" % (self.M, self.d))
+        xd, _ = self._to_device(x, torch.float64)
+        self._x = xd  # keep alive until the sort kernels have read it
+        _lib.check(self._lib.nfft_set_points(self._h, ctypes.c_void_p(xd.data_ptr())), "nfft_set_points")
+
+    def adjoint(self, f, out=None):
+        """Eq. 5.  f: (M,) or (R, M) complex; returns N or (R,) + N complex."""
+        single = f.dim() == 1
+        rows = (1 if single else f.shape[0]) if self.M == 0 else -1
+        fd, host = self._to_device(f.reshape(rows, self.M), self.cdtype)
+        R = fd.shape[0]
+        if out is None:
+            out = torch.empty((R,) + self.N, dtype=self.cdtype, device=self.device)
+        _lib.check(self._lib.nfft_adjoint(self._h, ctypes.c_void_p(fd.data_ptr()), ctypes.c_void_p(out.data_ptr()), R),
+                   "nfft_adjoint")
+        if host:
+            with torch.cuda.stream(self.stream):
+                out = out.to("cpu")
+        return out[0] if single else out
+
+    def forward(self, fhat, out=None):
+        """Eq. 6.  fhat: N or (R,) + N complex; returns (M,) or (R, M) complex."""
+        single = fhat.dim() == self.d
+        hd, host = self._to_device(fhat.reshape((-1,) + self.N), self.cdtype)
+        R = hd.shape[0]
+        if out is None:
+            out = torch.empty((R, self.M), dtype=self.cdtype, device=self.device)
+        _lib.check(self._lib.nfft_forward(self._h, ctypes.c_void_p(hd.data_ptr()), ctypes.c_void_p(out.data_ptr()), R),
+                   "nfft_forward")
+        if host:
+            with torch.cuda.stream(self.stream):
+                out = out.to("cpu")
+        return out[0] if single else out
+
+    def sync(self):
+        """Wait for the plan's stream; raises NFFTError for a device-side error."""
+        _lib.check(self._lib.nfft_sync(self._h), "nfft_sync")
+
+    def set_option(self, option, value):
+        _lib.check(self._lib.nfft_set_option(self._h, int(option), int(value)), "nfft_set_option")
+
+    def info(self):
+        inf = _lib.PlanInfo()
+        _lib.check(self._lib.nfft_get_info(self._h, ctypes.byref(inf)), "nfft_get_info")
+        return dict(d=inf.d, N=tuple(inf.N[:inf.d]), n=tuple(inf.n[:inf.d]), M=inf.M, m=inf.m, taps=inf.taps,
+                    window=inf.window, precision=inf.precision, method=inf.method, bin=tuple(inf.bin[:inf.d]),
+                    n_bins=inf.n_bins, rhs_capacity=inf.rhs_capacity, threads=inf.threads,
+                    device_bytes=inf.device_bytes, sigma=tuple(inf.sigma[:inf.d]))
+
+    def stage_times(self, reset=False):
+        """Per-stage milliseconds and call counts (needs OPT_PROFILE on)."""
+        ms = (ctypes.c_double * len(_lib.STAGES))()
+        n = (ctypes.c_int64 * len(_lib.STAGES))()
+        _lib.check(self._lib.nfft_stage_times(self._h, ms, n, 1 if reset else 0), "nfft_stage_times")
+        return {s: (ms[i], n[i]) for i, s in enumerate(_lib.STAGES)}
+
+
+def plan_params(N, sigma=2.0, m=4, window="kaiser_bessel"):
+    """Host-only rule: oversampled sizes n_t and window taps per dimension."""
+    lib = _lib.load()
+    d = len(N)
+    Narr = (ctypes.c_int64 * d)(*[int(v) for v in N])
+    nout = (ctypes.c_int64 * d)()
+    taps = ctypes.c_int()
+    win = _lib.WINDOWS[window] if isinstance(window, str) else int(window)
+    _lib.check(lib.nfft_plan_params(d, Narr, float(sigma), int(m), win, nout, ctypes.byref(taps)), "nfft_plan_params")
+    return tuple(nout), taps.value

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Two oracles, two bars:
+  - the direct NDFT (Eqs. 5, 6): relative l2 error (Eq. 9) within the window
+    error stated per configuration;
+  - the step-by-step gridding NFFT in FP64 (same window, same n, same taps):
+    element by element at rounding level (FP64 path) or FP32 rounding level
+    (mixed path), which pins the kernels themselves, not just the method.
+Sizes span several bins and a ragged last bin; edge cases cover empty and
+tiny inputs, points on cell boundaries and outside [-1/2, 1/2), lattice
+points on grid nodes, and the error statuses.
+"""
+import numpy as np
+import pytest
+
+from oracle import ndft, nfft_steps as S
+from paper_2001_01583_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WIN = {"gaussian": S.GAUSSIAN, "kaiser_bessel": S.KAISER_BESSEL}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _plan(N, M, sigma, m, window, precision, **opts):
+    from paper_2001_01583_gb300 import Plan, _lib
+    p = Plan(N, M, sigma, m, window, precision)
+    for k, v in opts.items():
+        p.set_option(getattr(_lib, "OPT_" + k.upper()), v)
+    return p
+
+
+def _cdt(precision):
+    return torch.complex128 if precision == "fp64" else torch.complex64
+
+
+def _run(N, x, f, fh, sigma, m, window, precision, **opts):
+    M = x.shape[0]
+    with _plan(N, M, sigma, m, window, precision, **opts) as p:
+        p.set_points(torch.from_numpy(x).cuda())
+        a = p.adjoint(torch.from_numpy(f).to(_cdt(precision)).cuda())
+        b = p.forward(torch.from_numpy(fh).to(_cdt(precision)).cuda())
+        p.sync()
+        return a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128), p.info()
+
+
+def _elementwise(got, ref, tol):
+    """max |got - ref| <= tol * rms(ref), element by element."""
+    got = np.asarray(got).ravel()
+    ref = np.asarray(ref).ravel()
+    scale = np.sqrt(np.mean(np.abs(ref) ** 2))
+    err = np.max(np.abs(got - ref)) / scale
+    assert err <= tol, "elementwise error %.3g > %.3g" % (err, tol)
+
+
+# ---- the 1-D plain FP64 configuration: N = 256, M = 1024, sigma = 2 ----------
+@pytest.mark.parametrize("window,m,tol", [("gaussian", 6, 2e-6), ("kaiser_bessel", 12, 1e-12),
+                                          ("gaussian", 12, 5e-12), ("kaiser_bessel", 6, 1e-10)])
+def test_1d_fp64_against_direct_ndft(window, m, tol):
+    N, M = (256,), 1024
+    rng = np.random.default_rng(0)
+    x = rng.random((M, 1)) - 0.5
+    f = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    fh = inputs.complex_normal(N, seed=1)
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, "fp64")
+    assert info["n"] == (512,)
+    assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= tol
+    assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= tol
+    # the kernels reproduce the FP64 gridding method to rounding
+    _elementwise(a, S.adjoint(x, f, N, 2.0, m, WIN[window]), 1e-12)
+    _elementwise(b, S.forward(x, fh, N, 2.0, m, WIN[window]), 1e-12)
+
+
+# ---- multi-dimensional, several bins with ragged last bins -------------------
+CASES = [
+    # d, N, M, window, m
+    (1, (200,), 3001, "kaiser_bessel", 5),
+    (2, (44, 36), 4000, "gaussian", 3),
+    (2, (40, 30), 2500, "kaiser_bessel", 4),
+    (3, (22, 18, 16), 5000, "kaiser_bessel", 4),
+    (3, (20, 14, 12), 3000, "gaussian", 2),
+]
+
+
+@pytest.mark.parametrize("d,N,M,window,m", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("method", ["tiled", "global"])
+def test_against_oracles(d, N, M, window, m, precision, method):
+    x = inputs.uniform_points(M, d, seed=5 + d)
+    f = inputs.complex_normal(M, seed=6)
+    fh = inputs.complex_normal(N, seed=7)
+    meth = {"tiled": 1, "global": 2}[method]
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, method=meth)
+    assert info["method"] == meth
+    sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
+    sb = S.forward(x, fh, N, 2.0, m, WIN[window])
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    _elementwise(a, sa, tol)
+    _elementwise(b, sb, tol)
+    # against the exact sums: the method's own error plus rounding
+    ea = ndft.rel_l2(sa, ndft.adjoint(x, f, N))
+    eb = ndft.rel_l2(sb, ndft.forward(x, fh, N))
+    slack = 1e-13 if precision == "fp64" else 1e-6
+    assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= ea * 1.01 + slack
+    assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= eb * 1.01 + slack
+
+
+def test_3d_config_accuracy_target_small():
+    # the 3-D target: Kaiser-Bessel m = 4, sigma = 2, rel-l2 1e-6 in FP32
+    N, M = (32, 32, 32), 20000
+    x = inputs.uniform_points(M, 3, seed=21)
+    f = inputs.complex_normal(M, seed=22)
+    fh = inputs.complex_normal(N, seed=23)
+    for precision in ("fp32", "fp64"):
+        a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", precision)
+        assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 1e-6
+        assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= 1e-6
+
+
+def test_clustered_points_split_into_subproblems():
+    N, M = (24, 24, 24), 30000
+    x = inputs.clustered_points(M, 3, 4, 0.01, seed=31)
+    f = inputs.complex_normal(M, seed=32)
+    fh = inputs.complex_normal(N, seed=33)
+    for P in (64, 1024):
+        a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", "fp32", max_subproblem=P)
+        _elementwise(a, S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL), 2e-6)
+        _elementwise(b, S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL), 2e-6)
+
+
+def test_multiple_right_hand_sides():
+    N, M, R = (16, 20, 12), 3000, 5
+    x = inputs.uniform_points(M, 3, seed=41)
+    F = inputs.complex_normal((R, M), seed=42)
+    H = inputs.complex_normal((R,) + N, seed=43)
+    with _plan(N, M, 2.0, 4, "kaiser_bessel", "fp64", rhs_capacity=2) as p:
+        p.set_points(torch.from_numpy(x).cuda())
+        A = p.adjoint(torch.from_numpy(F).cuda()).cpu().numpy()
+        B = p.forward(torch.from_numpy(H).cuda()).cpu().numpy()
+        p.sync()
+    for r in range(R):
+        _elementwise(A[r], S.adjoint(x, F[r], N, 2.0, 4, S.KAISER_BESSEL), 1e-12)
+        _elementwise(B[r], S.forward(x, H[r], N, 2.0, 4, S.KAISER_BESSEL), 1e-12)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_adjoint_identity_on_gpu(precision, tol):
+    N, M = (18, 16, 14), 4000
+    x = inputs.uniform_points(M, 3, seed=51)
+    f = inputs.complex_normal(M, seed=52)
+    g = inputs.complex_normal(N, seed=53)
+    a, b, _ = _run(N, x, f, g, 2.0, 4, "kaiser_bessel", precision)
+    lhs = np.vdot(b, f)      # <A^H g, f>
+    rhs = np.vdot(g, a)      # <g, A f>
+    assert abs(lhs - rhs) <= tol * abs(lhs)
+
+
+# ---- edge cases ---------------------------------------------------------------
+def test_empty_point_set():
+    N = (8, 8)
+    with _plan(N, 0, 2.0, 3, "kaiser_bessel", "fp64") as p:
+        p.set_points(torch.zeros((0, 2), dtype=torch.float64, device="cuda"))
+        a = p.adjoint(torch.zeros((0,), dtype=torch.complex128, device="cuda"))
+        b = p.forward(torch.ones(N, dtype=torch.complex128, device="cuda"))
+        p.sync()
+    assert torch.count_nonzero(a).item() == 0
+    assert b.numel() == 0
+
+
+def test_single_point_and_boundaries():
+    N = (16, 12, 10)
+    pts = np.array([[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [0.49999999999, -0.25, 0.0], [3.75, -7.125, 12.5]])
+    f = np.array([1.0 + 0.0j, 0.5 - 2j, -1j, 2.0])
+    fh = inputs.complex_normal(N, seed=61)
+    for precision, tol in (("fp64", 1e-12), ("fp32", 2e-6)):
+        a, b, _ = _run(N, pts, f, fh, 2.0, 5, "kaiser_bessel", precision)
+        _elementwise(a, S.adjoint(pts, f, N, 2.0, 5, S.KAISER_BESSEL), tol)
+        _elementwise(b, S.forward(pts, fh, N, 2.0, 5, S.KAISER_BESSEL), tol)
+        assert ndft.rel_l2(a, ndft.adjoint(pts, f, N)) <= 1e-7
+        a1, _, _ = _run(N, pts[:1], f[:1], fh, 2.0, 5, "kaiser_bessel", precision)
+        assert ndft.rel_l2(a1, ndft.adjoint(pts[:1], f[:1], N)) <= 1e-7   # exp(-2 pi i k.x)
+
+
+def test_lattice_points_on_grid_nodes():
+    # fluorite lattice, 2 cells: n x_t lands exactly on cell boundaries
+    r, q, L = inputs.fluorite(2)
+    x = inputs.box_points(r, L)
+    N = (16, 16, 16)
+    f = q.astype(np.complex128)
+    fh = inputs.complex_normal(N, seed=71)
+    a, b, _ = _run(N, x, f, fh, 2.0, 6, "kaiser_bessel", "fp64")
+    _elementwise(a, S.adjoint(x, f, N, 2.0, 6, S.KAISER_BESSEL), 1e-12)
+    _elementwise(b, S.forward(x, fh, N, 2.0, 6, S.KAISER_BESSEL), 1e-12)
+    assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 1e-9
+
+
+def test_error_statuses():
+    from paper_2001_01583_gb300 import _lib
+    N, M = (8, 8), 10
+    with _plan(N, M, 2.0, 3, "kaiser_bessel", "fp64") as p:
+        f = torch.zeros(M, dtype=torch.complex128, device="cuda")
+        with pytest.raises(_lib.NFFTError) as e:
+            p.adjoint(f)                                     # before set_points
+        assert e.value.status == _lib.ERR_NOT_READY
+        x = torch.zeros((M, 2), dtype=torch.float64, device="cuda")
+        x[3, 1] = float("nan")
+        p.set_points(x)
+        with pytest.raises(_lib.NFFTError) as e:
+            p.sync()
+        assert e.value.status == _lib.ERR_DOMAIN
+        p.sync()                                             # the flag was cleared
+        with pytest.raises(_lib.NFFTError) as e:
+            p.set_option(_lib.OPT_THREADS, 33)
+        assert e.value.status == _lib.ERR_INVALID_ARG
+    with pytest.raises(_lib.NFFTError) as e:
+        _plan((7, 8), 10, 2.0, 3, "kaiser_bessel", "fp64")
+    assert e.value.status == _lib.ERR_INVALID_ARG
+
+
+def test_host_buffers_end_to_end():
+    N, M = (16, 16), 500
+    x = inputs.uniform_points(M, 2, seed=81)
+    f = inputs.complex_normal(M, seed=82)
+    with _plan(N, M, 2.0, 4, "kaiser_bessel", "fp64") as p:
+        p.set_points(torch.from_numpy(x).pin_memory())
+        a = p.adjoint(torch.from_numpy(f).pin_memory())
+        p.sync()
+    assert a.device.type == "cpu"
+    _elementwise(a.numpy(), S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL), 1e-12)
+
+
+# ---- full size of the 3-D configuration, sampled oracle ----------------------
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_full_size_3d_sampled(kind):
+    N, M = (64, 64, 64), 10 ** 6
+    if kind == "uniform":
+        x = inputs.uniform_points(M, 3, seed=0)
+    else:
+        x = inputs.clustered_points(M, 3, 32, 0.02, seed=0)
+    f = inputs.complex_normal(M, seed=1, dtype=np.complex64).astype(np.complex128)
+    fh = inputs.complex_normal(N, seed=2, dtype=np.complex64).astype(np.complex128)
+    a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", "fp32")
+    rng = np.random.default_rng(3)
+    ks = np.stack([rng.integers(-32, 32, size=48) for _ in range(3)], axis=1)
+    ref_a = ndft.adjoint(x, f, N, ksel=ks)
+    got_a = a[ks[:, 0] + 32, ks[:, 1] + 32, ks[:, 2] + 32]
+    assert ndft.rel_l2(got_a, ref_a) <= 1e-6
+    js = rng.integers(0, M, size=48)
+    assert ndft.rel_l2(b[js], ndft.forward(x, fh, N, jsel=js)) <= 1e-6
