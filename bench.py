@@ -1,22 +1,24 @@
 """Throughput benchmark of the GB300 NFFT library.
 
-Workload (one "step"): the 3-D configuration N = 64^3, M = 10^6, Kaiser-Bessel
-window m = 4, sigma = 2, mixed FP32 form, on two point sets (uniform, and 32
-Gaussian clusters of std 0.02).  For each set a step runs nfft_set_points
-(argument reduction + bin sort), the adjoint NFFT (Eq. 5: spread, FFT, scale)
-and the forward NFFT (Eq. 6: subdivide, inverse FFT, interpolate).  Units: a
-transform of M points counts M nonuniform points, so a step processes
-2 sets x 2 transforms x M points.
+Workload (one "step", default): the 3-D configuration N = 64^3, M = 10^6,
+Kaiser-Bessel window m = 4, sigma = 2, mixed FP32 form, on two point sets
+(uniform, and 32 Gaussian clusters of std 0.02).  For each set a step runs
+nfft_set_points (argument reduction + bin sort), the adjoint NFFT (Eq. 5:
+spread, FFT, scale) and the forward NFFT (Eq. 6: subdivide, inverse FFT,
+interpolate).  Units: a transform of M points counts M nonuniform points, so a
+step processes 2 sets x 2 transforms x M points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload config|small] [--no-cpu-baseline]
 
-Prints one JSON line (rank 0).  Under torchrun every rank runs its own
-independent copy of the workload (weak scaling, no collective on the data
-path); the value is all ranks' points over the slowest rank's time.
+"--workload small" (N = 32^3, M = 2.5e5, uniform only) is the case profiled
+with ncu's multi-pass sections.  Prints one JSON line (rank 0).  Under torchrun
+every rank runs its own independent copy of the workload (weak scaling, no
+collective on the data path); the value is all ranks' points over the slowest
+rank's time.
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -30,10 +32,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NFFT nonuniform points/s at stated rel-l2 error; % of HBM roofline"
 UNIT = "points/s"
-N3 = (64, 64, 64)
-M = 10 ** 6
 SIGMA, MCUT, WINDOW = 2.0, 4, "kaiser_bessel"
-WORKLOAD = "3-D adjoint+forward NFFT, N=64^3, M=10^6, uniform + clustered (32 clusters, std 0.02), KB m=4, sigma=2, FP32 mixed"
+
+WORKLOADS = {
+    "config": dict(N=(64, 64, 64), M=10 ** 6, sets=("uniform", "clustered"),
+                   name="3-D adjoint+forward NFFT, N=64^3, M=10^6, uniform + clustered (32 clusters, std 0.02), "
+                        "Kaiser-Bessel m=4, sigma=2, mixed FP32"),
+    "small": dict(N=(32, 32, 32), M=250000, sets=("uniform",),
+                  name="3-D adjoint+forward NFFT, N=32^3, M=2.5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
+                       "(profiling case)"),
+}
+
+# bytes of the shared-memory traffic per cell visit: spread reads and writes
+# one complex64 tile cell, interpolation reads one
+SMEM_BYTES_PER_CELL = {"spread": 16, "interp": 8}
+SMEM_BYTES_PER_CLK_PER_SM = 128   # 32 banks x 4 B
 
 
 def _env_int(name, default):
@@ -48,7 +61,58 @@ def _peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return json.load(fh), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _taps():
+    return 2 * MCUT   # Kaiser-Bessel: 2m nonzero taps per dimension
+
+
+def _stage_hbm_bytes(stage, wl):
+    """Algorithmic HBM bytes of one launch of a stage (complex64 data)."""
+    M = wl["M"]
+    NN = int(np.prod(wl["N"]))
+    cells = int(np.prod([2 * n for n in wl["N"]]))
+    return {
+        # point record (4 B index + 4 B packed cell + 3 x 4 B offsets) + one value (8 B) + grid once (8 B / cell)
+        "spread": M * (20 + 8) + cells * 8,
+        "interp": M * (20 + 8) + cells * 8,
+        # in-place C2C FFT: one read and one write of the grid
+        "fft": 2 * cells * 8,
+        "ifft": 2 * cells * 8,
+        "deconv": NN * 8 * 2,
+        "pad": cells * 8 + NN * 8,
+        # x read twice (24 B each), bin/rank record written + read (8 B), sorted record written (20 B)
+        "sort": M * (2 * 24 + 16 + 20),
+    }[stage]
+
+
+def _step_hbm_bytes(wl):
+    per_set = sum(_stage_hbm_bytes(s, wl) for s in ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp"))
+    return per_set * len(wl["sets"])
+
+
+def _roofline(stages, wl, peaks, kind, sms):
+    total = {k: v[0] for k, v in stages.items() if v[1] > 0}
+    per_launch = {k: v[0] / v[1] for k, v in stages.items() if v[1] > 0}
+    dom = max(total, key=total.get)
+    t = per_launch[dom] * 1e-3
+    if dom in SMEM_BYTES_PER_CELL:
+        # on-chip bound: the shared-memory pipe, 128 B per clock per SM
+        visits = wl["M"] * _taps() ** 3
+        achieved = visits * SMEM_BYTES_PER_CELL[dom] / t / 1e9
+        peak = sms * SMEM_BYTES_PER_CLK_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        r = {"bound": "alu", "resource": "shared-memory load/store pipe (%d SMs x 128 B/clk x %.0f MHz)" %
+             (sms, peaks.get("sm_max_mhz", 2070.0)), "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "peak_kind": "derived from unit counts and max clock",
+             "cell_updates_per_s": visits / t}
+    else:
+        achieved = _stage_hbm_bytes(dom, wl) / t / 1e9
+        r = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind}
+    r.update({"kernel": dom, "traffic": None, "launch_ms": per_launch[dom],
+              "stage_share": {k: round(v / sum(total.values()), 4) for k, v in total.items()}})
+    return r
 
 
 class ClockSampler:
@@ -104,91 +168,89 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_sample(seconds_target=15.0):
+def _oracle_sample(wl, seconds_target=15.0):
     """Time the FP64 direct NDFT (the oracle, as it stands) on the host cores
-    for a bounded sample of the workload's points: adjoint over all of I_N
-    and forward at the same points.  Returns (points/s, threads, description)."""
+    for a bounded sample of the workload's points: the adjoint over all of I_N
+    and the forward at the same points.  Returns (points/s, threads, text)."""
     from oracle import ndft
     from paper_2001_01583_gb300 import inputs
+    N, M = wl["N"], wl["M"]
     x = inputs.uniform_points(M, 3, seed=0)
     f = inputs.complex_normal(M, seed=1)
-    fh = inputs.complex_normal(N3, seed=2)
+    fh = inputs.complex_normal(N, seed=2)
     threads = ndft.threads_used(0)
-    # calibrate on a small sample, then size the run to about seconds_target
     m0 = 256
     t0 = time.perf_counter()
-    ndft.adjoint(x[:m0], f[:m0], N3)
-    ndft.forward(x[:m0], fh, N3)
+    ndft.adjoint(x[:m0], f[:m0], N)
+    ndft.forward(x[:m0], fh, N)
     dt = max(time.perf_counter() - t0, 1e-3)
     ms = int(min(M, max(m0, m0 * seconds_target / dt)))
     t0 = time.perf_counter()
-    ndft.adjoint(x[:ms], f[:ms], N3)
-    ndft.forward(x[:ms], fh, N3)
+    ndft.adjoint(x[:ms], f[:ms], N)
+    ndft.forward(x[:ms], fh, N)
     dt = time.perf_counter() - t0
-    # two transforms of ms points each
-    return 2 * ms / dt, threads, "direct NDFT adjoint (all of I_N = 64^3) + forward at the first %d of the " \
-                                 "uniform points, FP64, %d threads, %.1f s" % (ms, threads, dt)
+    return 2 * ms / dt, threads, "direct NDFT adjoint (all of I_N = %s) + forward at the first %d uniform points, " \
+                                 "FP64, %d threads, %.1f s" % ("x".join(map(str, N)), ms, threads, dt)
 
 
-def run_reference(args, rank, world):
+def run_reference(args, wl, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
         return 0
-    steps = []
-    desc = ""
-    threads = 0
+    vals, desc, threads = [], "", 0
     for i in range(args.warmup + args.steps):
-        v, threads, desc = _oracle_sample(seconds_target=6.0 if i >= args.warmup else 2.0)
+        v, threads, desc = _oracle_sample(wl, seconds_target=6.0 if i >= args.warmup else 1.0)
         if i >= args.warmup:
-            steps.append(v)
-    value = float(np.median(steps))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            vals.append(v)
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"] + " (oracle: FP64 direct NDFT on a bounded sample of the points)",
+                       "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args, rank, world):
+def run_ours(args, wl, rank, world):
     import torch
     import torch.distributed as dist
 
     from paper_2001_01583_gb300 import Plan, _lib, inputs
-    from paper_2001_01583_gb300.build import build as build_lib
 
+    N, M = wl["N"], wl["M"]
     local = _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if not os.path.exists(_lib.LIB_PATH):
-        build_lib()
+    _lib.load()   # fails loudly if the CUDA library was not built
     stream = torch.cuda.Stream(dev)
 
     # inputs: every rank its own seeds (independent problems)
-    xs_host = [inputs.uniform_points(M, 3, seed=100 * rank + 0),
-               inputs.clustered_points(M, 3, 32, 0.02, seed=100 * rank + 1)]
-    f_host = inputs.complex_normal(M, seed=100 * rank + 2, dtype=np.complex64)
-    fh_host = inputs.complex_normal(N3, seed=100 * rank + 3, dtype=np.complex64)
+    gens = {"uniform": lambda s: inputs.uniform_points(M, 3, seed=s),
+            "clustered": lambda s: inputs.clustered_points(M, 3, 32, 0.02, seed=s)}
+    xs_host = [gens[name](100 * rank + i) for i, name in enumerate(wl["sets"])]
+    f_host = inputs.complex_normal(M, seed=100 * rank + 7, dtype=np.complex64)
+    fh_host = inputs.complex_normal(N, seed=100 * rank + 8, dtype=np.complex64)
 
     with torch.cuda.stream(stream):
         xs = [torch.from_numpy(x).to(dev) for x in xs_host]
         f = torch.from_numpy(f_host).to(dev)
         fh = torch.from_numpy(fh_host).to(dev)
-        outs_a = [torch.empty(N3, dtype=torch.complex64, device=dev) for _ in xs]
-        outs_f = [torch.empty(M, dtype=torch.complex64, device=dev) for _ in xs]
+        outs_a = [torch.empty((1,) + N, dtype=torch.complex64, device=dev) for _ in xs]
+        outs_f = [torch.empty((1, M), dtype=torch.complex64, device=dev) for _ in xs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
-    plans = [Plan(N3, M, SIGMA, MCUT, WINDOW, "fp32", stream=stream) for _ in xs]
+    plans = [Plan(N, M, SIGMA, MCUT, WINDOW, "fp32", stream=stream) for _ in xs]
     for p in plans:
         p.set_option(_lib.OPT_PROFILE, 1)
 
     def step():
         for p, x, a, b in zip(plans, xs, outs_a, outs_f):
             p.set_points(x)
-            p.adjoint(f, out=a.view((1,) + N3))
-            p.forward(fh, out=b.view(1, M))
+            p.adjoint(f, out=a)
+            p.forward(fh, out=b)
 
-    # warm-up
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -204,7 +266,7 @@ def run_ours(args, rank, world):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with torch.cuda.stream(stream):
         for i in range(args.steps):
-            flush.fill_(float(i))          # evict L2 between timed steps (outside the step's events)
+            flush.fill_(float(i))          # evict L2 between timed steps, outside the step's events
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
@@ -212,39 +274,39 @@ def run_ours(args, rank, world):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms_per_step = float(np.sum(step_ms)) / args.steps
-    stages = {}
-    for p in plans:
+    ms_per_step = float(np.sum([a.elapsed_time(b) for a, b in ev])) / args.steps
+    stages, per_set = {}, {}
+    for name, p in zip(wl["sets"], plans):
+        per_set[name] = {}
         for k, (ms, n) in p.stage_times(reset=True).items():
-            s = stages.setdefault(k, [0.0, 0])
-            s[0] += ms
-            s[1] += n
+            acc = stages.setdefault(k, [0.0, 0])
+            acc[0] += ms
+            acc[1] += n
+            if n:
+                per_set[name][k] = round(ms / n, 5)
     for p in plans:
         p.sync()
+        p.set_option(_lib.OPT_PROFILE, 0)
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned): inputs
+    # copied in and results copied out inside the timed region, every step
     xs_pin = [torch.from_numpy(x).pin_memory() for x in xs_host]
     f_pin = torch.from_numpy(f_host).pin_memory()
     fh_pin = torch.from_numpy(fh_host).pin_memory()
     h2d = sum(x.numel() * 8 for x in xs_pin) + f_pin.numel() * 8 + fh_pin.numel() * 8
-    d2h = len(xs) * (int(np.prod(N3)) * 8 + M * 8)
-    for p in plans:
-        p.set_option(_lib.OPT_PROFILE, 0)
+    d2h = len(xs) * (int(np.prod(N)) * 8 + M * 8)
 
     def e2e_step():
-        res = []
         for p, x in zip(plans, xs_pin):
             p.set_points(x)
-            res.append(p.adjoint(f_pin))
-            res.append(p.forward(fh_pin))
-        return res
+            p.adjoint(f_pin)
+            p.forward(fh_pin)
 
     with torch.cuda.stream(stream):
         e2e_step()
     torch.cuda.synchronize(dev)
     e_ms = []
-    for i in range(max(2, min(args.steps, 5))):
+    for i in range(max(3, min(args.steps, 5))):
         flush.fill_(float(i))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -261,39 +323,27 @@ def run_ours(args, rank, world):
     value = points_per_step * world / (ms_max * 1e-3)
     e2e_value = points_per_step * world / (e2e_max * 1e-3)
 
-    # roofline of the dominant kernel (largest stage share)
     peaks, kind = _peaks()
-    per_kernel = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
-    total = {k: v[0] for k, v in stages.items()}
-    dom = max(total, key=total.get)
-    cells = 128 ** 3
-    bytes_alg = {
-        # sorted point records read (4 B perm + 4 B packed cell + 12 B offsets) + gathered f (8 B) + grid flushed (8 B/cell)
-        "spread": M * (20 + 8) + cells * 8,
-        "interp": M * (20 + 8) + cells * 8,
-        "fft": 2 * 2 * cells * 8,
-        "ifft": 2 * 2 * cells * 8,
-        "deconv": int(np.prod(N3)) * 8 * 2,
-        "pad": cells * 8 + int(np.prod(N3)) * 8,
-        "sort": M * (24 + 8 + 24 + 20),
-    }
-    achieved = bytes_alg.get(dom, 0) / (per_kernel[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_kind": kind, "stage_ms_per_launch": {k: round(v, 5) for k, v in per_kernel.items()}}
+    props = torch.cuda.get_device_properties(dev)
+    roofline = _roofline(stages, wl, peaks, kind, props.multi_processor_count)
+    hbm_step = _step_hbm_bytes(wl)
+    roofline["step_hbm_bytes"] = hbm_step
+    roofline["step_hbm_frac"] = hbm_step / (ms_max * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    roofline["stage_ms_per_set"] = per_set
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, threads, desc = _oracle_sample()
+        v, threads, desc = _oracle_sample(wl)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
+    # kernels of this library per set and step: 6 in set_points, spread + scale, subdivide + interpolate
     launches_per_step = len(xs) * (6 + 2 + 2)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points_per_step_per_gpu": points_per_step,
-                       "l2": "flushed between timed steps (512 MB write, outside the step events)",
-                       "parallelism": "replicas x%d" % world},
+            "config": {"workload": wl["name"], "points_per_step_per_gpu": points_per_step,
+                       "l2": "flushed between timed steps (512 MB write outside the step events)",
+                       "parallelism": "independent replicas x%d" % world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
@@ -310,18 +360,20 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     if args.impl == "reference":
-        return run_reference(args, rank, world)
+        return run_reference(args, wl, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        return run_ours(args, rank, world)
+        return run_ours(args, wl, rank, world)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -4,8 +4,14 @@ Two oracles, two bars:
   - the direct NDFT (Eqs. 5, 6): relative l2 error (Eq. 9) within the window
     error stated per configuration;
   - the step-by-step gridding NFFT in FP64 (same window, same n, same taps):
-    element by element at rounding level (FP64 path) or FP32 rounding level
-    (mixed path), which pins the kernels themselves, not just the method.
+    element by element, max |gpu - oracle| / rms(oracle) <= 1e-12 for the FP64
+    path and <= FP32_ELEM for the mixed path, which pins the kernels
+    themselves, not just the method.
+FP32_ELEM: the mixed path rounds window weights (about 1e-7 relative each) and
+sums up to K contributions per grid cell in FP32, whose rounding grows like
+sqrt(K) * 6e-8 relative to a cell; with strongly clustered points (K in the
+thousands) the largest single output deviates by a few 1e-6 of the rms while
+the relative l2 error stays below 5e-7.
 Sizes span several bins and a ragged last bin; edge cases cover empty and
 tiny inputs, points on cell boundaries and outside [-1/2, 1/2), lattice
 points on grid nodes, and the error statuses.
@@ -20,6 +26,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 WIN = {"gaussian": S.GAUSSIAN, "kaiser_bessel": S.KAISER_BESSEL}
+FP32_ELEM = 1e-5
+FP32_L2 = 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -101,9 +109,11 @@ def test_against_oracles(d, N, M, window, m, precision, method):
     assert info["method"] == meth
     sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
     sb = S.forward(x, fh, N, 2.0, m, WIN[window])
-    tol = 1e-12 if precision == "fp64" else 2e-6
+    tol = 1e-12 if precision == "fp64" else FP32_ELEM
     _elementwise(a, sa, tol)
     _elementwise(b, sb, tol)
+    if precision == "fp32":
+        assert ndft.rel_l2(a, sa) <= FP32_L2 and ndft.rel_l2(b, sb) <= FP32_L2
     # against the exact sums: the method's own error plus rounding
     ea = ndft.rel_l2(sa, ndft.adjoint(x, f, N))
     eb = ndft.rel_l2(sb, ndft.forward(x, fh, N))
@@ -129,10 +139,15 @@ def test_clustered_points_split_into_subproblems():
     x = inputs.clustered_points(M, 3, 4, 0.01, seed=31)
     f = inputs.complex_normal(M, seed=32)
     fh = inputs.complex_normal(N, seed=33)
+    sa = S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL)
+    sb = S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL)
     for P in (64, 1024):
-        a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", "fp32", max_subproblem=P)
-        _elementwise(a, S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL), 2e-6)
-        _elementwise(b, S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL), 2e-6)
+        for precision, tol in (("fp32", FP32_ELEM), ("fp64", 1e-12)):
+            a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", precision, max_subproblem=P)
+            _elementwise(a, sa, tol)
+            _elementwise(b, sb, tol)
+            assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 1e-6
+            assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= 1e-6
 
 
 def test_multiple_right_hand_sides():
@@ -150,7 +165,7 @@ def test_multiple_right_hand_sides():
         _elementwise(B[r], S.forward(x, H[r], N, 2.0, 4, S.KAISER_BESSEL), 1e-12)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
 def test_adjoint_identity_on_gpu(precision, tol):
     N, M = (18, 16, 14), 4000
     x = inputs.uniform_points(M, 3, seed=51)
@@ -179,13 +194,15 @@ def test_single_point_and_boundaries():
     pts = np.array([[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [0.49999999999, -0.25, 0.0], [3.75, -7.125, 12.5]])
     f = np.array([1.0 + 0.0j, 0.5 - 2j, -1j, 2.0])
     fh = inputs.complex_normal(N, seed=61)
-    for precision, tol in (("fp64", 1e-12), ("fp32", 2e-6)):
+    for precision, tol in (("fp64", 1e-12), ("fp32", FP32_ELEM)):
         a, b, _ = _run(N, pts, f, fh, 2.0, 5, "kaiser_bessel", precision)
         _elementwise(a, S.adjoint(pts, f, N, 2.0, 5, S.KAISER_BESSEL), tol)
         _elementwise(b, S.forward(pts, fh, N, 2.0, 5, S.KAISER_BESSEL), tol)
-        assert ndft.rel_l2(a, ndft.adjoint(pts, f, N)) <= 1e-7
+        # Kaiser-Bessel m = 5 is accurate to about 1e-9, so FP32 rounding sets the bar
+        bar = 1e-8 if precision == "fp64" else FP32_L2
+        assert ndft.rel_l2(a, ndft.adjoint(pts, f, N)) <= bar
         a1, _, _ = _run(N, pts[:1], f[:1], fh, 2.0, 5, "kaiser_bessel", precision)
-        assert ndft.rel_l2(a1, ndft.adjoint(pts[:1], f[:1], N)) <= 1e-7   # exp(-2 pi i k.x)
+        assert ndft.rel_l2(a1, ndft.adjoint(pts[:1], f[:1], N)) <= bar   # exp(-2 pi i k.x)
 
 
 def test_lattice_points_on_grid_nodes():
