@@ -149,6 +149,26 @@ int nfft_adjoint(nfft_plan* plan, const void* f_dev, void* fhat_dev, int R);
 /* Eq. 6 for R right-hand sides (Fig. 2, Algorithm 5): f_dev[r] = A^H fhat_dev[r]. */
 int nfft_forward(nfft_plan* plan, const void* fhat_dev, void* f_dev, int R);
 
+/* Reciprocal-space Ewald energy of Section 5, Eq. 12, for charges q_j at the
+ * points set by nfft_set_points (x_j = r_j / L in box units):
+ *   U^K = 1/(2 pi L) sum_{n in I_N, n != 0} exp(-pi^2 |n|^2 / (alpha L)^2) / |n|^2 |S(n)|^2
+ *         - alpha / sqrt(pi) sum_j q_j^2,
+ *   S(n) = sum_j q_j exp(-2 pi i n.x_j)   (the adjoint, Eq. 5).
+ * q_dev: M complex values of the plan's precision (real charges: imaginary
+ * part 0).  Runs spreading and the FFT, then reduces the scaled spectrum in
+ * FP64 without writing fhat.  out (host, 3 doubles): out[0] = U^K,
+ * out[1] = the n-sum term, out[2] = the self term.  Waits for the stream.
+ * The sum runs over I_N only: it is converged only if the Gaussian factor is
+ * negligible outside I_N. */
+int nfft_ewald_reciprocal(nfft_plan* plan, const void* q_dev, double L, double alpha, double* out);
+
+/* The n-sum term of Eq. 12, 1/(2 pi L) sum_{n != 0} exp(-pi^2 |n|^2/(alpha L)^2) / |n|^2 |S(n)|^2,
+ * from a structure factor S_dev given on the plan's I_N (|I_N| complex of the
+ * plan's precision, layout of fhat).  Writes one double to sum_dev (device),
+ * asynchronously on the plan's stream, with a deterministic FP64 reduction
+ * (fixed tiles of 8192 elements, fixed summation tree). */
+int nfft_ewald_reciprocal_sum(nfft_plan* plan, const void* S_dev, double L, double alpha, double* sum_dev);
+
 /* Wait for the plan's stream, then report (and clear) the device error flag. */
 int nfft_sync(nfft_plan* plan);
 

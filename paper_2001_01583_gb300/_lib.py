@@ -81,6 +81,9 @@ def _declare(lib):
         "nfft_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), i64p, ctypes.c_int]),
         "nfft_plan_params": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_int, i64p,
                                             ctypes.POINTER(ctypes.c_int)]),
+        "nfft_ewald_reciprocal": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.POINTER(ctypes.c_double)]),
+        "nfft_ewald_reciprocal_sum": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, vp]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }

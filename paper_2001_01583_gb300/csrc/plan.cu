@@ -6,11 +6,13 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <vector>
 
 #include "gbnfft.h"
+#include "ewald.h"
 #include "kernels.h"
 
 using namespace gbnfft;
@@ -70,6 +72,8 @@ struct nfft_plan {
   uint32_t* local = nullptr;
   void* delta[3] = {nullptr, nullptr, nullptr};
   int* err_flag = nullptr;
+  double* ewald_partials = nullptr;   // reduction scratch (Eq. 12)
+  double* ewald_out = nullptr;        // [reciprocal sum, self term]
   int64_t device_bytes = 0;
   int64_t sort_capacity_bins = 0;
 
@@ -193,6 +197,8 @@ void release_all(nfft_plan* p) {
   v = p->perm; free_dev(v); p->perm = nullptr;
   v = p->local; free_dev(v); p->local = nullptr;
   v = p->err_flag; free_dev(v); p->err_flag = nullptr;
+  v = p->ewald_partials; free_dev(v); p->ewald_partials = nullptr;
+  v = p->ewald_out; free_dev(v); p->ewald_out = nullptr;
   for (auto& kv : p->ffts) cufftDestroy(kv.second);
   p->ffts.clear();
   for (auto& e : p->events) { cudaEventDestroy(e.start); cudaEventDestroy(e.stop); }
@@ -498,6 +504,51 @@ int set_points_impl(nfft_plan* p, const double* x) {
   return NFFT_OK;
 }
 
+EwaldGeom ewald_geom(const nfft_plan* p, double L, double alpha) {
+  EwaldGeom g{};
+  g.d = p->d;
+  g.NN = 1;
+  for (int t = 0; t < kMaxDim; ++t) {
+    g.N[t] = t < p->d ? (int)p->N[t] : 1;
+    g.n[t] = t < p->d ? (int)p->n[t] : 1;
+    g.inv_c[t] = t < p->d ? p->inv_c[t] : nullptr;
+  }
+  for (int t = 0; t < p->d; ++t) g.NN *= p->N[t];
+  const double al = alpha * L;
+  g.coef = M_PI * M_PI / (al * al);
+  return g;
+}
+
+// Eq. 12 from the charges: spread + FFT (adjoint steps 1-2), then the scaled
+// spectrum is weighted and reduced without forming fhat; the self term is a
+// second reduction over the charges.
+template <typename Real>
+int ewald_impl(nfft_plan* p, const void* q, double L, double alpha) {
+  using C = typename Cplx<Real>::type;
+  EventPair ev{};
+  TRY(stage_begin(p, NFFT_STAGE_SPREAD, &ev));
+  CK(cudaMemsetAsync(p->grid, 0, (size_t)p->geom.grid_cells * p->csize, p->stream));
+  if (p->M > 0) {
+    PointKernelArgs<Real> a = point_args<Real>(p);
+    a.f_in = static_cast<const C*>(q);
+    a.grid = static_cast<C*>(p->grid);
+    a.nrhs = 1;
+    TRY(run_points<Real>(p, a, true));
+  }
+  TRY(stage_end(p, &ev));
+  TRY(stage_begin(p, NFFT_STAGE_FFT, &ev));
+  TRY(run_fft(p, 1, CUFFT_FORWARD));
+  TRY(stage_end(p, &ev));
+  TRY(stage_begin(p, NFFT_STAGE_DECONV, &ev));
+  const EwaldGeom g = ewald_geom(p, L, alpha);
+  CK(launch_ewald_sum<Real>(static_cast<const C*>(p->grid), true, g, p->ewald_partials, 1.0 / (2.0 * M_PI * L), 0.0,
+                            p->ewald_out, p->stream));
+  CK(launch_sumsq<Real>(static_cast<const C*>(q), p->M, p->ewald_partials, -alpha / std::sqrt(M_PI), 0.0,
+                        p->ewald_out + 1, p->stream));
+  TRY(stage_end(p, &ev));
+  return NFFT_OK;
+}
+
 int validate_params(int d, const int64_t* N, int64_t M, double sigma, int m, int window, int precision) {
   if (d < 1 || d > 3 || !N) return NFFT_ERR_INVALID_ARG;
   if (M < 0 || M > (int64_t)INT32_MAX) return NFFT_ERR_INVALID_ARG;
@@ -618,6 +669,13 @@ int nfft_plan_create(nfft_plan** out, int d, const int64_t* N, int64_t M, double
     if ((s = alloc_dev(q, real_size * Mz, tot)) != NFFT_OK) return fail(s);
     p->delta[t] = q;
   }
+  {
+    int64_t NN = 1;
+    for (int t = 0; t < d; ++t) NN *= N[t];
+    const int64_t np = std::max(ewald_partials_needed(NN), ewald_partials_needed(M)) + 1;
+    if ((s = alloc_dev(p->ewald_partials, sizeof(double) * (size_t)np, tot)) != NFFT_OK) return fail(s);
+    if ((s = alloc_dev(p->ewald_out, sizeof(double) * 2, tot)) != NFFT_OK) return fail(s);
+  }
   if (cudaMemset(p->err_flag, 0, sizeof(int)) != cudaSuccess) return fail(NFFT_ERR_CUDA);
   if (cudaMemset(p->num_subs, 0, sizeof(int)) != cudaSuccess) return fail(NFFT_ERR_CUDA);
   if ((s = alloc_sort(p)) != NFFT_OK) return fail(s);
@@ -662,6 +720,35 @@ int nfft_forward(nfft_plan* p, const void* fhat_dev, void* f_dev, int R) {
   if (!p->points_set) return NFFT_ERR_NOT_READY;
   return p->precision == NFFT_FP64 ? forward_impl<double>(p, fhat_dev, f_dev, R)
                                    : forward_impl<float>(p, fhat_dev, f_dev, R);
+}
+
+int nfft_ewald_reciprocal(nfft_plan* p, const void* q_dev, double L, double alpha, double* out) {
+  if (!p || !out || !(L > 0.0) || !(alpha > 0.0) || !std::isfinite(L) || !std::isfinite(alpha))
+    return NFFT_ERR_INVALID_ARG;
+  if (!q_dev && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  if (!p->points_set) return NFFT_ERR_NOT_READY;
+  TRY(p->precision == NFFT_FP64 ? ewald_impl<double>(p, q_dev, L, alpha) : ewald_impl<float>(p, q_dev, L, alpha));
+  double parts[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(parts, p->ewald_out, sizeof(parts), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  out[0] = parts[0] + parts[1];
+  out[1] = parts[0];
+  out[2] = parts[1];
+  return NFFT_OK;
+}
+
+int nfft_ewald_reciprocal_sum(nfft_plan* p, const void* S_dev, double L, double alpha, double* sum_dev) {
+  if (!p || !S_dev || !sum_dev || !(L > 0.0) || !(alpha > 0.0) || !std::isfinite(L) || !std::isfinite(alpha))
+    return NFFT_ERR_INVALID_ARG;
+  const EwaldGeom g = ewald_geom(p, L, alpha);
+  const double scale = 1.0 / (2.0 * M_PI * L);
+  if (p->precision == NFFT_FP64)
+    CK(launch_ewald_sum<double>(static_cast<const double2*>(S_dev), false, g, p->ewald_partials, scale, 0.0, sum_dev,
+                                p->stream));
+  else
+    CK(launch_ewald_sum<float>(static_cast<const float2*>(S_dev), false, g, p->ewald_partials, scale, 0.0, sum_dev,
+                               p->stream));
+  return NFFT_OK;
 }
 
 int nfft_sync(nfft_plan* p) {

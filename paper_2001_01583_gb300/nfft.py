@@ -110,6 +110,25 @@ class Plan:
                 out = out.to("cpu")
         return out[0] if single else out
 
+    def ewald_reciprocal(self, q, L, alpha):
+        """Eq. 12 for charges q (M values) at the points set (x = r / L).
+        Returns (U^K, n-sum term, self term) as floats."""
+        qd, _ = self._to_device(q.reshape(self.M), self.cdtype)
+        out = (ctypes.c_double * 3)()
+        _lib.check(self._lib.nfft_ewald_reciprocal(self._h, ctypes.c_void_p(qd.data_ptr()), float(L), float(alpha),
+                                                   out), "nfft_ewald_reciprocal")
+        return out[0], out[1], out[2]
+
+    def ewald_reciprocal_sum(self, S, L, alpha, out=None):
+        """The n-sum term of Eq. 12 from a structure factor S on I_N; returns
+        a 1-element float64 CUDA tensor (asynchronous)."""
+        Sd, _ = self._to_device(S.reshape(self.N), self.cdtype)
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=self.device)
+        _lib.check(self._lib.nfft_ewald_reciprocal_sum(self._h, ctypes.c_void_p(Sd.data_ptr()), float(L), float(alpha),
+                                                       ctypes.c_void_p(out.data_ptr())), "nfft_ewald_reciprocal_sum")
+        return out
+
     def sync(self):
         """Wait for the plan's stream; raises NFFTError for a device-side error."""
         _lib.check(self._lib.nfft_sync(self._h), "nfft_sync")
