@@ -169,6 +169,29 @@ int nfft_ewald_reciprocal(nfft_plan* plan, const void* q_dev, double L, double a
  * (fixed tiles of 8192 elements, fixed summation tree). */
 int nfft_ewald_reciprocal_sum(nfft_plan* plan, const void* S_dev, double L, double alpha, double* sum_dev);
 
+/* Largest |I_N| nfft_ewald_reciprocal_sum_noalloc accepts (4096 tiles of 8192). */
+#define NFFT_NOALLOC_MAX_MODES 33554432
+
+/* The same n-sum as nfft_ewald_reciprocal_sum, for callers that cannot
+ * allocate device memory when they need it: code inside a framework whose
+ * caching allocator owns the GPU memory (a direct cudaMalloc there can fail
+ * or synchronise the device), steady-state loops that forbid allocation, or
+ * callers with no plan.  The paper has no counterpart; it is a library
+ * convenience.  No plan is needed and nothing is allocated: the caller passes
+ * S_dev (|I_N| complex of `precision`'s type, layout of fhat, with I_N given
+ * by d and N) and sum_dev (one device double, written asynchronously on
+ * cuda_stream, NULL = legacy default stream).  Scratch is a static 32 KiB
+ * device array of the library, held on every GPU that loads it until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current); make that first
+ * call outside any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (different streams, different host threads) race
+ * and must be serialised by the caller.  Returns NFFT_ERR_UNSUPPORTED without
+ * touching the GPU when |I_N| > NFFT_NOALLOC_MAX_MODES, NFFT_ERR_INVALID_ARG
+ * for bad arguments, NFFT_ERR_CUDA if the launch fails. */
+int nfft_ewald_reciprocal_sum_noalloc(int d, const int64_t* N, int precision, const void* S_dev, double L,
+                                      double alpha, double* sum_dev, void* cuda_stream);
+
 /* Wait for the plan's stream, then report (and clear) the device error flag. */
 int nfft_sync(nfft_plan* plan);
 

@@ -84,6 +84,8 @@ def _declare(lib):
         "nfft_ewald_reciprocal": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(ctypes.c_double)]),
         "nfft_ewald_reciprocal_sum": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, vp]),
+        "nfft_ewald_reciprocal_sum_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_double,
+                                                              ctypes.c_double, vp, vp]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }
