@@ -11,7 +11,7 @@ step processes 2 sets x 2 transforms x M points.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload config|small] [--no-cpu-baseline]
 
-"--workload small" (N = 32^3, M = 2.5e5, uniform only) is the case profiled
+"--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  Prints one JSON line (rank 0).  Under torchrun
 every rank runs its own independent copy of the workload (weak scaling, no
 collective on the data path); the value is all ranks' points over the slowest
@@ -38,9 +38,9 @@ WORKLOADS = {
     "config": dict(N=(64, 64, 64), M=10 ** 6, sets=("uniform", "clustered"),
                    name="3-D adjoint+forward NFFT, N=64^3, M=10^6, uniform + clustered (32 clusters, std 0.02), "
                         "Kaiser-Bessel m=4, sigma=2, mixed FP32"),
-    "small": dict(N=(32, 32, 32), M=250000, sets=("uniform",),
-                  name="3-D adjoint+forward NFFT, N=32^3, M=2.5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
-                       "(profiling case)"),
+    "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",),
+                  name="3-D adjoint+forward NFFT, N=64^3, M=5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
+                       "(profiling case: the same grid and bins, half the points, one set)"),
 }
 
 # bytes of the shared-memory traffic per cell visit: spread reads and writes

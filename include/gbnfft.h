@@ -72,10 +72,13 @@ typedef enum {
 
 /* Spreading / interpolation kernels. */
 typedef enum {
-  NFFT_METHOD_AUTO = 0,   /* tiled if the tile fits in shared memory, else global */
+  NFFT_METHOD_AUTO = 0,   /* warp if available, else tiled if the tile fits, else global */
   NFFT_METHOD_TILED = 1,  /* bin-sorted points, per-subproblem shared-memory tile */
-  NFFT_METHOD_GLOBAL = 2  /* one thread per point, atomics straight into the grid
+  NFFT_METHOD_GLOBAL = 2, /* one thread per point, atomics straight into the grid
                              (the paper's spread kernel, Section 3) */
+  NFFT_METHOD_WARP = 3    /* d = 2, 3 and up to 16 taps: one warp per point, lanes
+                             on distinct cells; spreading into warp-private
+                             shared-memory tiles without atomics */
 } nfft_method;
 
 /* Options for nfft_set_option. */

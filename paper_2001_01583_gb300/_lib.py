@@ -30,7 +30,7 @@ FP64 = 0
 FP32_MIXED = 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
 
-METHOD_AUTO, METHOD_TILED, METHOD_GLOBAL = 0, 1, 2
+METHOD_AUTO, METHOD_TILED, METHOD_GLOBAL, METHOD_WARP = 0, 1, 2, 3
 OPT_METHOD, OPT_BIN_0, OPT_BIN_1, OPT_BIN_2, OPT_MAX_SUBPROBLEM, OPT_RHS_CAPACITY, OPT_PROFILE, OPT_THREADS = range(8)
 STAGES = ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp")
 

@@ -58,6 +58,23 @@ int tiled_blocks_per_sm(int d, int taps, bool spread, int threads, size_t smem);
 template <typename Real>
 cudaError_t tiled_set_smem_limit(int d, int taps, bool spread, size_t smem);
 
+// Warp-per-point kernels (points_wpp.cuh, d = 2, 3, taps <= 16): the block
+// layout the host chooses.
+struct WppLayout {
+  int pitch;        // row pitch of a tile, in complex elements
+  int warp_cells;   // elements of one private tile (rows * pitch), spread only
+  int warps;        // warps per block
+};
+const void* wpp_kernel_f32(int d, int taps, bool spread);
+const void* wpp_kernel_f64(int d, int taps, bool spread);
+// 3-D shared-tile kernels (points_planes.cuh): plane-owner spreading and
+// point-group interpolation, taps <= 16, same WppLayout (warps divides taps
+// for spreading).
+const void* planes_kernel_f32(int taps, int warps, bool spread);
+const void* planes_kernel_f64(int taps, int warps, bool spread);
+size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile);
+
 // ---- scaling (deconv.cu) --------------------------------------------------
 // Adjoint step 3: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
 template <typename Real>

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <climits>
 #include <map>
 #include <new>
 #include <vector>
@@ -46,6 +47,9 @@ struct nfft_plan {
   int device = 0;
   int num_sms = 1;
   size_t smem_optin = 48 * 1024;
+  size_t smem_per_sm = 100 * 1024;
+  int wpp_pitch = 0;   // row pitch of the warp-per-point tiles
+  std::map<std::pair<const void*, std::pair<int, size_t>>, int> occupancy;  // (kernel, threads, smem) -> blocks/SM
 
   // options
   int method_opt = NFFT_METHOD_AUTO;
@@ -55,6 +59,7 @@ struct nfft_plan {
   int max_sub_opt = 0;
   int rhs_cap = 1;
   int threads = 256;
+  int threads_opt = 0;   // explicit threads per block for the 3-D warp kernels (0 = chosen per launch)
   bool profile = false;
 
   // device memory
@@ -213,14 +218,49 @@ size_t tile_bytes(const nfft_plan* p, const int* bin) {
   return cells * p->csize;
 }
 
+// Row pitch for the warp-per-point tiles: a warp instruction touches Q rows
+// of W consecutive elements; the pitch (>= the row length `last`) that needs
+// the fewest shared-memory wavefronts -- the largest number of 4-byte words
+// one bank must serve, averaged over the row's start -- wins, the smallest on
+// ties.
+int choose_pitch(int last, int W, int csize) {
+  const int Q = 32 / W > 0 ? 32 / W : 1;
+  const int words = csize / 4;
+  int best = last, best_cost = INT_MAX;
+  for (int pitch = last; pitch < last + 32; ++pitch) {
+    int cost = 0;
+    for (int x0 = 0; x0 < 32; ++x0) {
+      int bank[32] = {0};
+      for (int q = 0; q < Q; ++q)
+        for (int ix = 0; ix < W; ++ix)
+          for (int w = 0; w < words; ++w) ++bank[((q * pitch + x0 + ix) * words + w) % 32];
+      int mx = 0;
+      for (int b = 0; b < 32; ++b) mx = bank[b] > mx ? bank[b] : mx;
+      cost += mx;
+    }
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = pitch;
+    }
+  }
+  return best;
+}
+
+size_t wpp_tile_bytes(const nfft_plan* p, const int* bin, int pitch) {
+  size_t rows = 1;
+  for (int t = 0; t + 1 < p->d; ++t) rows *= (size_t)(bin[t] + p->win.taps - 1);
+  return rows * (size_t)pitch * p->csize;
+}
+
 // Choose bins and the method.  Default bins: 1-D 1024, 2-D 32 x 32,
-// 3-D 8 x 8 x 8 (clamped to the grid), halved while the tile exceeds the
-// per-block shared-memory budget; the global method if nothing fits.
+// 3-D 8 x 8 x 16 (the fastest dimension longest: fewer tile rows to flush),
+// clamped to the grid and halved while the tile exceeds the per-block
+// shared-memory budget; the global method if nothing fits.
 int configure_bins(nfft_plan* p) {
-  const int defaults[3] = {1024, 32, 8};
+  const int defaults[3][3] = {{1024, 1, 1}, {32, 32, 1}, {8, 8, 16}};
   int bin[3] = {1, 1, 1};
   for (int t = 0; t < p->d; ++t) {
-    int b = p->bin_opt[t] > 0 ? p->bin_opt[t] : defaults[p->d - 1];
+    int b = p->bin_opt[t] > 0 ? p->bin_opt[t] : defaults[p->d - 1][t];
     if (b > p->n[t]) b = (int)p->n[t];
     const int maxb = p->d == 1 ? (1 << 30) : (1 << local_bits(p->d)) - 1;
     if (b > maxb) b = maxb;
@@ -237,9 +277,17 @@ int configure_bins(nfft_plan* p) {
   }
   bool tiled_ok = tile_bytes(p, bin) <= budget;
   const bool have_kernel = (p->win.taps <= (p->d == 3 ? 26 : 32));
+  const int last = bin[p->d - 1] + p->win.taps - 1;
+  p->wpp_pitch = choose_pitch(last, p->win.taps, (int)p->csize);
+  // the warp-per-point form needs at least two private tiles per block
+  const size_t wtile = wpp_tile_bytes(p, bin, p->wpp_pitch);
+  const bool warp_ok = p->d >= 2 && p->win.taps <= 16 &&
+                       (p->d == 3 ? wtile + 32768 <= budget : 2 * wtile + 4096 <= budget);
   int method = p->method_opt;
-  if (method == NFFT_METHOD_AUTO) method = (tiled_ok && have_kernel) ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL;
+  if (method == NFFT_METHOD_AUTO)
+    method = warp_ok ? NFFT_METHOD_WARP : ((tiled_ok && have_kernel) ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
   if (method == NFFT_METHOD_TILED && (!tiled_ok || !have_kernel)) return NFFT_ERR_UNSUPPORTED;
+  if (method == NFFT_METHOD_WARP && !warp_ok) return NFFT_ERR_UNSUPPORTED;
   p->method = method;
   GridGeom& g = p->geom;
   g.d = p->d;
@@ -385,7 +433,134 @@ PointKernelArgs<Real> point_args(nfft_plan* p) {
 }
 
 template <typename Real>
+const void* wpp_kernel(int d, int taps, bool spread);
+template <>
+const void* wpp_kernel<float>(int d, int taps, bool spread) { return wpp_kernel_f32(d, taps, spread); }
+template <>
+const void* wpp_kernel<double>(int d, int taps, bool spread) { return wpp_kernel_f64(d, taps, spread); }
+
+int blocks_per_sm(nfft_plan* p, const void* fn, int threads, size_t smem) {
+  const auto key = std::make_pair(fn, std::make_pair(threads, smem));
+  auto it = p->occupancy.find(key);
+  if (it != p->occupancy.end()) return it->second;
+  int nb = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess)
+    nb = 0;
+  p->occupancy[key] = nb;
+  return nb;
+}
+
+template <typename Real>
+const void* planes_kernel(int taps, int warps, bool spread);
+template <>
+const void* planes_kernel<float>(int taps, int warps, bool spread) { return planes_kernel_f32(taps, warps, spread); }
+template <>
+const void* planes_kernel<double>(int taps, int warps, bool spread) { return planes_kernel_f64(taps, warps, spread); }
+template <typename Real>
+size_t planes_table_bytes(int taps, int bp, int np, int nw, const int* tile);
+template <>
+size_t planes_table_bytes<float>(int taps, int bp, int np, int nw, const int* tile) {
+  return planes_table_bytes_f32(taps, bp, np, nw, tile);
+}
+template <>
+size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* tile) {
+  return planes_table_bytes_f64(taps, bp, np, nw, tile);
+}
+
+// 3-D: one shared tile per block.  Spreading splits the tile's planes among
+// the block's warps (a power of two dividing the taps); interpolation gives
+// each warp groups of points.  Warps per block: the option if set, else the
+// most resident warps (ties: fewer warps per block, which share the per-point
+// work among fewer warps).  Right-hand sides per pass fit two blocks per SM.
+template <typename Real>
+int run_planes(nfft_plan* p, PointKernelArgs<Real>& a, bool spread) {
+  const int W = p->win.taps;
+  const size_t rows = (size_t)p->geom.tile[0] * p->geom.tile[1];
+  const size_t tbytes = rows * (size_t)p->wpp_pitch * p->csize;
+  auto smem_of = [&](int nw, int np) {
+    return (size_t)np * tbytes + planes_table_bytes<Real>(W, 32 * nw, np, nw, p->geom.tile);
+  };
+  int np = 1;
+  while (np < a.nrhs && smem_of(8, np + 1) <= p->smem_per_sm / 2) ++np;
+  int best_nw = 0, best_warps = 0;
+  size_t best_smem = 0;
+  const void* best_fn = nullptr;
+  for (int nw = 1; nw <= 8; nw *= 2) {
+    if (p->threads_opt > 0 && 32 * nw != p->threads_opt) continue;
+    const void* fn = planes_kernel<Real>(W, nw, spread);
+    if (!fn) continue;
+    const size_t smem = smem_of(nw, np);
+    if (smem > p->smem_optin) continue;
+    const int per_sm = blocks_per_sm(p, fn, 32 * nw, smem);
+    if (per_sm * nw > best_warps) {
+      best_warps = per_sm * nw;
+      best_nw = nw;
+      best_smem = smem;
+      best_fn = fn;
+    }
+  }
+  if (!best_fn || best_warps == 0) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = np;
+  WppLayout lay{p->wpp_pitch, (int)(rows * p->wpp_pitch), best_nw};
+  int64_t blocks = (int64_t)(best_warps / best_nw) * p->num_sms;
+  if (blocks > p->max_subs) blocks = p->max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a, &lay};
+  CK(cudaFuncSetAttribute(best_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
+  CK(cudaLaunchKernel(best_fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, p->stream));
+  return NFFT_OK;
+}
+
+// Warp per point: private tiles for spreading, one shared tile for
+// interpolation.  Right-hand sides per pass and warps per block are chosen
+// for the most resident warps within the shared-memory budget.
+template <typename Real>
+int run_wpp(nfft_plan* p, PointKernelArgs<Real>& a, bool spread) {
+  const int D = p->d, W = p->win.taps;
+  const void* fn = wpp_kernel<Real>(D, W, spread);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  const int last = p->geom.tile[D - 1];
+  const int rows = p->geom.tile_cells / last;
+  const size_t elems = (size_t)rows * p->wpp_pitch;
+  const size_t tbytes = elems * p->csize;
+  const size_t scratch = (size_t)(32 * D * W + (D == 3 ? W * W : W)) * sizeof(Real);  // weight table + row weights
+  const size_t sm = p->smem_per_sm;
+  int np = 1;
+  if (spread) {
+    while (np < a.nrhs && 4 * (size_t)(np + 1) * tbytes + 4 * scratch <= sm) ++np;
+  } else {
+    while (np < a.nrhs && (size_t)(np + 1) * tbytes + 8 * scratch <= sm / 2) ++np;
+  }
+  int best_nw = 0, best_warps = 0;
+  size_t best_smem = 0;
+  for (int nw = 1; nw <= 8; ++nw) {
+    // spread: per warp its tiles, weight table and the batch's values ([np][32] complex)
+    const size_t smem = spread ? (size_t)nw * ((size_t)np * tbytes + scratch + (size_t)np * 32 * p->csize)
+                               : (size_t)np * tbytes + nw * scratch;
+    if (smem > p->smem_optin) break;
+    const int per_sm = blocks_per_sm(p, fn, 32 * nw, smem);
+    if (per_sm * nw > best_warps) {
+      best_warps = per_sm * nw;
+      best_nw = nw;
+      best_smem = smem;
+    }
+  }
+  if (best_nw == 0) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = np;
+  WppLayout lay{p->wpp_pitch, (int)elems, best_nw};
+  int64_t blocks = (int64_t)(best_warps / best_nw) * p->num_sms;
+  if (blocks > p->max_subs) blocks = p->max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a, &lay};
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, p->stream));
+  return NFFT_OK;
+}
+
+template <typename Real>
 int run_points(nfft_plan* p, PointKernelArgs<Real>& a, bool spread) {
+  if (p->method == NFFT_METHOD_WARP) return p->d == 3 ? run_planes<Real>(p, a, spread) : run_wpp<Real>(p, a, spread);
   const int threads = p->threads;
   if (p->method == NFFT_METHOD_TILED) {
     const size_t one = (size_t)p->geom.tile_cells * p->csize;
@@ -635,6 +810,10 @@ int nfft_plan_create(nfft_plan** out, int d, const int64_t* N, int64_t M, double
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess)
     return fail(NFFT_ERR_CUDA);
   p->smem_optin = (size_t)optin;
+  int per_sm = 0;
+  if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device) != cudaSuccess)
+    return fail(NFFT_ERR_CUDA);
+  p->smem_per_sm = (size_t)per_sm;
 
   p->win.kind = window;
   p->win.m = m;
@@ -774,7 +953,7 @@ int nfft_set_option(nfft_plan* p, int option, int64_t value) {
   if (!p) return NFFT_ERR_INVALID_ARG;
   switch (option) {
     case NFFT_OPT_METHOD:
-      if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_GLOBAL) return NFFT_ERR_INVALID_ARG;
+      if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_WARP) return NFFT_ERR_INVALID_ARG;
       p->method_opt = (int)value;
       break;
     case NFFT_OPT_BIN_0:
@@ -803,6 +982,7 @@ int nfft_set_option(nfft_plan* p, int option, int64_t value) {
     case NFFT_OPT_THREADS:
       if (value != 0 && (value < 32 || value > 256 || value % 32 != 0)) return NFFT_ERR_INVALID_ARG;
       p->threads = value == 0 ? 256 : (int)value;
+      p->threads_opt = (int)value;
       return NFFT_OK;
     default:
       return NFFT_ERR_INVALID_ARG;

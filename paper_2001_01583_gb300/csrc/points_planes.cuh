@@ -1,0 +1,322 @@
+// 3-D spreading and interpolation with one shared tile per block.
+//
+// A block takes a subproblem (a run of bin-sorted points of one bin) and
+// stages its points in batches of blockDim.x: thread t loads point t's
+// record and value, evaluates its 3*W window weights into a shared table and
+// stores the point's tile offset, so the per-point work of every warp is
+// table lookups.  The wrapped grid index of every tile row and column is
+// tabulated once per subproblem for the tile load / flush.
+//
+// spread ("plane owner"): warp w of NW (a power of two dividing W) owns the
+//   tile planes z = w (mod NW), so for every point each warp updates exactly
+//   W/NW of the point's W planes, and no two warps ever write the same cell:
+//   plain shared-memory loads and stores, no atomics, one tile per block.
+//   Inside a plane, lane (ix, q) = (lane % W, lane / W) takes cell ix of rows
+//   q, q + Q, ... (Q = 32 / W).  After the subproblem the tile is added to
+//   the grid once (vector atomics: halos of neighbouring bins overlap).
+// interp ("point groups"): a warp works on 32/W points at once, W lanes per
+//   point; lane ix of a group sums column ix of its point's W x W rows from
+//   the read-only tile with the weights held in registers, then the group
+//   adds its W partial sums.
+#pragma once
+
+#include "points_tiled.cuh"
+
+namespace gbnfft {
+
+template <int W>
+struct PlaneShape {
+  static constexpr int Q = (32 / W) > 0 ? (32 / W) : 1;   // rows of a plane per pass
+  static constexpr int PASSES = (W + Q - 1) / Q;           // passes over a plane
+  static constexpr bool FULL = (Q * PASSES == W) && (32 % W == 0);  // every lane busy on every pass
+  static constexpr int PPW = (32 / W) > 0 ? (32 / W) : 1;  // interp: points per warp
+  static constexpr bool POW2 = (W & (W - 1)) == 0;
+};
+
+// Shared layout after the tiles (bp points per batch, np right-hand sides):
+//   wt[bp][3W] Real | vt[np][bp] complex | pt[bp] int2 (tile offset, plane) |
+//   jt[bp] int | gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
+template <int W, typename Real>
+__host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile) {
+  return (size_t)bp * (3 * W) * sizeof(Real) + (size_t)np * bp * 2 * sizeof(Real) + (size_t)bp * sizeof(int2) +
+         (size_t)bp * sizeof(int) + (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) +
+         (size_t)nw * 64 * sizeof(Real);
+}
+
+template <int W, typename Real>
+struct PlaneSmem {
+  typename Cplx<Real>::type* tile;   // [np][rows][pitch]
+  Real* wt;
+  typename Cplx<Real>::type* vt;
+  int2* pt;
+  int* jt;
+  int64_t* gz;
+  int64_t* gy;
+  int64_t* gx;
+  Real* red;
+};
+
+template <int W, typename Real>
+__device__ __forceinline__ PlaneSmem<W, Real> plane_smem(unsigned char* raw, int np_max, int tile_elems, int bp,
+                                                         const GridGeom& g) {
+  using C = typename Cplx<Real>::type;
+  PlaneSmem<W, Real> s;
+  s.tile = reinterpret_cast<C*>(raw);
+  s.wt = reinterpret_cast<Real*>(s.tile + (size_t)np_max * tile_elems);
+  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * 3 * W);
+  s.pt = reinterpret_cast<int2*>(s.vt + (size_t)np_max * bp);
+  s.jt = reinterpret_cast<int*>(s.pt + bp);
+  s.gz = reinterpret_cast<int64_t*>(s.jt + bp + (bp & 1));   // keep 8-byte alignment
+  s.gy = s.gz + g.tile[0];
+  s.gx = s.gy + g.tile[1];
+  s.red = reinterpret_cast<Real*>(s.gx + g.tile[2]);
+  return s;
+}
+
+// Wrapped grid offsets of the tile's planes, rows and columns.
+template <int W, typename Real>
+__device__ __forceinline__ void plane_index_tables(const PlaneSmem<W, Real>& s, const GridGeom& g,
+                                                   const int* origin) {
+  for (int i = threadIdx.x; i < g.tile[0] + g.tile[1] + g.tile[2]; i += blockDim.x) {
+    if (i < g.tile[0]) {
+      s.gz[i] = (int64_t)wrap_mod(origin[0] + i, g.n[0]) * g.n[1] * g.n[2];
+    } else if (i < g.tile[0] + g.tile[1]) {
+      const int y = i - g.tile[0];
+      s.gy[y] = (int64_t)wrap_mod(origin[1] + y, g.n[1]) * g.n[2];
+    } else {
+      const int x = i - g.tile[0] - g.tile[1];
+      s.gx[x] = wrap_mod(origin[2] + x, g.n[2]);
+    }
+  }
+}
+
+// Stage a batch: thread t handles point first + t.
+template <int W, typename Real>
+__device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a, const PlaneSmem<W, Real>& s,
+                                                  int first, int nb, int r0, int np, int bp, int T1, int pitch,
+                                                  bool want_values) {
+  const int t = threadIdx.x;
+  if (t < nb) {
+    const int idx = first + t;
+    const int j = a.pts.perm[idx];
+    const uint32_t loc = a.pts.local[idx];
+    const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
+    s.pt[t] = make_int2((l0 * T1 + l1) * pitch + l2, l0);
+    s.jt[t] = j;
+    Real* w = s.wt + t * (3 * W);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const Real base = a.pts.delta[d][idx] + (Real)(a.win.m - a.win.shift);
+#pragma unroll
+      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(a.win, d, base - (Real)i);
+    }
+    if (want_values)
+      for (int r = 0; r < np; ++r) s.vt[r * bp + t] = a.f_in[(int64_t)(r0 + r) * a.M + j];
+  }
+}
+
+template <int W, int NW, typename Real>
+__global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real> a, WppLayout lay) {
+  using C = typename Cplx<Real>::type;
+  using S = PlaneShape<W>;
+  static_assert(W % NW == 0 && (NW & (NW - 1)) == 0, "warps must be a power of two dividing the taps");
+  constexpr int TAPS = W / NW;   // planes of every point this warp updates
+  constexpr int BP = 32 * NW;    // points per batch
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const GridGeom& g = a.geom;
+  const int np_max = a.rhs_per_pass;
+  const int T1 = g.tile[1], T2 = g.tile[2];
+  const int rows = g.tile[0] * T1;
+  const int pitch = lay.pitch;
+  const int tile_elems = rows * pitch;
+  const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, g);
+  const int ix = lane % W, q = lane / W;
+  const bool active = S::FULL || q < S::Q;
+  const int nsub = *a.pts.num_subs;
+  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+    const SubProblem sub = a.pts.subs[sp];
+    int bc[kMaxDim], origin[kMaxDim];
+    bin_coords(sub.bin, g, bc);
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
+    plane_index_tables<W, Real>(s, g, origin);
+    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+      for (int e = threadIdx.x; e < np * tile_elems; e += BP) s.tile[e] = cmake<C>(0.0, 0.0);
+      for (int pb = 0; pb < sub.count; pb += BP) {
+        const int nb = min(BP, sub.count - pb);
+        __syncthreads();   // tile zeroed / previous batch no longer read
+        plane_stage_batch<W, Real>(a, s, sub.start + pb, nb, r0, np, BP, T1, pitch, true);
+        __syncthreads();
+        for (int pp = 0; pp < nb; ++pp) {
+          const int2 rec = s.pt[pp];                // (tile offset of the point's first tap, its plane)
+          const Real* w = s.wt + pp * (3 * W);
+          const Real wx = w[2 * W + ix];
+          Real wy[S::PASSES];
+#pragma unroll
+          for (int k = 0; k < S::PASSES; ++k) {
+            const int iy = k * S::Q + q;
+            wy[k] = (active && iy < W) ? w[W + iy] : (Real)0;
+          }
+          const int i0 = (warp - rec.y) & (NW - 1);   // first tap whose plane this warp owns
+          const int lanebase = rec.x + ix + q * pitch;
+          for (int r = 0; r < np; ++r) {
+            const C v = s.vt[r * BP + pp];
+            C* tr = s.tile + r * tile_elems + lanebase;
+#pragma unroll
+            for (int u = 0; u < TAPS; ++u) {
+              const int i = i0 + u * NW;
+              const Real wzx = w[i] * wx;
+              const Real vr = v.x * wzx, vi = v.y * wzx;
+              C* plane = tr + i * T1 * pitch;
+              C cell[S::PASSES];
+#pragma unroll
+              for (int k = 0; k < S::PASSES; ++k)
+                if (active && k * S::Q + q < W) cell[k] = plane[k * S::Q * pitch];
+#pragma unroll
+              for (int k = 0; k < S::PASSES; ++k) {
+                if (active && k * S::Q + q < W) {
+                  cell[k].x += vr * wy[k];
+                  cell[k].y += vi * wy[k];
+                  plane[k * S::Q * pitch] = cell[k];
+                }
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // flush the tile into the grid once: a warp per row, lanes along the row
+      for (int e = warp; e < np * rows; e += NW) {
+        const int r = e / rows;
+        const int row = e - r * rows;
+        const int z = row / T1, y = row - z * T1;
+        const int64_t gb = (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
+        const C* src = s.tile + r * tile_elems + row * pitch;
+        for (int x = lane; x < T2; x += 32) {
+          const C c = src[x];
+          if (c.x != (Real)0 || c.y != (Real)0) grid_add(a.grid + gb + s.gx[x], c);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int W, typename Real>
+__global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
+  using C = typename Cplx<Real>::type;
+  using S = PlaneShape<W>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = lay.warps;
+  const int bp = blockDim.x;
+  const GridGeom& g = a.geom;
+  const int np_max = a.rhs_per_pass;
+  const int T1 = g.tile[1], T2 = g.tile[2];
+  const int rows = g.tile[0] * T1;
+  const int pitch = lay.pitch;
+  const int tile_elems = rows * pitch;
+  const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, g);
+  const int grp = lane / W, ix = lane % W;
+  const bool active = grp < S::PPW;
+  const int plane_stride = T1 * pitch;
+  const int nsub = *a.pts.num_subs;
+  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+    const SubProblem sub = a.pts.subs[sp];
+    int bc[kMaxDim], origin[kMaxDim];
+    bin_coords(sub.bin, g, bc);
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
+    __syncthreads();   // the previous subproblem's readers are done
+    plane_index_tables<W, Real>(s, g, origin);
+    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+      __syncthreads();
+      // load the tile: a warp per row, lanes along the row
+      for (int e = warp; e < np * rows; e += nw) {
+        const int r = e / rows;
+        const int row = e - r * rows;
+        const int z = row / T1, y = row - z * T1;
+        const int64_t gb = (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
+        C* dst = s.tile + r * tile_elems + row * pitch;
+        for (int x = lane; x < T2; x += 32) dst[x] = a.grid_in[gb + s.gx[x]];
+      }
+      for (int pb = 0; pb < sub.count; pb += bp) {
+        const int nb = min(bp, sub.count - pb);
+        __syncthreads();
+        plane_stage_batch<W, Real>(a, s, sub.start + pb, nb, r0, np, bp, T1, pitch, false);
+        __syncthreads();
+        for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
+          const int pp = p0 + grp;
+          const bool mine = active && pp < nb;
+          Real wz[W], wy[W];
+          Real wx = 0;
+          int base = 0;
+          if (mine) {
+            const Real* w = s.wt + pp * (3 * W);
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+              wz[i] = w[i];
+              wy[i] = w[W + i];
+            }
+            wx = w[2 * W + ix];
+            base = s.pt[pp].x + ix;
+          }
+          for (int r = 0; r < np; ++r) {
+            Real ar = 0, ai = 0;
+            if (mine) {
+              const C* tr = s.tile + r * tile_elems + base;
+#pragma unroll
+              for (int iz = 0; iz < W; ++iz) {
+                Real pr = 0, pi = 0;
+                const C* pl = tr + iz * plane_stride;
+#pragma unroll
+                for (int iy = 0; iy < W; ++iy) {
+                  const C c = pl[iy * pitch];
+                  pr += c.x * wy[iy];
+                  pi += c.y * wy[iy];
+                }
+                ar += pr * wz[iz];
+                ai += pi * wz[iz];
+              }
+              ar *= wx;
+              ai *= wx;
+            }
+            if (S::POW2) {
+#pragma unroll
+              for (int o = W / 2; o > 0; o >>= 1) {
+                ar += __shfl_xor_sync(0xffffffffu, ar, o);
+                ai += __shfl_xor_sync(0xffffffffu, ai, o);
+              }
+            } else {
+              Real* rw = s.red + warp * 64;
+              rw[lane] = ar;
+              rw[32 + lane] = ai;
+              __syncwarp();
+              if (mine && ix == 0) {
+                ar = 0;
+                ai = 0;
+                for (int k = 0; k < W; ++k) {
+                  ar += rw[grp * W + k];
+                  ai += rw[32 + grp * W + k];
+                }
+              }
+              __syncwarp();
+            }
+            if (mine && ix == 0) a.f_out[(int64_t)(r0 + r) * a.M + s.jt[pp]] = cmake<C>(ar, ai);
+          }
+        }
+      }
+    }
+  }
+}
+
+// (taps, warps) pairs instantiated for spreading: warps a power of two dividing the taps.
+#define GBNFFT_PLANE_SPREAD_CASES(X, R)                                                                    \
+  X(2, 1, R) X(2, 2, R) X(4, 1, R) X(4, 2, R) X(4, 4, R) X(6, 1, R) X(6, 2, R) X(8, 1, R) X(8, 2, R)      \
+      X(8, 4, R) X(8, 8, R) X(10, 1, R) X(10, 2, R) X(12, 1, R) X(12, 2, R) X(12, 4, R) X(14, 1, R)       \
+          X(14, 2, R) X(16, 1, R) X(16, 2, R) X(16, 4, R) X(16, 8, R)
+#define GBNFFT_PLANE_TAPS(X, R) X(2, R) X(4, R) X(6, R) X(8, R) X(10, R) X(12, R) X(14, R) X(16, R)
+
+}  // namespace gbnfft

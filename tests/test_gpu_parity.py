@@ -99,12 +99,14 @@ CASES = [
 
 @pytest.mark.parametrize("d,N,M,window,m", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("method", ["tiled", "global"])
+@pytest.mark.parametrize("method", ["tiled", "global", "warp"])
 def test_against_oracles(d, N, M, window, m, precision, method):
+    if method == "warp" and d == 1:
+        pytest.skip("the warp-per-point kernels cover d = 2, 3")
     x = inputs.uniform_points(M, d, seed=5 + d)
     f = inputs.complex_normal(M, seed=6)
     fh = inputs.complex_normal(N, seed=7)
-    meth = {"tiled": 1, "global": 2}[method]
+    meth = {"tiled": 1, "global": 2, "warp": 3}[method]
     a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, method=meth)
     assert info["method"] == meth
     sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
@@ -141,21 +143,22 @@ def test_clustered_points_split_into_subproblems():
     fh = inputs.complex_normal(N, seed=33)
     sa = S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL)
     sb = S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL)
-    for P in (64, 1024):
+    for P, method in ((64, 3), (1024, 3), (64, 1)):
         for precision, tol in (("fp32", FP32_ELEM), ("fp64", 1e-12)):
-            a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", precision, max_subproblem=P)
+            a, b, _ = _run(N, x, f, fh, 2.0, 4, "kaiser_bessel", precision, max_subproblem=P, method=method)
             _elementwise(a, sa, tol)
             _elementwise(b, sb, tol)
             assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 1e-6
             assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= 1e-6
 
 
-def test_multiple_right_hand_sides():
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_multiple_right_hand_sides(method):
     N, M, R = (16, 20, 12), 3000, 5
     x = inputs.uniform_points(M, 3, seed=41)
     F = inputs.complex_normal((R, M), seed=42)
     H = inputs.complex_normal((R,) + N, seed=43)
-    with _plan(N, M, 2.0, 4, "kaiser_bessel", "fp64", rhs_capacity=2) as p:
+    with _plan(N, M, 2.0, 4, "kaiser_bessel", "fp64", rhs_capacity=4, method=method) as p:
         p.set_points(torch.from_numpy(x).cuda())
         A = p.adjoint(torch.from_numpy(F).cuda()).cpu().numpy()
         B = p.forward(torch.from_numpy(H).cuda()).cpu().numpy()
