@@ -217,6 +217,59 @@ int nfft_stage_times(nfft_plan* plan, double* ms, int64_t* launches, int reset);
  * each of the d bandwidths and the number of window taps per dimension. */
 int nfft_plan_params(int d, const int64_t* N, double sigma, int m, int window, int64_t* n_out, int* taps_out);
 
+/* ---- batches ------------------------------------------------------------
+ * Many independent transforms of uneven sizes (and items with several
+ * right-hand sides sharing one point set), set up once and run together:
+ * one sort pass over all items' points, one persistent spreading /
+ * interpolation launch per group of items with the same d, taps and bin
+ * shape, one cuFFT plan-many per oversampled grid size and one scaling
+ * launch for all items, captured in a CUDA graph that each call replays.
+ * Items keep their own parameters (Section 2); the precision is common. */
+typedef struct nfft_batch nfft_batch;
+
+typedef struct {
+  int d;              /* 1, 2 or 3 */
+  int64_t N[3];       /* bandwidths (first d used), even */
+  int64_t M;          /* points */
+  double sigma;       /* oversampling >= 1 */
+  int m;              /* cut-off */
+  int window;         /* nfft_window */
+  int nrhs;           /* right-hand sides transformed per call (>= 1) */
+} nfft_batch_item;
+
+/* Create a batch of `count` items (allocates everything, including one grid
+ * per right-hand side of every item and the cuFFT plans). */
+int nfft_batch_create(nfft_batch** out, int count, const nfft_batch_item* items, int precision, void* cuda_stream);
+
+int nfft_batch_destroy(nfft_batch* batch);
+
+/* Set every item's points: x_dev is a host array of `count` device pointers
+ * (item i: M_i x d_i doubles, layout of nfft_set_points).  Sorts all points in
+ * one pass and waits for the stream (the pointer table is copied). */
+int nfft_batch_set_points(nfft_batch* batch, const double* const* x_dev);
+
+/* Eq. 5 for every item: f_dev and fhat_dev are host arrays of `count` device
+ * pointers (item i: nrhs_i x M_i and nrhs_i x |I_N_i| complex).  One CUDA
+ * graph launch: the pointer table upload, zeroing of the grids, one
+ * spreading launch per item group, the batched FFTs and one scaling launch.
+ * Asynchronous; the pointer arrays may be reused when the call returns. */
+int nfft_batch_adjoint(nfft_batch* batch, const void* const* f_dev, void* const* fhat_dev);
+
+/* Eq. 6 for every item (one graph launch: table upload, scaling + padding,
+ * batched inverse FFTs, interpolation). */
+int nfft_batch_forward(nfft_batch* batch, const void* const* fhat_dev, void* const* f_dev);
+
+int nfft_batch_sync(nfft_batch* batch);
+
+/* nfft_set_option for all items of the batch (NFFT_OPT_RHS_CAPACITY is not
+ * available: a batch fixes each item's right-hand sides).  Layout options
+ * require nfft_batch_set_points again. */
+int nfft_batch_set_option(nfft_batch* batch, int option, int64_t value);
+
+/* Stage times with NFFT_OPT_PROFILE on: a whole adjoint graph is booked as
+ * NFFT_STAGE_SPREAD, a whole forward graph as NFFT_STAGE_INTERP. */
+int nfft_batch_stage_times(nfft_batch* batch, double* ms, int64_t* launches, int reset);
+
 /* Human-readable name of a status code (static string). */
 const char* nfft_status_string(int status);
 

@@ -55,6 +55,18 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("N", ctypes.c_int64 * 3),
+        ("M", ctypes.c_int64),
+        ("sigma", ctypes.c_double),
+        ("m", ctypes.c_int),
+        ("window", ctypes.c_int),
+        ("nrhs", ctypes.c_int),
+    ]
+
+
 class NFFTError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -86,6 +98,15 @@ def _declare(lib):
         "nfft_ewald_reciprocal_sum": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, vp]),
         "nfft_ewald_reciprocal_sum_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_double,
                                                               ctypes.c_double, vp, vp]),
+        "nfft_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int,
+                                              vp]),
+        "nfft_batch_destroy": (ctypes.c_int, [vp]),
+        "nfft_batch_set_points": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
+        "nfft_batch_adjoint": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "nfft_batch_forward": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "nfft_batch_sync": (ctypes.c_int, [vp]),
+        "nfft_batch_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
+        "nfft_batch_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), i64p, ctypes.c_int]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }

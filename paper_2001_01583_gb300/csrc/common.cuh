@@ -80,22 +80,12 @@ __device__ __forceinline__ double window_psi<double>(const WindowDev& w, int t, 
   return e * m * s * w.kb_norm[t];
 }
 
-// One subproblem: a run of sorted points inside one bin.
+// One subproblem: a run of sorted points inside one bin of one item.
 struct SubProblem {
-  int bin;
-  int start;
+  int bin;     // bin id within the item
+  int start;   // first sorted position
   int count;
-  int pad_;
-};
-
-// Point data after sorting (all arrays indexed by sorted position).
-template <typename Real>
-struct SortedPoints {
-  const int* perm;           // sorted position -> original point index
-  const uint32_t* local;     // packed in-bin cell offsets
-  const Real* delta[kMaxDim];
-  const SubProblem* subs;
-  const int* num_subs;       // device scalar
+  int item;
 };
 
 struct GridGeom {
@@ -106,6 +96,37 @@ struct GridGeom {
   int tile[kMaxDim];         // bin + W - 1 (unused dims = 1)
   int64_t grid_cells;        // prod n
   int tile_cells;            // prod tile
+};
+
+// One transform of a batch (a single plan is a batch of one), as the
+// kernels see it.  Items of one kernel launch share d, the taps and the bin
+// edges (so the tile shape); n, M, the window shape and the pointers may
+// differ.
+struct ItemDev {
+  GridGeom geom;
+  WindowDev win;
+  int N[kMaxDim];
+  int64_t NN;                  // |I_N|
+  int64_t M;
+  int nrhs;
+  int bin_offset;              // first global bin id of the item
+  int64_t point_offset;        // first point of the item in the unsorted concatenation
+  const double* x;             // M x d points (read by nfft_set_points only)
+  void* grid;                  // nrhs grids of geom.grid_cells
+  const double* inv_c[kMaxDim];
+  const void* in;              // per call: f (adjoint) or fhat (forward), nrhs blocks
+  void* out;                   // per call: fhat (adjoint) or f (forward)
+};
+
+// Point data after sorting (all arrays indexed by sorted position).
+template <typename Real>
+struct SortedPoints {
+  const int* perm;           // sorted position -> point index within its item
+  const uint32_t* local;     // packed in-bin cell offsets
+  const Real* delta[kMaxDim];
+  const SubProblem* subs;
+  const int* sub_start;      // exclusive scan of subproblems per global bin
+  const int* num_subs;       // device scalar: all subproblems
 };
 
 // Pack / unpack of in-bin offsets: 32 bits split evenly over d dimensions.

@@ -1,4 +1,5 @@
-// Scaling kernels of Section 2.
+// Scaling kernels of Section 2, for every item of a batch in one launch
+// (blockIdx.y = item).
 //   adjoint step 3 ("scale", Algorithm 2): fhat(k) = ghat(k) / c_k(phi~), k in I_N,
 //     read from the oversampled spectrum at array index k mod n (crop);
 //   forward step 1 ("subdivide", Algorithm 5): ghat(k) = fhat(k) / c_k(phi~)
@@ -11,128 +12,107 @@ namespace gbnfft {
 
 namespace {
 
-struct ScaleGeom {
-  int d;
-  int N[kMaxDim];
-  int n[kMaxDim];
-  int64_t NN;      // |I_N|
-  int64_t cells;   // |I_n|
-  const double* inv_c[kMaxDim];
-};
-
 template <typename Real>
-__global__ void k_deconv_crop(const typename Cplx<Real>::type* __restrict__ grid,
-                              typename Cplx<Real>::type* __restrict__ fhat, ScaleGeom s, int R) {
+__global__ void k_deconv_crop(const ItemDev* __restrict__ items, void* out_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
+  const ItemDev& it = items[blockIdx.y];
+  const int nrhs = out_override ? nrhs_override : it.nrhs;
+  C* fhat = static_cast<C*>(out_override ? out_override : it.out);
+  const C* grid = static_cast<const C*>(it.grid);
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= s.NN * R) return;
-  const int r = (int)(e / s.NN);
-  int64_t rem = e - (int64_t)r * s.NN;
+  if (e >= it.NN * nrhs) return;
+  const int d = it.geom.d;
+  const int r = (int)(e / it.NN);
+  int64_t rem = e - (int64_t)r * it.NN;
   int a[kMaxDim];
-  for (int t = s.d - 1; t >= 0; --t) {
-    a[t] = (int)(rem % s.N[t]);
-    rem /= s.N[t];
+  for (int t = d - 1; t >= 0; --t) {
+    a[t] = (int)(rem % it.N[t]);
+    rem /= it.N[t];
   }
   int64_t flat = 0;
   double factor = 1.0;
-  for (int t = 0; t < s.d; ++t) {
-    const int k = a[t] - s.N[t] / 2;          // k_t in [-N_t/2, N_t/2)
-    flat = flat * s.n[t] + (k < 0 ? k + s.n[t] : k);
-    factor *= s.inv_c[t][a[t]];
+  for (int t = 0; t < d; ++t) {
+    const int k = a[t] - it.N[t] / 2;          // k_t in [-N_t/2, N_t/2)
+    flat = flat * it.geom.n[t] + (k < 0 ? k + it.geom.n[t] : k);
+    factor *= it.inv_c[t][a[t]];
   }
-  const C g = grid[(int64_t)r * s.cells + flat];
+  const C g = grid[(int64_t)r * it.geom.grid_cells + flat];
   const Real f = (Real)factor;
-  C out;
-  out.x = g.x * f;
-  out.y = g.y * f;
-  fhat[e] = out;
+  C o;
+  o.x = g.x * f;
+  o.y = g.y * f;
+  fhat[e] = o;
 }
 
 template <typename Real>
-__global__ void k_pad_deconv(const typename Cplx<Real>::type* __restrict__ fhat,
-                             typename Cplx<Real>::type* __restrict__ grid, ScaleGeom s, int R) {
+__global__ void k_pad_deconv(const ItemDev* __restrict__ items, const void* in_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
+  const ItemDev& it = items[blockIdx.y];
+  const int nrhs = in_override ? nrhs_override : it.nrhs;
+  const C* fhat = static_cast<const C*>(in_override ? in_override : it.in);
+  C* grid = static_cast<C*>(it.grid);
+  const int64_t cells = it.geom.grid_cells;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= s.cells * R) return;
-  const int r = (int)(e / s.cells);
-  int64_t rem = e - (int64_t)r * s.cells;
+  if (e >= cells * nrhs) return;
+  const int d = it.geom.d;
+  const int r = (int)(e / cells);
+  int64_t rem = e - (int64_t)r * cells;
   int l[kMaxDim];
-  for (int t = s.d - 1; t >= 0; --t) {
-    l[t] = (int)(rem % s.n[t]);
-    rem /= s.n[t];
+  for (int t = d - 1; t >= 0; --t) {
+    l[t] = (int)(rem % it.geom.n[t]);
+    rem /= it.geom.n[t];
   }
   bool inside = true;
   int64_t flat = 0;
   double factor = 1.0;
-  for (int t = 0; t < s.d; ++t) {
-    const int half = s.N[t] / 2;
+  for (int t = 0; t < d; ++t) {
+    const int half = it.N[t] / 2;
     int k;
     if (l[t] < half) k = l[t];
-    else if (l[t] >= s.n[t] - half) k = l[t] - s.n[t];
+    else if (l[t] >= it.geom.n[t] - half) k = l[t] - it.geom.n[t];
     else { inside = false; break; }
     const int a = k + half;
-    flat = flat * s.N[t] + a;
-    factor *= s.inv_c[t][a];
+    flat = flat * it.N[t] + a;
+    factor *= it.inv_c[t][a];
   }
-  C out;
+  C o;
   if (inside) {
-    const C h = fhat[(int64_t)r * s.NN + flat];
+    const C h = fhat[(int64_t)r * it.NN + flat];
     const Real f = (Real)factor;
-    out.x = h.x * f;
-    out.y = h.y * f;
+    o.x = h.x * f;
+    o.y = h.y * f;
   } else {
-    out.x = (Real)0;
-    out.y = (Real)0;
+    o.x = (Real)0;
+    o.y = (Real)0;
   }
-  grid[e] = out;
-}
-
-ScaleGeom make_geom(const double* const* inv_c, const GridGeom& g, const int* N) {
-  ScaleGeom s;
-  s.d = g.d;
-  s.NN = 1;
-  s.cells = 1;
-  for (int t = 0; t < kMaxDim; ++t) {
-    s.N[t] = t < g.d ? N[t] : 1;
-    s.n[t] = t < g.d ? g.n[t] : 1;
-    s.inv_c[t] = t < g.d ? inv_c[t] : nullptr;
-  }
-  for (int t = 0; t < g.d; ++t) {
-    s.NN *= s.N[t];
-    s.cells *= s.n[t];
-  }
-  return s;
+  grid[e] = o;
 }
 
 }  // namespace
 
 template <typename Real>
-cudaError_t launch_deconv_crop(const typename Cplx<Real>::type* grid, typename Cplx<Real>::type* fhat,
-                               const double* const* inv_c, const GridGeom& g, const int* N, int R, cudaStream_t st) {
-  const ScaleGeom s = make_geom(inv_c, g, N);
-  const int64_t total = s.NN * R;
-  if (total == 0) return cudaSuccess;
-  k_deconv_crop<Real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(grid, fhat, s, R);
+cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
+                               int nrhs, cudaStream_t st) {
+  (void)in;
+  if (max_elems <= 0 || n_items <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((max_elems + 255) / 256), (unsigned)n_items);
+  k_deconv_crop<Real><<<grid, 256, 0, st>>>(items, out, nrhs);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_pad_deconv(const typename Cplx<Real>::type* fhat, typename Cplx<Real>::type* grid,
-                              const double* const* inv_c, const GridGeom& g, const int* N, int R, cudaStream_t st) {
-  const ScaleGeom s = make_geom(inv_c, g, N);
-  const int64_t total = s.cells * R;
-  if (total == 0) return cudaSuccess;
-  k_pad_deconv<Real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(fhat, grid, s, R);
+cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
+                              int nrhs, cudaStream_t st) {
+  (void)out;
+  if (max_elems <= 0 || n_items <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((max_elems + 255) / 256), (unsigned)n_items);
+  k_pad_deconv<Real><<<grid, 256, 0, st>>>(items, in, nrhs);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_deconv_crop<float>(const float2*, float2*, const double* const*, const GridGeom&,
-                                               const int*, int, cudaStream_t);
-template cudaError_t launch_deconv_crop<double>(const double2*, double2*, const double* const*, const GridGeom&,
-                                                const int*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<float>(const float2*, float2*, const double* const*, const GridGeom&,
-                                              const int*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<double>(const double2*, double2*, const double* const*, const GridGeom&,
-                                               const int*, int, cudaStream_t);
+template cudaError_t launch_deconv_crop<float>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
+template cudaError_t launch_deconv_crop<double>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
+template cudaError_t launch_pad_deconv<float>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
+template cudaError_t launch_pad_deconv<double>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
 
 }  // namespace gbnfft

@@ -1,0 +1,1181 @@
+// Host engine: layout, sort, transforms and batch graphs (see engine.h).
+#include "engine.h"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+namespace gbnfft {
+
+namespace {
+
+constexpr size_t kSmemBudget = 200 * 1024;   // per block (the opt-in limit is 227 KB)
+constexpr size_t kSmemTarget = 100 * 1024;   // thread-per-point tiles: aim at two blocks per SM
+
+#define CK(call)                                                             \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      cudaGetLastError();                                                    \
+      return e_ == cudaErrorMemoryAllocation ? NFFT_ERR_OOM : NFFT_ERR_CUDA; \
+    }                                                                        \
+  } while (0)
+
+#define TRY(x)                    \
+  do {                            \
+    int s_ = (x);                 \
+    if (s_ != NFFT_OK) return s_; \
+  } while (0)
+
+bool is_fft_friendly(int64_t n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int taps_for(int window, int m) { return window == NFFT_KAISER_BESSEL ? 2 * m : 2 * m + 2; }
+
+// Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2
+// (all terms positive, so it is accurate to rounding for the x used here).
+double bessel_i0(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 500; ++k) {
+    term *= q / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+double shape_param(int window, int m, double sigma) {
+  if (window == NFFT_GAUSSIAN) return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * M_PI);
+  return M_PI * (2.0 - 1.0 / sigma);
+}
+
+// 1 / c_k for k = -N/2 .. N/2-1 of one dimension, with the kernels' window
+// normalisation psi = phi / phi(0):  inv_c(k) = phi(0) / (n phihat(k)).
+//   Gaussian:       phi(0) = (pi b)^(-1/2),        n phihat(k) = exp(-b (pi k / n)^2)
+//   Kaiser-Bessel:  phi(0) = sinh(b m) / (pi m),   n phihat(k) = I0(m sqrt(b^2 - (2 pi k / n)^2))
+std::vector<double> scaling_table(int window, int m, int64_t N, int64_t n, double b) {
+  std::vector<double> out((size_t)N);
+  for (int64_t a = 0; a < N; ++a) {
+    const double k = (double)(a - N / 2);
+    if (window == NFFT_GAUSSIAN) {
+      const double t = M_PI * k / (double)n;
+      out[(size_t)a] = std::exp(b * t * t) / std::sqrt(M_PI * b);
+    } else {
+      const double w = 2.0 * M_PI * k / (double)n;
+      const double arg = m * std::sqrt(b * b - w * w);
+      out[(size_t)a] = std::sinh(b * m) / (M_PI * m * bessel_i0(arg));
+    }
+  }
+  return out;
+}
+
+// Row pitch for the warp kernels' tiles: a warp instruction touches Q rows of
+// W consecutive elements; the pitch (>= the row length) needing the fewest
+// shared-memory wavefronts -- the most 4-byte words one bank must serve,
+// averaged over the row's start -- wins, the smallest on ties.
+int choose_pitch(int last, int W, int csize) {
+  const int Q = 32 / W > 0 ? 32 / W : 1;
+  const int words = csize / 4;
+  int best = last, best_cost = INT_MAX;
+  for (int pitch = last; pitch < last + 32; ++pitch) {
+    int cost = 0;
+    for (int x0 = 0; x0 < 32; ++x0) {
+      int bank[32] = {0};
+      for (int q = 0; q < Q; ++q)
+        for (int ix = 0; ix < W; ++ix)
+          for (int w = 0; w < words; ++w) ++bank[((q * pitch + x0 + ix) * words + w) % 32];
+      int mx = 0;
+      for (int b = 0; b < 32; ++b) mx = bank[b] > mx ? bank[b] : mx;
+      cost += mx;
+    }
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = pitch;
+    }
+  }
+  return best;
+}
+
+template <typename T>
+int alloc_dev(T*& p, size_t bytes, int64_t& total) {
+  void* q = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? NFFT_ERR_OOM : NFFT_ERR_CUDA;
+  }
+  p = static_cast<T*>(q);
+  total += (int64_t)bytes;
+  return NFFT_OK;
+}
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <typename Real>
+const void* tiled_kernel(int d, int taps, bool spread);
+template <>
+const void* tiled_kernel<float>(int d, int taps, bool spread) {
+  return spread ? spread_tiled_kernel_f32(d, taps) : interp_tiled_kernel_f32(d, taps);
+}
+template <>
+const void* tiled_kernel<double>(int d, int taps, bool spread) {
+  return spread ? spread_tiled_kernel_f64(d, taps) : interp_tiled_kernel_f64(d, taps);
+}
+template <typename Real>
+const void* global_kernel(bool spread);
+template <>
+const void* global_kernel<float>(bool spread) { return global_kernel_f32(spread); }
+template <>
+const void* global_kernel<double>(bool spread) { return global_kernel_f64(spread); }
+template <typename Real>
+const void* wpp_kernel(int d, int taps, bool spread);
+template <>
+const void* wpp_kernel<float>(int d, int taps, bool spread) { return wpp_kernel_f32(d, taps, spread); }
+template <>
+const void* wpp_kernel<double>(int d, int taps, bool spread) { return wpp_kernel_f64(d, taps, spread); }
+template <typename Real>
+const void* planes_kernel(int taps, int warps, bool spread);
+template <>
+const void* planes_kernel<float>(int taps, int warps, bool spread) { return planes_kernel_f32(taps, warps, spread); }
+template <>
+const void* planes_kernel<double>(int taps, int warps, bool spread) { return planes_kernel_f64(taps, warps, spread); }
+template <typename Real>
+size_t planes_table_bytes(int taps, int bp, int np, int nw, const int* tile);
+template <>
+size_t planes_table_bytes<float>(int taps, int bp, int np, int nw, const int* tile) {
+  return planes_table_bytes_f32(taps, bp, np, nw, tile);
+}
+template <>
+size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* tile) {
+  return planes_table_bytes_f64(taps, bp, np, nw, tile);
+}
+
+}  // namespace
+
+// ===========================================================================
+// parameters shared with nfft_plan_params
+
+int64_t oversampled_size(int64_t N, double sigma) {
+  int64_t n = (int64_t)std::ceil(sigma * (double)N - 1e-9);
+  if (n < 2) n = 2;
+  while (n % 2 != 0 || !is_fft_friendly(n)) ++n;
+  return n;
+}
+
+int window_taps(int window, int m) { return taps_for(window, m); }
+
+int validate_spec(const ItemSpec& s, int precision) {
+  if (s.d < 1 || s.d > 3) return NFFT_ERR_INVALID_ARG;
+  if (s.M < 0 || s.M > (int64_t)INT32_MAX) return NFFT_ERR_INVALID_ARG;
+  if (!(s.sigma >= 1.0) || !std::isfinite(s.sigma) || s.sigma > 16.0) return NFFT_ERR_INVALID_ARG;
+  if (s.m < 1) return NFFT_ERR_INVALID_ARG;
+  if (s.window != NFFT_GAUSSIAN && s.window != NFFT_KAISER_BESSEL) return NFFT_ERR_INVALID_ARG;
+  if (precision != NFFT_FP64 && precision != NFFT_FP32_MIXED) return NFFT_ERR_INVALID_ARG;
+  if (s.nrhs < 1 || s.nrhs > 4096) return NFFT_ERR_INVALID_ARG;
+  if (taps_for(s.window, s.m) > kMaxTaps) return NFFT_ERR_UNSUPPORTED;
+  int64_t cells = 1;
+  for (int t = 0; t < s.d; ++t) {
+    if (s.N[t] < 2 || (s.N[t] & 1) || s.N[t] > ((int64_t)1 << 30)) return NFFT_ERR_INVALID_ARG;
+    const int64_t n = oversampled_size(s.N[t], s.sigma);
+    if (n < 2 * s.m + 2 || n < s.N[t]) return NFFT_ERR_INVALID_ARG;
+    cells *= n;
+  }
+  if (cells > (int64_t)INT32_MAX) return NFFT_ERR_UNSUPPORTED;
+  return NFFT_OK;
+}
+
+// ===========================================================================
+// lifetime
+
+Engine::~Engine() {
+  if (stream) cudaStreamSynchronize(stream);
+  drop_graphs();
+  if (capture_stream) cudaStreamDestroy(capture_stream);
+  release_layout();
+  for (auto& fc : fclasses) {
+    for (auto& kv : fc.plans) cufftDestroy(kv.second);
+    free_dev(fc.buf);
+  }
+  for (double* t : tables) cudaFree(t);
+  free_dev(err_flag);
+  free_dev(ewald_partials);
+  free_dev(ewald_out);
+  free_dev(d_items);
+  for (int k = 0; k < 2; ++k) {
+    if (h_table[k]) cudaFreeHost(h_table[k]);
+    if (slot_done[k]) cudaEventDestroy(slot_done[k]);
+  }
+  for (auto& e : events) {
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.stop);
+  }
+  for (auto& e : free_events) {
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.stop);
+  }
+}
+
+int Engine::init(const std::vector<ItemSpec>& in_specs, int prec, cudaStream_t st, bool is_single) {
+  if (in_specs.empty()) return NFFT_ERR_INVALID_ARG;
+  for (const auto& s : in_specs) TRY(validate_spec(s, prec));
+  specs = in_specs;
+  precision = prec;
+  csize = prec == NFFT_FP64 ? 16 : 8;
+  stream = st;
+  single = is_single;
+  CK(cudaGetDevice(&device));
+  CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+  int v = 0;
+  CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  smem_optin = (size_t)v;
+  CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  smem_per_sm = (size_t)v;
+  TRY(alloc_dev(err_flag, sizeof(int), device_bytes));
+  CK(cudaMemset(err_flag, 0, sizeof(int)));
+  TRY(alloc_dev(ewald_out, 2 * sizeof(double), device_bytes));
+  if (single) {
+    int64_t NN = 1;
+    for (int t = 0; t < specs[0].d; ++t) NN *= specs[0].N[t];
+    const int64_t np = std::max(ewald_partials_needed(NN), ewald_partials_needed(specs[0].M)) + 1;
+    TRY(alloc_dev(ewald_partials, sizeof(double) * (size_t)np, device_bytes));
+  }
+  TRY(alloc_dev(d_items, sizeof(ItemDev) * specs.size(), device_bytes));
+  if (!single) {
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaMallocHost((void**)&h_table[k], sizeof(ItemDev) * specs.size()));
+      CK(cudaEventCreateWithFlags(&slot_done[k], cudaEventDisableTiming));
+    }
+  }
+  TRY(build_fft());
+  TRY(build_layout());
+  return NFFT_OK;
+}
+
+// FFT classes: items with the same (d, n); every item owns spec.nrhs grids
+// (a plan: rhs_cap grids) in its class buffer.
+int Engine::build_fft() {
+  const int nitems = (int)specs.size();
+  item_fclass.assign(nitems, -1);
+  item_grid_offset.assign(nitems, 0);
+  for (int i = 0; i < nitems; ++i) {
+    const ItemSpec& s = specs[i];
+    int64_t n[3] = {1, 1, 1};
+    for (int t = 0; t < s.d; ++t) n[t] = oversampled_size(s.N[t], s.sigma);
+    int found = -1;
+    for (size_t c = 0; c < fclasses.size(); ++c)
+      if (fclasses[c].d == s.d && fclasses[c].n[0] == n[0] && fclasses[c].n[1] == n[1] && fclasses[c].n[2] == n[2])
+        found = (int)c;
+    if (found < 0) {
+      FClass fc;
+      fc.d = s.d;
+      fc.cells = 1;
+      for (int t = 0; t < 3; ++t) {
+        fc.n[t] = n[t];
+        fc.cells *= n[t];
+      }
+      fc.grids = 0;
+      fclasses.push_back(fc);
+      found = (int)fclasses.size() - 1;
+    }
+    FClass& fc = fclasses[found];
+    item_fclass[i] = found;
+    item_grid_offset[i] = (int64_t)fc.grids * fc.cells;
+    fc.grids += single ? rhs_cap : s.nrhs;
+  }
+  for (auto& fc : fclasses) {
+    TRY(alloc_dev(fc.buf, (size_t)fc.grids * (size_t)fc.cells * csize, device_bytes));
+    cufftHandle h;
+    TRY(fft_handle(fc, single ? 1 : fc.grids, &h));
+  }
+  return NFFT_OK;
+}
+
+int Engine::release_layout() {
+  free_dev(d_point_offsets);
+  free_dev(d_bin_offsets);
+  free_dev(bin_count);
+  free_dev(bin_start);
+  free_dev(sub_count);
+  free_dev(sub_start);
+  free_dev(num_subs);
+  free_dev(subs);
+  free_dev(bin_rank);
+  free_dev(perm);
+  free_dev(local);
+  for (int t = 0; t < 3; ++t) free_dev(delta[t]);
+  device_bytes -= layout_bytes;
+  layout_bytes = 0;
+  return NFFT_OK;
+}
+
+// Bins, kernel classes, the internal item order, the item table and the
+// sort buffers.  Re-run when the method, a bin edge or the subproblem size
+// changes; points must then be set again.
+int Engine::build_layout() {
+  drop_graphs();
+  release_layout();
+  points_set = false;
+  const int nitems = (int)specs.size();
+  max_sub = max_sub_opt > 0 ? max_sub_opt : 1024;
+  const size_t budget = smem_optin < kSmemBudget ? smem_optin : kSmemBudget;
+
+  struct Choice {
+    int bin[3], tile[3], pitch, method, taps;
+  };
+  std::vector<Choice> ch(nitems);
+  for (int i = 0; i < nitems; ++i) {
+    const ItemSpec& s = specs[i];
+    Choice& c = ch[i];
+    c.taps = taps_for(s.window, s.m);
+    const int defaults[3][3] = {{1024, 1, 1}, {32, 32, 1}, {8, 8, 16}};
+    int64_t n[3] = {1, 1, 1};
+    for (int t = 0; t < s.d; ++t) n[t] = oversampled_size(s.N[t], s.sigma);
+    for (int t = 0; t < 3; ++t) c.bin[t] = 1;
+    for (int t = 0; t < s.d; ++t) {
+      int b = bin_opt[t] > 0 ? bin_opt[t] : defaults[s.d - 1][t];
+      if (b > n[t]) b = (int)n[t];
+      const int maxb = s.d == 1 ? (1 << 30) : (1 << local_bits(s.d)) - 1;
+      if (b > maxb) b = maxb;
+      c.bin[t] = b;
+    }
+    auto tile_bytes = [&](const int* bin) {
+      size_t cells = 1;
+      for (int t = 0; t < s.d; ++t) cells *= (size_t)(bin[t] + c.taps - 1);
+      return cells * csize;
+    };
+    const bool explicit_bins = bin_opt[0] > 0 || bin_opt[1] > 0 || bin_opt[2] > 0;
+    while (tile_bytes(c.bin) > budget && !explicit_bins) {
+      int tmax = 0;
+      for (int t = 1; t < s.d; ++t)
+        if (c.bin[t] > c.bin[tmax]) tmax = t;
+      if (c.bin[tmax] <= 2) break;
+      c.bin[tmax] /= 2;
+    }
+    for (int t = 0; t < 3; ++t) c.tile[t] = t < s.d ? c.bin[t] + c.taps - 1 : 1;
+    c.pitch = choose_pitch(c.tile[s.d - 1], c.taps, (int)csize);
+    size_t rows = 1;
+    for (int t = 0; t + 1 < s.d; ++t) rows *= (size_t)c.tile[t];
+    const size_t wtile = rows * (size_t)c.pitch * csize;
+    const bool tiled_ok = tile_bytes(c.bin) <= budget && c.taps <= (s.d == 3 ? 26 : 32);
+    const bool warp_ok = s.d >= 2 && c.taps <= 16 &&
+                         (s.d == 3 ? wtile + 32768 <= budget : 2 * wtile + 4096 <= budget);
+    int method = method_opt;
+    if (method == NFFT_METHOD_AUTO) method = warp_ok ? NFFT_METHOD_WARP : (tiled_ok ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
+    if (method == NFFT_METHOD_TILED && !tiled_ok) return NFFT_ERR_UNSUPPORTED;
+    if (method == NFFT_METHOD_WARP && !warp_ok) return NFFT_ERR_UNSUPPORTED;
+    c.method = method;
+  }
+  // group items into kernel classes (stable by first appearance)
+  auto same = [&](int a, int b) {
+    return specs[a].d == specs[b].d && ch[a].taps == ch[b].taps && specs[a].window == specs[b].window &&
+           ch[a].method == ch[b].method && ch[a].bin[0] == ch[b].bin[0] && ch[a].bin[1] == ch[b].bin[1] &&
+           ch[a].bin[2] == ch[b].bin[2];
+  };
+  std::vector<int> rep;
+  std::vector<int> cls(nitems);
+  for (int i = 0; i < nitems; ++i) {
+    int found = -1;
+    for (size_t r = 0; r < rep.size(); ++r)
+      if (same(i, rep[r])) found = (int)r;
+    if (found < 0) {
+      rep.push_back(i);
+      found = (int)rep.size() - 1;
+    }
+    cls[i] = found;
+  }
+  order.clear();
+  for (size_t r = 0; r < rep.size(); ++r)
+    for (int i = 0; i < nitems; ++i)
+      if (cls[i] == (int)r) order.push_back(i);
+
+  // items in internal order
+  items.assign(nitems, ItemDev{});
+  kclasses.clear();
+  std::vector<int64_t> pts_off(nitems + 1, 0);
+  std::vector<int> bin_off(nitems + 1, 0);
+  max_subs_total = 0;
+  for (int k = 0; k < nitems; ++k) {
+    const int u = order[k];
+    const ItemSpec& s = specs[u];
+    const Choice& c = ch[u];
+    ItemDev& it = items[k];
+    std::memset(&it, 0, sizeof(it));
+    GridGeom& g = it.geom;
+    g.d = s.d;
+    g.grid_cells = 1;
+    g.tile_cells = 1;
+    int nb_total = 1;
+    for (int t = 0; t < 3; ++t) {
+      const int64_t n = t < s.d ? oversampled_size(s.N[t], s.sigma) : 1;
+      g.n[t] = (int)n;
+      g.bin[t] = c.bin[t];
+      g.nbins[t] = (int)((n + c.bin[t] - 1) / c.bin[t]);
+      g.tile[t] = c.tile[t];
+      g.grid_cells *= n;
+      g.tile_cells *= c.tile[t];
+      nb_total *= g.nbins[t];
+      it.N[t] = t < s.d ? (int)s.N[t] : 1;
+    }
+    it.NN = 1;
+    for (int t = 0; t < s.d; ++t) it.NN *= s.N[t];
+    it.M = s.M;
+    it.nrhs = single ? 1 : s.nrhs;
+    WindowDev& w = it.win;
+    w.kind = s.window;
+    w.m = s.m;
+    w.shift = s.window == NFFT_KAISER_BESSEL ? 1 : 0;
+    w.taps = c.taps;
+    for (int t = 0; t < 3; ++t) {
+      const double sig = t < s.d ? (double)g.n[t] / (double)s.N[t] : 2.0;
+      const double b = shape_param(s.window, s.m, sig);
+      w.b[t] = b;
+      w.kb_norm[t] = 1.0 / (1.0 - std::exp(-2.0 * b * s.m));
+      if (t < s.d) {
+        const auto key = std::make_tuple(s.window, s.N[t], (int64_t)g.n[t], s.m, 0);
+        auto f = table_cache.find(key);
+        if (f == table_cache.end()) {
+          std::vector<double> tab = scaling_table(s.window, s.m, s.N[t], g.n[t], b);
+          double* dtab = nullptr;
+          TRY(alloc_dev(dtab, sizeof(double) * tab.size(), device_bytes));
+          CK(cudaMemcpy(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+          tables.push_back(dtab);
+          f = table_cache.emplace(key, dtab).first;
+        }
+        it.inv_c[t] = f->second;
+      }
+    }
+    FClass& fc = fclasses[item_fclass[u]];
+    it.grid = static_cast<char*>(fc.buf) + item_grid_offset[u] * (int64_t)csize;
+    it.point_offset = pts_off[k];
+    it.bin_offset = bin_off[k];
+    pts_off[k + 1] = pts_off[k] + s.M;
+    bin_off[k + 1] = bin_off[k] + nb_total;
+    max_subs_total += nb_total + s.M / max_sub + 1;
+    if ((int64_t)bin_off[k + 1] > ((int64_t)1 << 30)) return NFFT_ERR_UNSUPPORTED;
+    // kernel class bookkeeping
+    if (kclasses.empty() || cls[u] != cls[order[kclasses.back().item_begin]]) {
+      KClass kc{};
+      kc.d = s.d;
+      kc.taps = c.taps;
+      kc.window = s.window;
+      kc.method = c.method;
+      for (int t = 0; t < 3; ++t) {
+        kc.bin[t] = c.bin[t];
+        kc.tile[t] = c.tile[t];
+      }
+      kc.pitch = c.pitch;
+      kc.item_begin = k;
+      kc.bin_begin = bin_off[k];
+      kc.max_nrhs = 0;
+      kc.max_subs = 0;
+      kclasses.push_back(kc);
+    }
+    KClass& kc = kclasses.back();
+    kc.item_end = k + 1;
+    kc.bin_end = bin_off[k + 1];
+    kc.max_nrhs = std::max(kc.max_nrhs, it.nrhs);
+    kc.max_subs += nb_total + s.M / max_sub + 1;
+  }
+  total_points = pts_off[nitems];
+  total_bins = bin_off[nitems];
+  // device buffers
+  int64_t before = device_bytes;
+  const size_t P = (size_t)std::max<int64_t>(total_points, 1);
+  const size_t B = (size_t)std::max(total_bins, 1);
+  TRY(alloc_dev(d_point_offsets, sizeof(int64_t) * (nitems + 1), device_bytes));
+  TRY(alloc_dev(d_bin_offsets, sizeof(int) * (nitems + 1), device_bytes));
+  TRY(alloc_dev(bin_count, sizeof(int) * B, device_bytes));
+  TRY(alloc_dev(bin_start, sizeof(int) * B, device_bytes));
+  TRY(alloc_dev(sub_count, sizeof(int) * B, device_bytes));
+  TRY(alloc_dev(sub_start, sizeof(int) * B, device_bytes));
+  TRY(alloc_dev(num_subs, sizeof(int), device_bytes));
+  TRY(alloc_dev(subs, sizeof(SubProblem) * (size_t)max_subs_total, device_bytes));
+  TRY(alloc_dev(bin_rank, sizeof(int2) * P, device_bytes));
+  TRY(alloc_dev(perm, sizeof(int) * P, device_bytes));
+  TRY(alloc_dev(local, sizeof(uint32_t) * P, device_bytes));
+  const int dmax = [&] {
+    int m = 1;
+    for (const auto& s : specs) m = std::max(m, s.d);
+    return m;
+  }();
+  const size_t rsize = precision == NFFT_FP64 ? 8 : 4;
+  for (int t = 0; t < dmax; ++t) TRY(alloc_dev(delta[t], rsize * P, device_bytes));
+  layout_bytes = device_bytes - before;
+  CK(cudaMemcpy(d_point_offsets, pts_off.data(), sizeof(int64_t) * (nitems + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_bin_offsets, bin_off.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemset(num_subs, 0, sizeof(int)));
+  CK(cudaMemset(sub_start, 0, sizeof(int) * B));
+  CK(cudaMemcpy(d_items, items.data(), sizeof(ItemDev) * nitems, cudaMemcpyHostToDevice));
+  if (!single)
+    for (int k = 0; k < 2; ++k) std::memcpy(h_table[k], items.data(), sizeof(ItemDev) * nitems);
+  return NFFT_OK;
+}
+
+int Engine::fft_handle(FClass& fc, int batch, cufftHandle* out) {
+  auto it = fc.plans.find(batch);
+  if (it != fc.plans.end()) {
+    *out = it->second;
+    return cufftSetStream(it->second, stream) == CUFFT_SUCCESS ? NFFT_OK : NFFT_ERR_CUFFT;
+  }
+  cufftHandle h;
+  if (cufftCreate(&h) != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
+  long long dims[3];
+  for (int t = 0; t < fc.d; ++t) dims[t] = fc.n[t];
+  size_t work = 0;
+  const cufftType type = precision == NFFT_FP64 ? CUFFT_Z2Z : CUFFT_C2C;
+  const cufftResult r =
+      cufftMakePlanMany64(h, fc.d, dims, nullptr, 1, fc.cells, nullptr, 1, fc.cells, type, batch, &work);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(h);
+    return r == CUFFT_ALLOC_FAILED ? NFFT_ERR_OOM : NFFT_ERR_CUFFT;
+  }
+  if (cufftSetStream(h, stream) != CUFFT_SUCCESS) {
+    cufftDestroy(h);
+    return NFFT_ERR_CUFFT;
+  }
+  fc.plans[batch] = h;
+  *out = h;
+  return NFFT_OK;
+}
+
+int Engine::run_fft(FClass& fc, int batch, int64_t grid_offset, int direction) {
+  cufftHandle h;
+  TRY(fft_handle(fc, batch, &h));
+  cufftResult r;
+  if (precision == NFFT_FP64) {
+    cufftDoubleComplex* g = static_cast<cufftDoubleComplex*>(fc.buf) + grid_offset;
+    r = cufftExecZ2Z(h, g, g, direction);
+  } else {
+    cufftComplex* g = static_cast<cufftComplex*>(fc.buf) + grid_offset;
+    r = cufftExecC2C(h, g, g, direction);
+  }
+  return r == CUFFT_SUCCESS ? NFFT_OK : NFFT_ERR_CUFFT;
+}
+
+// ===========================================================================
+// profiling
+
+int Engine::stage_begin(int stage, EventPair* ev) {
+  if (!profile) return NFFT_OK;
+  if (!free_events.empty()) {
+    *ev = free_events.back();
+    free_events.pop_back();
+  } else {
+    CK(cudaEventCreate(&ev->start));
+    CK(cudaEventCreate(&ev->stop));
+  }
+  ev->stage = stage;
+  CK(cudaEventRecord(ev->start, stream));
+  return NFFT_OK;
+}
+
+int Engine::stage_end(EventPair* ev) {
+  if (!profile) return NFFT_OK;
+  CK(cudaEventRecord(ev->stop, stream));
+  events.push_back(*ev);
+  return NFFT_OK;
+}
+
+int Engine::stage_times(double* ms, int64_t* launches, int reset) {
+  CK(cudaStreamSynchronize(stream));
+  for (auto& e : events) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e.start, e.stop));
+    stage_ms[e.stage] += t;
+    stage_calls[e.stage] += 1;
+    free_events.push_back(e);
+  }
+  events.clear();
+  for (int s = 0; s < NFFT_STAGE_COUNT; ++s) {
+    ms[s] = stage_ms[s];
+    if (launches) launches[s] = stage_calls[s];
+    if (reset) {
+      stage_ms[s] = 0;
+      stage_calls[s] = 0;
+    }
+  }
+  return NFFT_OK;
+}
+
+int Engine::blocks_per_sm(const void* fn, int threads, size_t smem) {
+  const auto key = std::make_tuple(fn, threads, smem);
+  auto it = occupancy.find(key);
+  if (it != occupancy.end()) return it->second;
+  int nb = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 0;
+  }
+  occupancy[key] = nb;
+  return nb;
+}
+
+// ===========================================================================
+// point kernels
+
+template <typename Real>
+int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out, int nrhs) {
+  PointKernelArgs<Real> a{};
+  a.pts.perm = perm;
+  a.pts.local = local;
+  for (int t = 0; t < 3; ++t) a.pts.delta[t] = static_cast<const Real*>(delta[t]);
+  a.pts.subs = subs;
+  a.pts.sub_start = sub_start;
+  a.pts.num_subs = num_subs;
+  a.items = d_items;
+  a.bin_begin = kc.bin_begin;
+  a.bin_end = kc.bin_end;
+  a.total_bins = total_bins;
+  a.in = in;
+  a.out = out;
+  a.nrhs = nrhs;
+  const int max_nrhs = in ? nrhs : kc.max_nrhs;
+  switch (kc.method) {
+    case NFFT_METHOD_WARP:
+      return kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs);
+    case NFFT_METHOD_TILED:
+      return run_tiled<Real>(kc, a, spread, max_nrhs);
+    default:
+      return run_global<Real>(kc, a, spread);
+  }
+}
+
+// 3-D: one shared tile per block.  Spreading splits the tile's planes among
+// the block's warps (a power of two dividing the taps); interpolation gives
+// each warp groups of points.  Warps per block: the option if set, else the
+// most resident warps (ties: fewer warps per block).  Right-hand sides per
+// pass fit two blocks per SM.
+template <typename Real>
+int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs) {
+  const int W = kc.taps;
+  const size_t rows = (size_t)kc.tile[0] * kc.tile[1];
+  const size_t tbytes = rows * (size_t)kc.pitch * csize;
+  auto smem_of = [&](int nw, int np) {
+    return (size_t)np * tbytes + planes_table_bytes<Real>(W, 32 * nw, np, nw, kc.tile);
+  };
+  int np = 1;
+  while (np < max_nrhs && smem_of(8, np + 1) <= smem_per_sm / 2) ++np;
+  int best_nw = 0, best_warps = 0;
+  size_t best_smem = 0;
+  const void* best_fn = nullptr;
+  for (int nw = 1; nw <= 8; nw *= 2) {
+    if (threads_opt > 0 && 32 * nw != threads_opt) continue;
+    const void* fn = planes_kernel<Real>(W, nw, spread);
+    if (!fn) continue;
+    const size_t smem = smem_of(nw, np);
+    if (smem > smem_optin) continue;
+    const int per_sm = blocks_per_sm(fn, 32 * nw, smem);
+    if (per_sm * nw > best_warps) {
+      best_warps = per_sm * nw;
+      best_nw = nw;
+      best_smem = smem;
+      best_fn = fn;
+    }
+  }
+  if (!best_fn || best_warps == 0) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = np;
+  WppLayout lay{kc.pitch, (int)(rows * kc.pitch), best_nw};
+  int64_t blocks = (int64_t)(best_warps / best_nw) * num_sms;
+  if (blocks > kc.max_subs) blocks = kc.max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a, &lay};
+  CK(cudaFuncSetAttribute(best_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
+  CK(cudaLaunchKernel(best_fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
+  return NFFT_OK;
+}
+
+// 2-D warp per point: private tiles for spreading, one shared tile for
+// interpolation.
+template <typename Real>
+int Engine::run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs) {
+  const int D = kc.d, W = kc.taps;
+  const void* fn = wpp_kernel<Real>(D, W, spread);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  size_t rows = 1;
+  for (int t = 0; t + 1 < D; ++t) rows *= (size_t)kc.tile[t];
+  const size_t elems = rows * (size_t)kc.pitch;
+  const size_t tbytes = elems * csize;
+  const size_t scratch = (size_t)(32 * D * W + (D == 3 ? W * W : W)) * (csize / 2);
+  int np = 1;
+  if (spread) {
+    while (np < max_nrhs && 4 * (size_t)(np + 1) * tbytes + 4 * scratch <= smem_per_sm) ++np;
+  } else {
+    while (np < max_nrhs && (size_t)(np + 1) * tbytes + 8 * scratch <= smem_per_sm / 2) ++np;
+  }
+  int best_nw = 0, best_warps = 0;
+  size_t best_smem = 0;
+  for (int nw = 1; nw <= 8; ++nw) {
+    const size_t smem = spread ? (size_t)nw * ((size_t)np * tbytes + scratch + (size_t)np * 32 * csize)
+                               : (size_t)np * tbytes + nw * scratch;
+    if (smem > smem_optin) break;
+    const int per_sm = blocks_per_sm(fn, 32 * nw, smem);
+    if (per_sm * nw > best_warps) {
+      best_warps = per_sm * nw;
+      best_nw = nw;
+      best_smem = smem;
+    }
+  }
+  if (best_nw == 0) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = np;
+  WppLayout lay{kc.pitch, (int)elems, best_nw};
+  int64_t blocks = (int64_t)(best_warps / best_nw) * num_sms;
+  if (blocks > kc.max_subs) blocks = kc.max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a, &lay};
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
+  return NFFT_OK;
+}
+
+// Thread per point with a shared tile (shared-memory atomics for spreading).
+template <typename Real>
+int Engine::run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs) {
+  const void* fn = tiled_kernel<Real>(kc.d, kc.taps, spread);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  size_t cells = 1;
+  for (int t = 0; t < kc.d; ++t) cells *= (size_t)kc.tile[t];
+  const size_t one = cells * csize;
+  size_t budget = smem_optin < kSmemBudget ? smem_optin : kSmemBudget;
+  if (budget > kSmemTarget && one <= kSmemTarget) budget = kSmemTarget;
+  int pass = (int)(budget / one);
+  if (pass < 1) pass = 1;
+  if (pass > max_nrhs) pass = max_nrhs;
+  a.rhs_per_pass = pass;
+  const size_t smem = one * (size_t)pass;
+  const int threads = threads_opt > 0 ? threads_opt : 256;
+  int per_sm = blocks_per_sm(fn, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)per_sm * num_sms;
+  if (blocks > kc.max_subs) blocks = kc.max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a};
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, stream));
+  return NFFT_OK;
+}
+
+template <typename Real>
+int Engine::run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread) {
+  const void* fn = global_kernel<Real>(spread);
+  a.rhs_per_pass = 1;
+  int64_t blocks = (int64_t)8 * num_sms;
+  if (blocks > kc.max_subs) blocks = kc.max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a};
+  const int threads = threads_opt > 0 ? threads_opt : 256;
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, 0, stream));
+  return NFFT_OK;
+}
+
+// ===========================================================================
+// set_points
+
+template <typename Real>
+int Engine::set_points_impl(const double* x_override) {
+  SortArgs s{};
+  s.items = d_items;
+  s.n_items = (int)items.size();
+  s.point_offsets = d_point_offsets;
+  s.bin_offsets = d_bin_offsets;
+  s.total_points = total_points;
+  s.total_bins = total_bins;
+  s.x_override = x_override;
+  s.err = err_flag;
+  EventPair ev{};
+  TRY(stage_begin(NFFT_STAGE_SORT, &ev));
+  CK(cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)std::max(total_bins, 1), stream));
+  CK(launch_bin_count<Real>(s, bin_count, bin_rank, stream));
+  CK(launch_scan(bin_count, bin_start, total_bins, nullptr, stream));
+  Real* d[3] = {static_cast<Real*>(delta[0]), static_cast<Real*>(delta[1]), static_cast<Real*>(delta[2])};
+  CK(launch_scatter<Real>(s, bin_start, bin_rank, perm, local, d, stream));
+  CK(launch_subproblem_count(bin_count, total_bins, max_sub, sub_count, stream));
+  CK(launch_scan(sub_count, sub_start, total_bins, num_subs, stream));
+  CK(launch_subproblem_fill(s, bin_count, bin_start, sub_start, max_sub, subs, stream));
+  TRY(stage_end(&ev));
+  return NFFT_OK;
+}
+
+int Engine::set_points_single(const double* x) {
+  points_set = false;
+  const int s = precision == NFFT_FP64 ? set_points_impl<double>(x) : set_points_impl<float>(x);
+  if (s == NFFT_OK) points_set = true;
+  return s;
+}
+
+int Engine::set_points_batch(const double* const* x) {
+  points_set = false;
+  for (size_t k = 0; k < items.size(); ++k) {
+    items[k].x = x[order[k]];
+    if (!items[k].x && items[k].M > 0) return NFFT_ERR_INVALID_ARG;
+  }
+  // the points pointers ride in both graph tables too
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaEventSynchronize(slot_done[k]));
+    for (size_t i = 0; i < items.size(); ++i) h_table[k][i].x = items[i].x;
+  }
+  CK(cudaMemcpyAsync(d_items, items.data(), sizeof(ItemDev) * items.size(), cudaMemcpyHostToDevice, stream));
+  const int s = precision == NFFT_FP64 ? set_points_impl<double>(nullptr) : set_points_impl<float>(nullptr);
+  // the host copy must outlive the async copy above
+  CK(cudaStreamSynchronize(stream));
+  if (s == NFFT_OK) points_set = true;
+  return s;
+}
+
+// ===========================================================================
+// transforms of a single item (per-call pointers as overrides)
+
+int Engine::adjoint_single(const void* f, void* fhat, int R) {
+  FClass& fc = fclasses[item_fclass[0]];
+  const ItemDev& it = items[0];
+  for (int r0 = 0; r0 < R; r0 += rhs_cap) {
+    const int nr = (R - r0) < rhs_cap ? (R - r0) : rhs_cap;
+    EventPair ev{};
+    TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
+    CK(cudaMemsetAsync(it.grid, 0, (size_t)nr * fc.cells * csize, stream));
+    if (it.M > 0) {
+      const void* fin = static_cast<const char*>(f) + (int64_t)r0 * it.M * (int64_t)csize;
+      TRY(precision == NFFT_FP64 ? run_points<double>(kclasses[0], true, fin, nullptr, nr)
+                                 : run_points<float>(kclasses[0], true, fin, nullptr, nr));
+    }
+    TRY(stage_end(&ev));
+    TRY(stage_begin(NFFT_STAGE_FFT, &ev));
+    TRY(run_fft(fc, nr, item_grid_offset[0], CUFFT_FORWARD));
+    TRY(stage_end(&ev));
+    TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
+    void* out = static_cast<char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
+    CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, 1, it.NN * nr, nullptr, out, nr, stream)
+                              : launch_deconv_crop<float>(d_items, 1, it.NN * nr, nullptr, out, nr, stream));
+    TRY(stage_end(&ev));
+  }
+  return NFFT_OK;
+}
+
+int Engine::forward_single(const void* fhat, void* f, int R) {
+  FClass& fc = fclasses[item_fclass[0]];
+  const ItemDev& it = items[0];
+  for (int r0 = 0; r0 < R; r0 += rhs_cap) {
+    const int nr = (R - r0) < rhs_cap ? (R - r0) : rhs_cap;
+    EventPair ev{};
+    TRY(stage_begin(NFFT_STAGE_PAD, &ev));
+    const void* hin = static_cast<const char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
+    CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, 1, fc.cells * nr, hin, nullptr, nr, stream)
+                              : launch_pad_deconv<float>(d_items, 1, fc.cells * nr, hin, nullptr, nr, stream));
+    TRY(stage_end(&ev));
+    TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
+    TRY(run_fft(fc, nr, item_grid_offset[0], CUFFT_INVERSE));
+    TRY(stage_end(&ev));
+    TRY(stage_begin(NFFT_STAGE_INTERP, &ev));
+    if (it.M > 0) {
+      void* fout = static_cast<char*>(f) + (int64_t)r0 * it.M * (int64_t)csize;
+      // interpolation reads `in` only through the override flag; the values come from the grid
+      TRY(precision == NFFT_FP64 ? run_points<double>(kclasses[0], false, fout, fout, nr)
+                                 : run_points<float>(kclasses[0], false, fout, fout, nr));
+    }
+    TRY(stage_end(&ev));
+  }
+  return NFFT_OK;
+}
+
+// ===========================================================================
+// transforms of a batch (pointers from the item table)
+
+template <typename Real>
+int Engine::adjoint_table(bool in_graph) {
+  EventPair ev{};
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
+  for (auto& fc : fclasses) CK(cudaMemsetAsync(fc.buf, 0, (size_t)fc.grids * fc.cells * csize, stream));
+  for (const auto& kc : kclasses) TRY(run_points<Real>(kc, true, nullptr, nullptr, 0));
+  if (!in_graph) TRY(stage_end(&ev));
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_FFT, &ev));
+  for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_FORWARD));
+  if (!in_graph) TRY(stage_end(&ev));
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
+  int64_t max_elems = 0;
+  for (const auto& it : items) max_elems = std::max(max_elems, it.NN * it.nrhs);
+  CK(launch_deconv_crop<Real>(d_items, (int)items.size(), max_elems, nullptr, nullptr, 0, stream));
+  if (!in_graph) TRY(stage_end(&ev));
+  return NFFT_OK;
+}
+
+template <typename Real>
+int Engine::forward_table(bool in_graph) {
+  EventPair ev{};
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_PAD, &ev));
+  int64_t max_elems = 0;
+  for (const auto& it : items) max_elems = std::max(max_elems, it.geom.grid_cells * it.nrhs);
+  CK(launch_pad_deconv<Real>(d_items, (int)items.size(), max_elems, nullptr, nullptr, 0, stream));
+  if (!in_graph) TRY(stage_end(&ev));
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
+  for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_INVERSE));
+  if (!in_graph) TRY(stage_end(&ev));
+  if (!in_graph) TRY(stage_begin(NFFT_STAGE_INTERP, &ev));
+  for (const auto& kc : kclasses) TRY(run_points<Real>(kc, false, nullptr, nullptr, 0));
+  if (!in_graph) TRY(stage_end(&ev));
+  return NFFT_OK;
+}
+
+void Engine::drop_graphs() {
+  for (int k = 0; k < 2; ++k) {
+    if (graph_adj[k]) cudaGraphExecDestroy(graph_adj[k]);
+    if (graph_fwd[k]) cudaGraphExecDestroy(graph_fwd[k]);
+    graph_adj[k] = graph_fwd[k] = nullptr;
+  }
+}
+
+// One graph per direction and table slot: the table upload (pinned host ->
+// device), then every launch of the transform.
+int Engine::capture_graphs() {
+  // capture on a private stream (the legacy default stream cannot be
+  // captured); the graphs are launched on the caller's stream
+  if (!capture_stream) CK(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+  struct Restore {
+    Engine* e;
+    cudaStream_t s;
+    ~Restore() { e->stream = s; }
+  } restore{this, stream};
+  stream = capture_stream;
+  for (int k = 0; k < 2; ++k) {
+    for (int dir = 0; dir < 2; ++dir) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      int s = NFFT_OK;
+      cudaError_t e = cudaMemcpyAsync(d_items, h_table[k], sizeof(ItemDev) * items.size(), cudaMemcpyHostToDevice,
+                                      stream);
+      if (e != cudaSuccess) s = NFFT_ERR_CUDA;
+      if (s == NFFT_OK) {
+        if (dir == 0)
+          s = precision == NFFT_FP64 ? adjoint_table<double>(true) : adjoint_table<float>(true);
+        else
+          s = precision == NFFT_FP64 ? forward_table<double>(true) : forward_table<float>(true);
+      }
+      const cudaError_t ee = cudaStreamEndCapture(stream, &g);
+      if (s != NFFT_OK || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s != NFFT_OK ? s : NFFT_ERR_CUDA;
+      }
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        cudaGetLastError();
+        return NFFT_ERR_CUDA;
+      }
+      (dir == 0 ? graph_adj : graph_fwd)[k] = ex;
+    }
+  }
+  return NFFT_OK;
+}
+
+int Engine::adjoint_batch(const void* const* f, void* const* fhat) {
+  if (!graph_adj[0]) TRY(capture_graphs());
+  const int k = slot;
+  slot ^= 1;
+  CK(cudaEventSynchronize(slot_done[k]));   // the launch that last read this table is done
+  for (size_t i = 0; i < items.size(); ++i) {
+    h_table[k][i].in = f[order[i]];
+    h_table[k][i].out = fhat[order[i]];
+  }
+  EventPair ev{};
+  TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));   // whole-graph time is booked as the spread stage
+  CK(cudaGraphLaunch(graph_adj[k], stream));
+  TRY(stage_end(&ev));
+  CK(cudaEventRecord(slot_done[k], stream));
+  return NFFT_OK;
+}
+
+int Engine::forward_batch(const void* const* fhat, void* const* f) {
+  if (!graph_fwd[0]) TRY(capture_graphs());
+  const int k = slot;
+  slot ^= 1;
+  CK(cudaEventSynchronize(slot_done[k]));
+  for (size_t i = 0; i < items.size(); ++i) {
+    h_table[k][i].in = fhat[order[i]];
+    h_table[k][i].out = f[order[i]];
+  }
+  EventPair ev{};
+  TRY(stage_begin(NFFT_STAGE_INTERP, &ev));
+  CK(cudaGraphLaunch(graph_fwd[k], stream));
+  TRY(stage_end(&ev));
+  CK(cudaEventRecord(slot_done[k], stream));
+  return NFFT_OK;
+}
+
+// ===========================================================================
+// Ewald reciprocal energy (single item)
+
+template <typename Real>
+int Engine::ewald_impl(const void* q, double L, double alpha) {
+  using C = typename Cplx<Real>::type;
+  FClass& fc = fclasses[item_fclass[0]];
+  const ItemDev& it = items[0];
+  EventPair ev{};
+  TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
+  CK(cudaMemsetAsync(it.grid, 0, (size_t)fc.cells * csize, stream));
+  if (it.M > 0) TRY(run_points<Real>(kclasses[0], true, q, nullptr, 1));
+  TRY(stage_end(&ev));
+  TRY(stage_begin(NFFT_STAGE_FFT, &ev));
+  TRY(run_fft(fc, 1, item_grid_offset[0], CUFFT_FORWARD));
+  TRY(stage_end(&ev));
+  TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
+  EwaldGeom g{};
+  g.d = it.geom.d;
+  g.NN = it.NN;
+  for (int t = 0; t < kMaxDim; ++t) {
+    g.N[t] = it.N[t];
+    g.n[t] = it.geom.n[t];
+    g.inv_c[t] = t < it.geom.d ? it.inv_c[t] : nullptr;
+  }
+  const double al = alpha * L;
+  g.coef = M_PI * M_PI / (al * al);
+  CK(launch_ewald_sum<Real>(static_cast<const C*>(it.grid), true, g, ewald_partials, 1.0 / (2.0 * M_PI * L), 0.0,
+                            ewald_out, stream));
+  CK(launch_sumsq<Real>(static_cast<const C*>(q), it.M, ewald_partials, -alpha / std::sqrt(M_PI), 0.0,
+                        ewald_out + 1, stream));
+  TRY(stage_end(&ev));
+  return NFFT_OK;
+}
+
+int Engine::ewald(const void* q, double L, double alpha, double* out) {
+  TRY(precision == NFFT_FP64 ? ewald_impl<double>(q, L, alpha) : ewald_impl<float>(q, L, alpha));
+  double parts[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(parts, ewald_out, sizeof(parts), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  out[0] = parts[0] + parts[1];
+  out[1] = parts[0];
+  out[2] = parts[1];
+  return NFFT_OK;
+}
+
+int Engine::ewald_sum(const void* S, double L, double alpha, double* sum_dev) {
+  const ItemDev& it = items[0];
+  EwaldGeom g{};
+  g.d = it.geom.d;
+  g.NN = it.NN;
+  for (int t = 0; t < kMaxDim; ++t) {
+    g.N[t] = it.N[t];
+    g.n[t] = it.geom.n[t];
+    g.inv_c[t] = nullptr;
+  }
+  const double al = alpha * L;
+  g.coef = M_PI * M_PI / (al * al);
+  const double scale = 1.0 / (2.0 * M_PI * L);
+  if (precision == NFFT_FP64)
+    CK(launch_ewald_sum<double>(static_cast<const double2*>(S), false, g, ewald_partials, scale, 0.0, sum_dev,
+                                stream));
+  else
+    CK(launch_ewald_sum<float>(static_cast<const float2*>(S), false, g, ewald_partials, scale, 0.0, sum_dev,
+                               stream));
+  return NFFT_OK;
+}
+
+// ===========================================================================
+// options, info, sync
+
+int Engine::sync() {
+  CK(cudaStreamSynchronize(stream));
+  int flag = 0;
+  CK(cudaMemcpy(&flag, err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemset(err_flag, 0, sizeof(int)));
+    if (flag & 2) return NFFT_ERR_TIMEOUT;
+    if (flag & 1) return NFFT_ERR_DOMAIN;
+  }
+  return NFFT_OK;
+}
+
+int Engine::set_stream(cudaStream_t s) {
+  stream = s;
+  drop_graphs();   // graphs are replayed on any stream, but the cuFFT plans follow the stream
+  return NFFT_OK;
+}
+
+int Engine::set_option(int option, int64_t value) {
+  switch (option) {
+    case NFFT_OPT_METHOD:
+      if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_WARP) return NFFT_ERR_INVALID_ARG;
+      method_opt = (int)value;
+      break;
+    case NFFT_OPT_BIN_0:
+    case NFFT_OPT_BIN_1:
+    case NFFT_OPT_BIN_2: {
+      const int t = option - NFFT_OPT_BIN_0;
+      int dmax = 1;
+      for (const auto& s : specs) dmax = std::max(dmax, s.d);
+      if (value < 0 || t >= dmax || value > 65535) return NFFT_ERR_INVALID_ARG;
+      bin_opt[t] = (int)value;
+      break;
+    }
+    case NFFT_OPT_MAX_SUBPROBLEM:
+      if (value < 0 || value > (1 << 20)) return NFFT_ERR_INVALID_ARG;
+      max_sub_opt = (int)value;
+      break;
+    case NFFT_OPT_RHS_CAPACITY: {
+      if (value < 1 || value > 4096) return NFFT_ERR_INVALID_ARG;
+      if (!single) return NFFT_ERR_UNSUPPORTED;   // a batch fixes its right-hand sides per item
+      CK(cudaStreamSynchronize(stream));
+      for (auto& fc : fclasses) {
+        for (auto& kv : fc.plans) cufftDestroy(kv.second);
+        fc.plans.clear();
+        device_bytes -= (int64_t)fc.grids * fc.cells * (int64_t)csize;
+        free_dev(fc.buf);
+      }
+      fclasses.clear();
+      rhs_cap = (int)value;
+      TRY(build_fft());
+      const bool had = points_set;
+      TRY(build_layout());   // item grid pointers moved
+      (void)had;
+      return NFFT_OK;
+    }
+    case NFFT_OPT_PROFILE:
+      profile = value != 0;
+      return NFFT_OK;
+    case NFFT_OPT_THREADS:
+      if (value != 0 && (value < 32 || value > 256 || value % 32 != 0)) return NFFT_ERR_INVALID_ARG;
+      threads_opt = (int)value;
+      return NFFT_OK;
+    default:
+      return NFFT_ERR_INVALID_ARG;
+  }
+  CK(cudaStreamSynchronize(stream));
+  return build_layout();
+}
+
+int Engine::info(nfft_plan_info* out) const {
+  std::memset(out, 0, sizeof(*out));
+  const ItemSpec& s = specs[0];
+  const ItemDev& it = items[0];
+  out->d = s.d;
+  out->M = s.M;
+  out->m = s.m;
+  out->taps = it.win.taps;
+  out->window = s.window;
+  out->precision = precision;
+  out->method = kclasses.empty() ? 0 : kclasses[0].method;
+  out->n_bins = 1;
+  for (int t = 0; t < 3; ++t) {
+    out->N[t] = t < s.d ? s.N[t] : 1;
+    out->n[t] = it.geom.n[t];
+    out->bin[t] = it.geom.bin[t];
+    out->sigma[t] = t < s.d ? (double)it.geom.n[t] / (double)s.N[t] : 1.0;
+    if (t < s.d) out->n_bins *= it.geom.nbins[t];
+  }
+  out->rhs_capacity = single ? rhs_cap : s.nrhs;
+  out->threads = threads_opt;
+  out->device_bytes = device_bytes;
+  return NFFT_OK;
+}
+
+}  // namespace gbnfft

@@ -1,0 +1,173 @@
+// The host engine behind the C ABI: a set of NFFT items (one for a plan, many
+// for a batch) with their sort buffers, grids, cuFFT plans and kernel
+// launches.
+//
+//   kernel class: items with the same d, taps, window and bin edges (hence
+//                 tile shape); their points are spread / interpolated by one
+//                 persistent launch over the class's subproblems;
+//   FFT class:    items with the same oversampled grid; their grids are
+//                 contiguous and transformed by one cuFFT plan-many.
+#pragma once
+
+#include <cufft.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ewald.h"
+#include "gbnfft.h"
+#include "kernels.h"
+
+namespace gbnfft {
+
+struct ItemSpec {
+  int d;
+  int64_t N[3];
+  int64_t M;
+  double sigma;
+  int m;
+  int window;
+  int nrhs;     // grids kept for the item (batch: its right-hand sides)
+};
+
+struct KClass {
+  int d, taps, window, method;
+  int bin[3], tile[3], nbins_total;
+  int pitch;
+  int item_begin, item_end;   // internal item range
+  int bin_begin, bin_end;     // global bin range
+  int max_nrhs;
+  int64_t max_subs;           // bound on the class's subproblems
+};
+
+struct FClass {
+  int d;
+  int64_t n[3];
+  int64_t cells;
+  int grids;                  // grids in the buffer
+  void* buf = nullptr;
+  std::map<int, cufftHandle> plans;
+};
+
+struct EventPair {
+  int stage;
+  cudaEvent_t start, stop;
+};
+
+// Shared parameter rules (engine.cu).
+int64_t oversampled_size(int64_t N, double sigma);
+int window_taps(int window, int m);
+int validate_spec(const ItemSpec& s, int precision);
+
+class Engine {
+ public:
+  ~Engine();
+  // Validate, allocate everything, build the layout.  single = one item whose
+  // pointers come with every call (a plan); else a batch (pointer table).
+  int init(const std::vector<ItemSpec>& specs, int precision, cudaStream_t stream, bool single);
+
+  int set_option(int option, int64_t value);
+  int set_stream(cudaStream_t s);
+  int set_points_single(const double* x);
+  int set_points_batch(const double* const* x);
+  int adjoint_single(const void* f, void* fhat, int R);
+  int forward_single(const void* fhat, void* f, int R);
+  int adjoint_batch(const void* const* f, void* const* fhat);
+  int forward_batch(const void* const* fhat, void* const* f);
+  int sync();
+  int stage_times(double* ms, int64_t* launches, int reset);
+  int ewald(const void* q, double L, double alpha, double* out3);
+  int ewald_sum(const void* S, double L, double alpha, double* sum_dev);
+  int info(nfft_plan_info* out) const;
+
+  // exposed for the C ABI
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<ItemSpec> specs;        // user order
+  bool points_set = false;
+
+ private:
+  int build_layout();
+  int release_layout();
+  int build_fft();
+  template <typename Real> int set_points_impl(const double* x_override);
+  template <typename Real> int run_points(const KClass& kc, bool spread, const void* in, void* out, int nrhs);
+  template <typename Real> int run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
+  template <typename Real> int run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
+  template <typename Real> int run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
+  template <typename Real> int run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
+  template <typename Real> int adjoint_table(bool in_graph);
+  template <typename Real> int forward_table(bool in_graph);
+  template <typename Real> int ewald_impl(const void* q, double L, double alpha);
+  int run_fft(FClass& fc, int batch, int64_t grid_offset, int direction);
+  int fft_handle(FClass& fc, int batch, cufftHandle* out);
+  int blocks_per_sm(const void* fn, int threads, size_t smem);
+  int stage_begin(int stage, EventPair* ev);
+  int stage_end(EventPair* ev);
+  int capture_graphs();
+  void drop_graphs();
+
+  size_t csize = 16;
+  int device = 0, num_sms = 1;
+  size_t smem_optin = 48 * 1024, smem_per_sm = 100 * 1024;
+  bool single = true;
+
+  // options
+  int method_opt = NFFT_METHOD_AUTO;
+  int bin_opt[3] = {0, 0, 0};
+  int max_sub_opt = 0;
+  int max_sub = 1024;
+  int threads_opt = 0;
+  int rhs_cap = 1;
+  bool profile = false;
+
+  // items (internal order: grouped by kernel class)
+  std::vector<int> order;             // internal -> user
+  std::vector<ItemDev> items;         // internal order, host copy
+  ItemDev* d_items = nullptr;
+  ItemDev* h_table[2] = {nullptr, nullptr};   // pinned copies the batch graphs upload
+  std::vector<int> item_fclass;       // user order
+  std::vector<int64_t> item_grid_offset;   // user order, elements into the FFT class buffer
+  std::vector<KClass> kclasses;
+  std::vector<FClass> fclasses;
+  std::vector<double*> tables;        // scaling tables (owned)
+  std::map<std::tuple<int, int64_t, int64_t, int, int>, double*> table_cache;
+
+  // sort buffers
+  int64_t total_points = 0;
+  int total_bins = 0;
+  int64_t max_subs_total = 0;
+  int64_t* d_point_offsets = nullptr;
+  int* d_bin_offsets = nullptr;
+  int* bin_count = nullptr;
+  int* bin_start = nullptr;
+  int* sub_count = nullptr;
+  int* sub_start = nullptr;
+  int* num_subs = nullptr;
+  SubProblem* subs = nullptr;
+  int2* bin_rank = nullptr;
+  int* perm = nullptr;
+  uint32_t* local = nullptr;
+  void* delta[3] = {nullptr, nullptr, nullptr};
+  int* err_flag = nullptr;
+  double* ewald_partials = nullptr;
+  double* ewald_out = nullptr;
+  int64_t device_bytes = 0;
+  int64_t layout_bytes = 0;
+
+  // batch graphs (two slots: the host fills one table while the other runs)
+  cudaGraphExec_t graph_adj[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_fwd[2] = {nullptr, nullptr};
+  cudaEvent_t slot_done[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
+  int slot = 0;
+
+  // profiling
+  std::vector<EventPair> events, free_events;
+  double stage_ms[NFFT_STAGE_COUNT] = {0};
+  int64_t stage_calls[NFFT_STAGE_COUNT] = {0};
+  std::map<std::tuple<const void*, int, size_t>, int> occupancy;
+};
+
+}  // namespace gbnfft

@@ -1,4 +1,9 @@
-// Internal launch interface between the host plan code and the kernels.
+// Internal launch interface between the host engine and the kernels.
+//
+// Every launch works on a table of items (ItemDev): a single plan is a
+// batch of one item.  Per-call pointers can be passed as overrides in the
+// launch arguments (single-item launches) or read from the table (batched
+// launches, where a CUDA graph refreshes the table before the kernels).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,80 +14,101 @@
 namespace gbnfft {
 
 // ---- set_points (sort.cu) -------------------------------------------------
-// Cell and bin of every point, and its rank inside its bin (warp-aggregated
-// atomics on bin_count).  err gets bit 0 for a non-finite coordinate.
+struct SortArgs {
+  const ItemDev* items;
+  int n_items;
+  const int64_t* point_offsets;   // n_items + 1 prefix sums of M (device)
+  const int* bin_offsets;         // n_items + 1 prefix sums of bins (device)
+  int64_t total_points;
+  int total_bins;
+  const double* x_override;       // single item: points of this call (else items[i].x)
+  int* err;                       // bit 0: non-finite coordinate
+};
+// Cell and global bin of every point, and its rank inside its bin.
 template <typename Real>
-cudaError_t launch_bin_count(const double* x, int64_t M, const GridGeom& g, int* bin_count, int2* bin_rank,
-                             int* err, cudaStream_t st);
-// Exclusive prefix sum of n ints (one block); *total = sum (may be null).
+cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st);
+// Exclusive prefix sum of n ints; *total = sum (may be null).
 cudaError_t launch_scan(const int* in, int* out, int n, int* total, cudaStream_t st);
-// Write every point to its sorted slot: perm, packed in-bin offsets, deltas.
+// Write every point to its sorted slot: perm (index within its item), packed in-bin offsets, deltas.
 template <typename Real>
-cudaError_t launch_scatter(const double* x, int64_t M, const GridGeom& g, const int* bin_start, const int2* bin_rank,
-                           int* perm, uint32_t* local, Real* const* delta, cudaStream_t st);
-// Subproblems per bin (ceil(count / P)), then their records after a scan.
+cudaError_t launch_scatter(const SortArgs& s, const int* bin_start, const int2* bin_rank, int* perm, uint32_t* local,
+                           Real* const* delta, cudaStream_t st);
+// Subproblems per global bin (ceil(count / P)), then their records.
 cudaError_t launch_subproblem_count(const int* bin_count, int nbins, int P, int* sub_count, cudaStream_t st);
-cudaError_t launch_subproblem_fill(const int* bin_count, const int* bin_start, const int* sub_start, int nbins,
+cudaError_t launch_subproblem_fill(const SortArgs& s, const int* bin_count, const int* bin_start, const int* sub_start,
                                    int P, SubProblem* subs, cudaStream_t st);
 
-// ---- spreading / interpolation (spread_*.cu, interp_*.cu) -----------------
+// ---- spreading / interpolation ---------------------------------------------
 template <typename Real>
 struct PointKernelArgs {
   SortedPoints<Real> pts;
-  GridGeom geom;
-  WindowDev win;
-  int64_t M;
-  const typename Cplx<Real>::type* f_in;   // spread: R x M values
-  typename Cplx<Real>::type* f_out;        // interp: R x M values
-  typename Cplx<Real>::type* grid;         // R grids of geom.grid_cells
-  const typename Cplx<Real>::type* grid_in;
-  int nrhs;                                // right-hand sides in this call
-  int rhs_per_pass;                        // tiles held in shared memory at once
+  const ItemDev* items;
+  int bin_begin, bin_end;   // the global bins of this launch's items
+  int total_bins;
+  int rhs_per_pass;         // tiles held in shared memory at once
+  // single-item overrides (in == nullptr: read the item table)
+  const void* in;
+  void* out;
+  int nrhs;
 };
 
-// Tiled (shared-memory) kernels; false if (d, taps) has no instantiation.
+// The launch's subproblems: [lo, hi).
 template <typename Real>
-bool launch_spread_tiled(const PointKernelArgs<Real>& a, int blocks, int threads, size_t smem, cudaStream_t st,
-                         cudaError_t* err);
-template <typename Real>
-bool launch_interp_tiled(const PointKernelArgs<Real>& a, int blocks, int threads, size_t smem, cudaStream_t st,
-                         cudaError_t* err);
-// Global-memory kernels (any d, any taps <= kMaxTaps).
-template <typename Real>
-cudaError_t launch_spread_global(const PointKernelArgs<Real>& a, int blocks, int threads, cudaStream_t st);
-template <typename Real>
-cudaError_t launch_interp_global(const PointKernelArgs<Real>& a, int blocks, int threads, cudaStream_t st);
-// Occupancy query for the tiled kernels (blocks per SM, 0 if unsupported).
-template <typename Real>
-int tiled_blocks_per_sm(int d, int taps, bool spread, int threads, size_t smem);
-template <typename Real>
-cudaError_t tiled_set_smem_limit(int d, int taps, bool spread, size_t smem);
+__device__ __forceinline__ void launch_subs(const PointKernelArgs<Real>& a, int& lo, int& hi) {
+  lo = a.pts.sub_start[a.bin_begin];
+  hi = a.bin_end < a.total_bins ? a.pts.sub_start[a.bin_end] : *a.pts.num_subs;
+}
 
-// Warp-per-point kernels (points_wpp.cuh, d = 2, 3, taps <= 16): the block
-// layout the host chooses.
+// Per-call view of an item.
+struct ItemCall {
+  const void* in;
+  void* out;
+  int nrhs;
+};
+template <typename Real>
+__device__ __forceinline__ ItemCall item_call(const PointKernelArgs<Real>& a, const ItemDev& it) {
+  ItemCall c;
+  c.in = a.in ? a.in : it.in;
+  c.out = a.in ? a.out : it.out;
+  c.nrhs = a.in ? a.nrhs : it.nrhs;
+  return c;
+}
+
+// Tiled thread-per-point kernels (any d, taps <= 32; d = 3 up to 26).
+const void* spread_tiled_kernel_f32(int d, int taps);
+const void* spread_tiled_kernel_f64(int d, int taps);
+const void* interp_tiled_kernel_f32(int d, int taps);
+const void* interp_tiled_kernel_f64(int d, int taps);
+// Global-memory kernels (any d, taps <= 32).
+const void* global_kernel_f32(bool spread);
+const void* global_kernel_f64(bool spread);
+
+// Warp-per-point (d = 2) and shared-tile (d = 3) kernels, taps <= 16.
 struct WppLayout {
   int pitch;        // row pitch of a tile, in complex elements
-  int warp_cells;   // elements of one private tile (rows * pitch), spread only
+  int warp_cells;   // elements of one tile (rows * pitch)
   int warps;        // warps per block
 };
 const void* wpp_kernel_f32(int d, int taps, bool spread);
 const void* wpp_kernel_f64(int d, int taps, bool spread);
-// 3-D shared-tile kernels (points_planes.cuh): plane-owner spreading and
-// point-group interpolation, taps <= 16, same WppLayout (warps divides taps
-// for spreading).
+// 3-D shared-tile kernels (points_planes.cuh): plane-owner spreading (warps
+// a power of two dividing the taps) and point-group interpolation.
 const void* planes_kernel_f32(int taps, int warps, bool spread);
 const void* planes_kernel_f64(int taps, int warps, bool spread);
 size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile);
 size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile);
 
 // ---- scaling (deconv.cu) --------------------------------------------------
-// Adjoint step 3: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
+// Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
+// Forward step 1 for every item: grid[r][l] = fhat[r][k] * inv_c(k) if l = k mod n, else 0.
+// One launch over all items (blockIdx.y = item); max_elems = max over items
+// of nrhs * |I_N| (crop) or nrhs * |I_n| (pad).  in/out/nrhs override the
+// item table when in != nullptr (single-item launches).
 template <typename Real>
-cudaError_t launch_deconv_crop(const typename Cplx<Real>::type* grid, typename Cplx<Real>::type* fhat,
-                               const double* const* inv_c, const GridGeom& g, const int* N, int R, cudaStream_t st);
-// Forward step 1: grid[r][l] = fhat[r][k] * inv_c(k) if l = k mod n, k in I_N, else 0.
+cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
+                               int nrhs, cudaStream_t st);
 template <typename Real>
-cudaError_t launch_pad_deconv(const typename Cplx<Real>::type* fhat, typename Cplx<Real>::type* grid,
-                              const double* const* inv_c, const GridGeom& g, const int* N, int R, cudaStream_t st);
+cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
+                              int nrhs, cudaStream_t st);
 
 }  // namespace gbnfft

@@ -93,8 +93,9 @@ __device__ __forceinline__ void plane_index_tables(const PlaneSmem<W, Real>& s, 
 // Stage a batch: thread t handles point first + t.
 template <int W, typename Real>
 __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a, const PlaneSmem<W, Real>& s,
-                                                  int first, int nb, int r0, int np, int bp, int T1, int pitch,
-                                                  bool want_values) {
+                                                  const WindowDev& win, const typename Cplx<Real>::type* f_in,
+                                                  int64_t M, int first, int nb, int r0, int np, int bp, int T1,
+                                                  int pitch, bool want_values) {
   const int t = threadIdx.x;
   if (t < nb) {
     const int idx = first + t;
@@ -106,12 +107,12 @@ __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a
     Real* w = s.wt + t * (3 * W);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const Real base = a.pts.delta[d][idx] + (Real)(a.win.m - a.win.shift);
+      const Real base = a.pts.delta[d][idx] + (Real)(win.m - win.shift);
 #pragma unroll
-      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(a.win, d, base - (Real)i);
+      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(win, d, base - (Real)i);
     }
     if (want_values)
-      for (int r = 0; r < np; ++r) s.vt[r * bp + t] = a.f_in[(int64_t)(r0 + r) * a.M + j];
+      for (int r = 0; r < np; ++r) s.vt[r * bp + t] = f_in[(int64_t)(r0 + r) * M + j];
   }
 }
 
@@ -124,29 +125,34 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   constexpr int BP = 32 * NW;    // points per batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const GridGeom& g = a.geom;
   const int np_max = a.rhs_per_pass;
-  const int T1 = g.tile[1], T2 = g.tile[2];
-  const int rows = g.tile[0] * T1;
   const int pitch = lay.pitch;
-  const int tile_elems = rows * pitch;
-  const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, g);
+  const int tile_elems = lay.warp_cells;
   const int ix = lane % W, q = lane / W;
   const bool active = S::FULL || q < S::Q;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
+    const ItemDev& it = a.items[sub.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    const C* f_in = static_cast<const C*>(call.in);
+    C* grid = static_cast<C*>(it.grid);
+    const int T1 = g.tile[1], T2 = g.tile[2];
+    const int rows = g.tile[0] * T1;
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, g);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
-    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
     plane_index_tables<W, Real>(s, g, origin);
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
       for (int e = threadIdx.x; e < np * tile_elems; e += BP) s.tile[e] = cmake<C>(0.0, 0.0);
       for (int pb = 0; pb < sub.count; pb += BP) {
         const int nb = min(BP, sub.count - pb);
         __syncthreads();   // tile zeroed / previous batch no longer read
-        plane_stage_batch<W, Real>(a, s, sub.start + pb, nb, r0, np, BP, T1, pitch, true);
+        plane_stage_batch<W, Real>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, np, BP, T1, pitch, true);
         __syncthreads();
         for (int pp = 0; pp < nb; ++pp) {
           const int2 rec = s.pt[pp];                // (tile offset of the point's first tap, its plane)
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
         const C* src = s.tile + r * tile_elems + row * pitch;
         for (int x = lane; x < T2; x += 32) {
           const C c = src[x];
-          if (c.x != (Real)0 || c.y != (Real)0) grid_add(a.grid + gb + s.gx[x], c);
+          if (c.x != (Real)0 || c.y != (Real)0) grid_add(grid + gb + s.gx[x], c);
         }
       }
       __syncthreads();
@@ -212,26 +218,31 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = lay.warps;
   const int bp = blockDim.x;
-  const GridGeom& g = a.geom;
   const int np_max = a.rhs_per_pass;
-  const int T1 = g.tile[1], T2 = g.tile[2];
-  const int rows = g.tile[0] * T1;
   const int pitch = lay.pitch;
-  const int tile_elems = rows * pitch;
-  const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, g);
+  const int tile_elems = lay.warp_cells;
   const int grp = lane / W, ix = lane % W;
   const bool active = grp < S::PPW;
-  const int plane_stride = T1 * pitch;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
+    const ItemDev& it = a.items[sub.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    C* f_out = static_cast<C*>(call.out);
+    const C* grid_in = static_cast<const C*>(it.grid);
+    const int T1 = g.tile[1], T2 = g.tile[2];
+    const int rows = g.tile[0] * T1;
+    const int plane_stride = T1 * pitch;
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, g);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
-    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
     __syncthreads();   // the previous subproblem's readers are done
     plane_index_tables<W, Real>(s, g, origin);
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
       __syncthreads();
       // load the tile: a warp per row, lanes along the row
       for (int e = warp; e < np * rows; e += nw) {
@@ -240,12 +251,12 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
         const int z = row / T1, y = row - z * T1;
         const int64_t gb = (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
         C* dst = s.tile + r * tile_elems + row * pitch;
-        for (int x = lane; x < T2; x += 32) dst[x] = a.grid_in[gb + s.gx[x]];
+        for (int x = lane; x < T2; x += 32) dst[x] = grid_in[gb + s.gx[x]];
       }
       for (int pb = 0; pb < sub.count; pb += bp) {
         const int nb = min(bp, sub.count - pb);
         __syncthreads();
-        plane_stage_batch<W, Real>(a, s, sub.start + pb, nb, r0, np, bp, T1, pitch, false);
+        plane_stage_batch<W, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, np, bp, T1, pitch, false);
         __syncthreads();
         for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
           const int pp = p0 + grp;
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
               }
               __syncwarp();
             }
-            if (mine && ix == 0) a.f_out[(int64_t)(r0 + r) * a.M + s.jt[pp]] = cmake<C>(ar, ai);
+            if (mine && ix == 0) f_out[(int64_t)(r0 + r) * it.M + s.jt[pp]] = cmake<C>(ar, ai);
           }
         }
       }

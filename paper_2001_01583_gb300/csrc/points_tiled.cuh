@@ -64,18 +64,25 @@ __global__ void __launch_bounds__(256) k_spread_tiled(PointKernelArgs<Real> a) {
   using C = typename Cplx<Real>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* tile = reinterpret_cast<Real*>(smem_raw);  // interleaved (re, im)
-  const GridGeom& g = a.geom;
-  const int tc = g.tile_cells;
-  const int T1 = D >= 2 ? g.tile[1] : 1;
-  const int T2 = D >= 3 ? g.tile[2] : 1;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
+    const ItemDev& it = a.items[s.item];
+    const GridGeom& g = it.geom;
+    const WindowDev& win = it.win;
+    const ItemCall call = item_call(a, it);
+    const C* f_in = static_cast<const C*>(call.in);
+    C* grid = static_cast<C*>(it.grid);
+    const int64_t M = it.M;
+    const int tc = g.tile_cells;
+    const int T1 = D >= 2 ? g.tile[1] : 1;
+    const int T2 = D >= 3 ? g.tile[2] : 1;
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(s.bin, g, bc);
-    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - win.m + win.shift;
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
       for (int e = threadIdx.x; e < 2 * tc * np; e += blockDim.x) tile[e] = (Real)0;
       __syncthreads();
       for (int p = threadIdx.x; p < s.count; p += blockDim.x) {
@@ -83,14 +90,14 @@ __global__ void __launch_bounds__(256) k_spread_tiled(PointKernelArgs<Real> a) {
         const int j = a.pts.perm[idx];
         const uint32_t loc = a.pts.local[idx];
         Real w0[W], w1[W], w2[W];
-        taps_of<W, Real>(a.win, 0, a.pts.delta[0][idx], w0);
-        if (D >= 2) taps_of<W, Real>(a.win, 1, a.pts.delta[1][idx], w1);
-        if (D >= 3) taps_of<W, Real>(a.win, 2, a.pts.delta[2][idx], w2);
+        taps_of<W, Real>(win, 0, a.pts.delta[0][idx], w0);
+        if (D >= 2) taps_of<W, Real>(win, 1, a.pts.delta[1][idx], w1);
+        if (D >= 3) taps_of<W, Real>(win, 2, a.pts.delta[2][idx], w2);
         const int l0 = unpack_local(loc, D, 0);
         const int l1 = D >= 2 ? unpack_local(loc, D, 1) : 0;
         const int l2 = D >= 3 ? unpack_local(loc, D, 2) : 0;
         for (int r = 0; r < np; ++r) {
-          const C v = a.f_in[(int64_t)(r0 + r) * a.M + j];
+          const C v = f_in[(int64_t)(r0 + r) * M + j];
           Real* tr = tile + 2 * r * tc;
           if (D == 1) {
 #pragma unroll
@@ -134,7 +141,7 @@ __global__ void __launch_bounds__(256) k_spread_tiled(PointKernelArgs<Real> a) {
         val.x = tile[2 * e];
         val.y = tile[2 * e + 1];
         if (val.x != (Real)0 || val.y != (Real)0)
-          grid_add(a.grid + (int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin), val);
+          grid_add(grid + (int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin), val);
       }
       __syncthreads();
     }
@@ -146,22 +153,30 @@ __global__ void __launch_bounds__(256) k_interp_tiled(PointKernelArgs<Real> a) {
   using C = typename Cplx<Real>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
-  const GridGeom& g = a.geom;
-  const int tc = g.tile_cells;
-  const int T1 = D >= 2 ? g.tile[1] : 1;
-  const int T2 = D >= 3 ? g.tile[2] : 1;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
+    const ItemDev& it = a.items[s.item];
+    const GridGeom& g = it.geom;
+    const WindowDev& win = it.win;
+    const ItemCall call = item_call(a, it);
+    C* f_out = static_cast<C*>(call.out);
+    const C* grid_in = static_cast<const C*>(it.grid);
+    const int64_t M = it.M;
+    const int tc = g.tile_cells;
+    const int T1 = D >= 2 ? g.tile[1] : 1;
+    const int T2 = D >= 3 ? g.tile[2] : 1;
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(s.bin, g, bc);
-    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - win.m + win.shift;
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
+      __syncthreads();
       for (int e = threadIdx.x; e < tc * np; e += blockDim.x) {
         const int r = e / tc;
         const int ee = e - r * tc;
-        tile[e] = a.grid_in[(int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin)];
+        tile[e] = grid_in[(int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin)];
       }
       __syncthreads();
       for (int p = threadIdx.x; p < s.count; p += blockDim.x) {
@@ -169,9 +184,9 @@ __global__ void __launch_bounds__(256) k_interp_tiled(PointKernelArgs<Real> a) {
         const int j = a.pts.perm[idx];
         const uint32_t loc = a.pts.local[idx];
         Real w0[W], w1[W], w2[W];
-        taps_of<W, Real>(a.win, 0, a.pts.delta[0][idx], w0);
-        if (D >= 2) taps_of<W, Real>(a.win, 1, a.pts.delta[1][idx], w1);
-        if (D >= 3) taps_of<W, Real>(a.win, 2, a.pts.delta[2][idx], w2);
+        taps_of<W, Real>(win, 0, a.pts.delta[0][idx], w0);
+        if (D >= 2) taps_of<W, Real>(win, 1, a.pts.delta[1][idx], w1);
+        if (D >= 3) taps_of<W, Real>(win, 2, a.pts.delta[2][idx], w2);
         const int l0 = unpack_local(loc, D, 0);
         const int l1 = D >= 2 ? unpack_local(loc, D, 1) : 0;
         const int l2 = D >= 3 ? unpack_local(loc, D, 2) : 0;
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(256) k_interp_tiled(PointKernelArgs<Real> a) {
           C out;
           out.x = ar;
           out.y = ai;
-          a.f_out[(int64_t)(r0 + r) * a.M + j] = out;
+          f_out[(int64_t)(r0 + r) * M + j] = out;
         }
       }
       __syncthreads();

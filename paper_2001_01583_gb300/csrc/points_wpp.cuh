@@ -49,8 +49,8 @@ struct WppBatch {
 };
 
 template <int D, int W, typename Real>
-__device__ __forceinline__ WppBatch<D, W, Real> wpp_load_batch(const PointKernelArgs<Real>& a, int first, int nb,
-                                                               Real* wtab, int lane) {
+__device__ __forceinline__ WppBatch<D, W, Real> wpp_load_batch(const PointKernelArgs<Real>& a, const WindowDev& win,
+                                                               int first, int nb, Real* wtab, int lane) {
   WppBatch<D, W, Real> b{0, 0u};
   if (lane < nb) {
     const int idx = first + lane;
@@ -59,9 +59,9 @@ __device__ __forceinline__ WppBatch<D, W, Real> wpp_load_batch(const PointKernel
     Real* w = wtab + lane * (D * W);
 #pragma unroll
     for (int t = 0; t < D; ++t) {
-      const Real base = a.pts.delta[t][idx] + (Real)(a.win.m - a.win.shift);
+      const Real base = a.pts.delta[t][idx] + (Real)(win.m - win.shift);
 #pragma unroll
-      for (int i = 0; i < W; ++i) w[t * W + i] = window_psi<Real>(a.win, t, base - (Real)i);
+      for (int i = 0; i < W; ++i) w[t * W + i] = window_psi<Real>(win, t, base - (Real)i);
     }
   }
   __syncwarp();
@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(256) k_spread_wpp(PointKernelArgs<Real> a, Wpp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = lay.warps;
-  const GridGeom& g = a.geom;
   const int np_max = a.rhs_per_pass;
   C* tiles = reinterpret_cast<C*>(smem_raw);                                   // [nw][np][warp_cells]
   Real* scratch = reinterpret_cast<Real*>(tiles + (size_t)nw * np_max * lay.warp_cells);
@@ -95,24 +94,30 @@ __global__ void __launch_bounds__(256) k_spread_wpp(PointKernelArgs<Real> a, Wpp
   // the batch's values, [np][32] per warp, after all warps' weight tables
   C* vtab = reinterpret_cast<C*>(scratch + nw * wpp_scratch_reals<D, W, Real>()) + (size_t)warp * np_max * 32;
   C* mine = tiles + (size_t)warp * np_max * lay.warp_cells;
-  const int T1 = D == 3 ? g.tile[1] : 1;                                       // rows of a 3-D tile plane
   const int ix = lane % W, q = lane / W;
   const bool active = q < S::Q;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
+    const ItemDev& it = a.items[s.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    const C* f_in = static_cast<const C*>(call.in);
+    C* grid = static_cast<C*>(it.grid);
+    const int T1 = D == 3 ? g.tile[1] : 1;                                     // rows of a 3-D tile plane
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(s.bin, g, bc);
-    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
       for (int e = lane; e < np * lay.warp_cells; e += 32) mine[e] = cmake<C>(0.0, 0.0);
       __syncwarp();
       for (int pb = warp * 32; pb < s.count; pb += nw * 32) {
         const int nb = min(32, s.count - pb);
-        const WppBatch<D, W, Real> bt = wpp_load_batch<D, W, Real>(a, s.start + pb, nb, wtab, lane);
+        const WppBatch<D, W, Real> bt = wpp_load_batch<D, W, Real>(a, it.win, s.start + pb, nb, wtab, lane);
         for (int r = 0; r < np; ++r)
-          if (lane < nb) vtab[r * 32 + lane] = a.f_in[(int64_t)(r0 + r) * a.M + bt.j];
+          if (lane < nb) vtab[r * 32 + lane] = f_in[(int64_t)(r0 + r) * it.M + bt.j];
         __syncwarp();
         for (int pp = 0; pp < nb; ++pp) {
           const uint32_t loc = __shfl_sync(0xffffffffu, bt.loc, pp);
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(256) k_spread_wpp(PointKernelArgs<Real> a, Wpp
           sy += c.y;
         }
         if (sx != (Real)0 || sy != (Real)0)
-          grid_add(a.grid + (int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin), cmake<C>(sx, sy));
+          grid_add(grid + (int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin), cmake<C>(sx, sy));
       }
       __syncthreads();
     }
@@ -183,36 +188,41 @@ __global__ void __launch_bounds__(256) k_interp_wpp(PointKernelArgs<Real> a, Wpp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = lay.warps;
-  const GridGeom& g = a.geom;
-  const int rows_total = g.tile_cells / g.tile[D - 1];
-  const int tile_elems = rows_total * lay.pitch;
+  const int tile_elems = lay.warp_cells;
   C* tile = reinterpret_cast<C*>(smem_raw);                                    // [np][rows][pitch]
   Real* scratch = reinterpret_cast<Real*>(tile + (size_t)a.rhs_per_pass * tile_elems);
   Real* wtab = scratch + warp * wpp_scratch_reals<D, W, Real>();
   Real* wrow = wtab + 32 * D * W;
-  const int T1 = D == 3 ? g.tile[1] : 1;
   const int ix = lane % W, q = lane / W;
   const bool active = q < S::Q;
-  const int nsub = *a.pts.num_subs;
-  for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
+    const ItemDev& it = a.items[s.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    C* f_out = static_cast<C*>(call.out);
+    const C* grid_in = static_cast<const C*>(it.grid);
+    const int T1 = D == 3 ? g.tile[1] : 1;
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(s.bin, g, bc);
-    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - a.win.m + a.win.shift;
-    for (int r0 = 0; r0 < a.nrhs; r0 += a.rhs_per_pass) {
-      const int np = min(a.rhs_per_pass, a.nrhs - r0);
+    for (int t = 0; t < D; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
+    for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
+      const int np = min(a.rhs_per_pass, call.nrhs - r0);
+      __syncthreads();
       for (int e = threadIdx.x; e < np * g.tile_cells; e += blockDim.x) {
         const int r = e / g.tile_cells;
         const int ee = e - r * g.tile_cells;
         const int last = g.tile[D - 1];
         const int row = ee / last, col = ee - row * last;
         tile[r * tile_elems + row * lay.pitch + col] =
-            a.grid_in[(int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin)];
+            grid_in[(int64_t)(r0 + r) * g.grid_cells + tile_to_grid(ee, g, origin)];
       }
       __syncthreads();
       for (int pb = warp * 32; pb < s.count; pb += nw * 32) {
         const int nb = min(32, s.count - pb);
-        const WppBatch<D, W, Real> bt = wpp_load_batch<D, W, Real>(a, s.start + pb, nb, wtab, lane);
+        const WppBatch<D, W, Real> bt = wpp_load_batch<D, W, Real>(a, it.win, s.start + pb, nb, wtab, lane);
         for (int r = 0; r < np; ++r) {
           const C* tr = tile + r * tile_elems;
           // lane L keeps the finished value of point L of the batch
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(256) k_interp_wpp(PointKernelArgs<Real> a, Wpp
             }
             __syncwarp();
           }
-          if (lane < nb) a.f_out[(int64_t)(r0 + r) * a.M + bt.j] = cmake<C>(outr, outi);
+          if (lane < nb) f_out[(int64_t)(r0 + r) * it.M + bt.j] = cmake<C>(outr, outi);
         }
         __syncwarp();
       }

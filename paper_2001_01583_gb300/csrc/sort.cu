@@ -2,11 +2,27 @@
 // by spatial bin.  The bins are the on-device form of the paper's subcells
 // (Section 3, Eqs. 7-8): a transform is the sum of the sub-transforms of any
 // partition of the points, so every bin can be spread independently.
+//
+// All items of a batch are sorted in one pass: item i's points are global
+// points [point_offsets[i], point_offsets[i+1]) and its bins are global bins
+// [bin_offsets[i], bin_offsets[i+1]).
 #include "kernels.h"
 
 namespace gbnfft {
 
 namespace {
+
+// Largest i with offs[i] <= v (offs ascending, offs[0] = 0 <= v < offs[n]).
+template <typename T>
+__device__ __forceinline__ int find_item(const T* offs, int n, T v) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // Reduce one coordinate: x -> x - floor(x) in [0, 1] (exact for Eq. 5, which
 // is 1-periodic), u = n x, cell c = floor(u) in [0, n), offset u - c in FP64,
@@ -38,21 +54,26 @@ __device__ __forceinline__ double load_coord(const double* x, int64_t j, int d, 
 }
 
 template <typename Real>
-__global__ void k_bin_count(const double* __restrict__ x, int64_t M, GridGeom g, int* __restrict__ bin_count,
-                            int2* __restrict__ bin_rank, int* __restrict__ err) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = j < M;
+__global__ void k_bin_count(SortArgs s, int* __restrict__ bin_count, int2* __restrict__ bin_rank) {
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = gidx < s.total_points;
   int bin = -1;
   if (valid) {
+    const int item = find_item<int64_t>(s.point_offsets, s.n_items, gidx);
+    const ItemDev& it = s.items[item];
+    const int64_t j = gidx - it.point_offset;
+    const double* x = s.x_override ? s.x_override : it.x;
+    const GridGeom& g = it.geom;
     bool bad = false;
-    bin = 0;
+    int local = 0;
     for (int t = 0; t < g.d; ++t) {
       int c;
       Real dl;
       reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
-      bin = bin * g.nbins[t] + c / g.bin[t];
+      local = local * g.nbins[t] + c / g.bin[t];
     }
-    if (bad) atomicOr(err, 1);
+    if (bad) atomicOr(s.err, 1);
+    bin = it.bin_offset + local;
   }
   // warp-aggregated rank: lanes with the same bin share one atomic
   const unsigned peers = __match_any_sync(0xffffffffu, bin);
@@ -61,16 +82,20 @@ __global__ void k_bin_count(const double* __restrict__ x, int64_t M, GridGeom g,
   int base = 0;
   if (valid && lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
   base = __shfl_sync(peers, base, leader);
-  if (valid) bin_rank[j] = make_int2(bin, base + __popc(peers & ((1u << lane) - 1u)));
+  if (valid) bin_rank[gidx] = make_int2(bin, base + __popc(peers & ((1u << lane) - 1u)));
 }
 
 template <typename Real>
-__global__ void k_scatter(const double* __restrict__ x, int64_t M, GridGeom g, const int* __restrict__ bin_start,
-                          const int2* __restrict__ bin_rank, int* __restrict__ perm, uint32_t* __restrict__ local,
-                          Real* d0, Real* d1, Real* d2) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const int2 br = bin_rank[j];
+__global__ void k_scatter(SortArgs s, const int* __restrict__ bin_start, const int2* __restrict__ bin_rank,
+                          int* __restrict__ perm, uint32_t* __restrict__ local, Real* d0, Real* d1, Real* d2) {
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= s.total_points) return;
+  const int item = find_item<int64_t>(s.point_offsets, s.n_items, gidx);
+  const ItemDev& it = s.items[item];
+  const int64_t j = gidx - it.point_offset;
+  const double* x = s.x_override ? s.x_override : it.x;
+  const GridGeom& g = it.geom;
+  const int2 br = bin_rank[gidx];
   const int pos = bin_start[br.x] + br.y;
   bool bad = false;
   uint32_t packed = 0;
@@ -122,19 +147,22 @@ __global__ void k_sub_count(const int* __restrict__ bin_count, int nbins, int P,
   if (b < nbins) sub_count[b] = (bin_count[b] + P - 1) / P;
 }
 
-__global__ void k_sub_fill(const int* __restrict__ bin_count, const int* __restrict__ bin_start,
-                           const int* __restrict__ sub_start, int nbins, int P, SubProblem* __restrict__ subs) {
+__global__ void k_sub_fill(SortArgs s, const int* __restrict__ bin_count, const int* __restrict__ bin_start,
+                           const int* __restrict__ sub_start, int P, SubProblem* __restrict__ subs) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbins) return;
+  if (b >= s.total_bins) return;
   const int cnt = bin_count[b];
+  if (cnt == 0) return;
+  const int item = find_item<int>(s.bin_offsets, s.n_items, b);
+  const int local_bin = b - s.bin_offsets[item];
   const int s0 = sub_start[b];
-  for (int s = 0, off = 0; off < cnt; ++s, off += P) {
+  for (int k = 0, off = 0; off < cnt; ++k, off += P) {
     SubProblem sp;
-    sp.bin = b;
+    sp.bin = local_bin;
     sp.start = bin_start[b] + off;
     sp.count = min(P, cnt - off);
-    sp.pad_ = 0;
-    subs[s0 + s] = sp;
+    sp.item = item;
+    subs[s0 + k] = sp;
   }
 }
 
@@ -143,10 +171,9 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 template <typename Real>
-cudaError_t launch_bin_count(const double* x, int64_t M, const GridGeom& g, int* bin_count, int2* bin_rank, int* err,
-                             cudaStream_t st) {
-  if (M == 0) return cudaSuccess;
-  k_bin_count<Real><<<blocks_for(M, 256), 256, 0, st>>>(x, M, g, bin_count, bin_rank, err);
+cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st) {
+  if (s.total_points == 0) return cudaSuccess;
+  k_bin_count<Real><<<blocks_for(s.total_points, 256), 256, 0, st>>>(s, bin_count, bin_rank);
   return cudaGetLastError();
 }
 
@@ -156,11 +183,11 @@ cudaError_t launch_scan(const int* in, int* out, int n, int* total, cudaStream_t
 }
 
 template <typename Real>
-cudaError_t launch_scatter(const double* x, int64_t M, const GridGeom& g, const int* bin_start, const int2* bin_rank,
-                           int* perm, uint32_t* local, Real* const* delta, cudaStream_t st) {
-  if (M == 0) return cudaSuccess;
-  k_scatter<Real><<<blocks_for(M, 256), 256, 0, st>>>(x, M, g, bin_start, bin_rank, perm, local, delta[0], delta[1],
-                                                      delta[2]);
+cudaError_t launch_scatter(const SortArgs& s, const int* bin_start, const int2* bin_rank, int* perm, uint32_t* local,
+                           Real* const* delta, cudaStream_t st) {
+  if (s.total_points == 0) return cudaSuccess;
+  k_scatter<Real><<<blocks_for(s.total_points, 256), 256, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0],
+                                                                   delta[1], delta[2]);
   return cudaGetLastError();
 }
 
@@ -169,17 +196,17 @@ cudaError_t launch_subproblem_count(const int* bin_count, int nbins, int P, int*
   return cudaGetLastError();
 }
 
-cudaError_t launch_subproblem_fill(const int* bin_count, const int* bin_start, const int* sub_start, int nbins, int P,
-                                   SubProblem* subs, cudaStream_t st) {
-  k_sub_fill<<<blocks_for(nbins, 256), 256, 0, st>>>(bin_count, bin_start, sub_start, nbins, P, subs);
+cudaError_t launch_subproblem_fill(const SortArgs& s, const int* bin_count, const int* bin_start, const int* sub_start,
+                                   int P, SubProblem* subs, cudaStream_t st) {
+  k_sub_fill<<<blocks_for(s.total_bins, 256), 256, 0, st>>>(s, bin_count, bin_start, sub_start, P, subs);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_bin_count<float>(const double*, int64_t, const GridGeom&, int*, int2*, int*, cudaStream_t);
-template cudaError_t launch_bin_count<double>(const double*, int64_t, const GridGeom&, int*, int2*, int*, cudaStream_t);
-template cudaError_t launch_scatter<float>(const double*, int64_t, const GridGeom&, const int*, const int2*, int*,
-                                           uint32_t*, float* const*, cudaStream_t);
-template cudaError_t launch_scatter<double>(const double*, int64_t, const GridGeom&, const int*, const int2*, int*,
-                                            uint32_t*, double* const*, cudaStream_t);
+template cudaError_t launch_bin_count<float>(const SortArgs&, int*, int2*, cudaStream_t);
+template cudaError_t launch_bin_count<double>(const SortArgs&, int*, int2*, cudaStream_t);
+template cudaError_t launch_scatter<float>(const SortArgs&, const int*, const int2*, int*, uint32_t*, float* const*,
+                                           cudaStream_t);
+template cudaError_t launch_scatter<double>(const SortArgs&, const int*, const int2*, int*, uint32_t*,
+                                            double* const*, cudaStream_t);
 
 }  // namespace gbnfft

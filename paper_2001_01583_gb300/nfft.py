@@ -152,6 +152,96 @@ class Plan:
         return {s: (ms[i], n[i]) for i, s in enumerate(_lib.STAGES)}
 
 
+class Batch:
+    """Many independent transforms set up once and run together (one CUDA
+    graph launch per call).  items: list of dicts with keys N (tuple), M,
+    and optionally sigma, m, window, nrhs."""
+
+    def __init__(self, items, precision="fp32", stream=None, sigma=2.0, m=4, window="kaiser_bessel"):
+        self._lib = _lib.load()
+        self.precision = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.cdtype = torch.complex128 if self.precision == _lib.FP64 else torch.complex64
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (_lib.BatchItem * len(items))()
+        self.items = []
+        for i, it in enumerate(items):
+            N = tuple(int(v) for v in it["N"])
+            win = it.get("window", window)
+            win = _lib.WINDOWS[win] if isinstance(win, str) else int(win)
+            arr[i].d = len(N)
+            for t in range(3):
+                arr[i].N[t] = N[t] if t < len(N) else 1
+            arr[i].M = int(it["M"])
+            arr[i].sigma = float(it.get("sigma", sigma))
+            arr[i].m = int(it.get("m", m))
+            arr[i].window = win
+            arr[i].nrhs = int(it.get("nrhs", 1))
+            self.items.append(dict(N=N, M=int(it["M"]), nrhs=arr[i].nrhs))
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.nfft_batch_create(ctypes.byref(h), len(items), arr, self.precision,
+                                               _stream_handle(self.stream)), "nfft_batch_create")
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.nfft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _ptrs(tensors):
+        return (ctypes.c_void_p * len(tensors))(*[ctypes.c_void_p(t.data_ptr()) for t in tensors])
+
+    def set_points(self, xs):
+        """xs: list of (M_i, d_i) float64 CUDA tensors."""
+        xs = [x.contiguous() for x in xs]
+        self._x = xs
+        _lib.check(self._lib.nfft_batch_set_points(self._h, self._ptrs(xs)), "nfft_batch_set_points")
+
+    def adjoint(self, fs, outs=None):
+        """Eq. 5 for every item: fs[i] (nrhs_i, M_i) complex -> (nrhs_i,) + N_i."""
+        fs = [f.contiguous() for f in fs]
+        if outs is None:
+            outs = [torch.empty((it["nrhs"],) + it["N"], dtype=self.cdtype, device=self.device) for it in self.items]
+        self._keep = [fs, outs]
+        _lib.check(self._lib.nfft_batch_adjoint(self._h, self._ptrs(fs), self._ptrs(outs)), "nfft_batch_adjoint")
+        return outs
+
+    def forward(self, fhats, outs=None):
+        """Eq. 6 for every item: fhats[i] (nrhs_i,) + N_i -> (nrhs_i, M_i)."""
+        fhats = [h.contiguous() for h in fhats]
+        if outs is None:
+            outs = [torch.empty((it["nrhs"], it["M"]), dtype=self.cdtype, device=self.device) for it in self.items]
+        self._keep = [fhats, outs]
+        _lib.check(self._lib.nfft_batch_forward(self._h, self._ptrs(fhats), self._ptrs(outs)), "nfft_batch_forward")
+        return outs
+
+    def sync(self):
+        _lib.check(self._lib.nfft_batch_sync(self._h), "nfft_batch_sync")
+
+    def set_option(self, option, value):
+        _lib.check(self._lib.nfft_batch_set_option(self._h, int(option), int(value)), "nfft_batch_set_option")
+
+    def stage_times(self, reset=False):
+        ms = (ctypes.c_double * len(_lib.STAGES))()
+        n = (ctypes.c_int64 * len(_lib.STAGES))()
+        _lib.check(self._lib.nfft_batch_stage_times(self._h, ms, n, 1 if reset else 0), "nfft_batch_stage_times")
+        return {s: (ms[i], n[i]) for i, s in enumerate(_lib.STAGES)}
+
+
 def plan_params(N, sigma=2.0, m=4, window="kaiser_bessel"):
     """Host-only rule: oversampled sizes n_t and window taps per dimension."""
     lib = _lib.load()
