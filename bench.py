@@ -38,6 +38,10 @@ WORKLOADS = {
     "config": dict(N=(64, 64, 64), M=10 ** 6, sets=("uniform", "clustered"),
                    name="3-D adjoint+forward NFFT, N=64^3, M=10^6, uniform + clustered (32 clusters, std 0.02), "
                         "Kaiser-Bessel m=4, sigma=2, mixed FP32"),
+    "batch": dict(N=None, M=None, sets=("batch",),
+                  name="batched 3-D adjoint+forward NFFT: 512 transforms, N from {32^3, 64^3}, M log-uniform in "
+                       "[1e3, 1e5], plus one 64^3 point set with M=2e5 and 16 right-hand sides; Kaiser-Bessel m=4, "
+                       "sigma=2; one CUDA-graph launch per direction"),
     "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",),
                   name="3-D adjoint+forward NFFT, N=64^3, M=5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
                        "(profiling case: the same grid and bins, half the points, one set)"),
@@ -231,17 +235,24 @@ def run_ours(args, wl, rank, world):
     gens = {"uniform": lambda s: inputs.uniform_points(M, 3, seed=s),
             "clustered": lambda s: inputs.clustered_points(M, 3, 32, 0.02, seed=s)}
     xs_host = [gens[name](100 * rank + i) for i, name in enumerate(wl["sets"])]
-    f_host = inputs.complex_normal(M, seed=100 * rank + 7, dtype=np.complex64)
-    fh_host = inputs.complex_normal(N, seed=100 * rank + 8, dtype=np.complex64)
+    ctype = np.complex64 if args.precision == "fp32" else np.complex128
+    tctype = torch.complex64 if args.precision == "fp32" else torch.complex128
+    f_host = inputs.complex_normal(M, seed=100 * rank + 7, dtype=ctype)
+    fh_host = inputs.complex_normal(N, seed=100 * rank + 8, dtype=ctype)
 
     with torch.cuda.stream(stream):
         xs = [torch.from_numpy(x).to(dev) for x in xs_host]
         f = torch.from_numpy(f_host).to(dev)
         fh = torch.from_numpy(fh_host).to(dev)
-        outs_a = [torch.empty((1,) + N, dtype=torch.complex64, device=dev) for _ in xs]
-        outs_f = [torch.empty((1, M), dtype=torch.complex64, device=dev) for _ in xs]
+        outs_a = [torch.empty((1,) + N, dtype=tctype, device=dev) for _ in xs]
+        outs_f = [torch.empty((1, M), dtype=tctype, device=dev) for _ in xs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
-    plans = [Plan(N, M, SIGMA, MCUT, WINDOW, "fp32", stream=stream) for _ in xs]
+    plans = [Plan(N, M, SIGMA, MCUT, WINDOW, args.precision, stream=stream) for _ in xs]
+    if args.autotune:
+        with torch.cuda.stream(stream):
+            for p, x in zip(plans, xs):
+                p.set_points(x)
+                p.autotune(reps=3)
     for p in plans:
         p.set_option(_lib.OPT_PROFILE, 1)
 
@@ -340,8 +351,9 @@ def run_ours(args, wl, rank, world):
     launches_per_step = len(xs) * (6 + 2 + 2)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points_per_step,
+                       "precision": args.precision, "autotuned": bool(args.autotune),
                        "l2": "flushed between timed steps (512 MB write outside the step events)",
                        "parallelism": "independent replicas x%d" % world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -354,6 +366,75 @@ def run_ours(args, wl, rank, world):
     return 0
 
 
+def run_batch(args, wl, rank, world):
+    """The batch workload: every step is one adjoint and one forward graph
+    launch over all 513 items (independent problems per rank)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_01583_gb300 import Batch, _lib, inputs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.load()
+    stream = torch.cuda.Stream(dev)
+    ctype = np.complex64 if args.precision == "fp32" else np.complex128
+    items = inputs.batch_items(512, N_choices=(32, 64), M_lo=1000, M_hi=100000, d=3, seed=100 * rank)
+    items = [dict(N=it["N"], M=it["M"], nrhs=1, seed=it["seed"]) for it in items]
+    items.append(dict(N=(64, 64, 64), M=200000, nrhs=16, seed=100 * rank + 99))
+    with torch.cuda.stream(stream):
+        xs = [torch.from_numpy(inputs.uniform_points(it["M"], 3, seed=it["seed"])).to(dev) for it in items]
+        fs = [torch.from_numpy(inputs.complex_normal((it["nrhs"], it["M"]), seed=it["seed"] + 1, dtype=ctype)).to(dev)
+              for it in items]
+        hs = [torch.from_numpy(inputs.complex_normal((it["nrhs"],) + it["N"], seed=it["seed"] + 2,
+                                                     dtype=ctype)).to(dev) for it in items]
+        outs_a = [torch.empty_like(h) for h in hs]
+        outs_f = [torch.empty_like(f) for f in fs]
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b = Batch([dict(N=it["N"], M=it["M"], nrhs=it["nrhs"]) for it in items], args.precision, stream=stream)
+    with torch.cuda.stream(stream):
+        b.set_points(xs)
+        if args.autotune:
+            b.autotune(reps=3)
+        for _ in range(args.warmup):
+            b.adjoint(fs, outs_a)
+            b.forward(hs, outs_f)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            b.adjoint(fs, outs_a)
+            b.forward(hs, outs_f)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = float(np.sum([x.elapsed_time(y) for x, y in ev])) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = t.item()
+    points = 2 * sum(it["M"] * it["nrhs"] for it in items)
+    line = {"metric": METRIC, "value": points * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "points_per_step_per_gpu": points, "items": len(items),
+                       "precision": args.precision, "autotuned": bool(args.autotune),
+                       "l2": "flushed between timed steps (512 MB write outside the step events)"},
+            "gpu_launches": None, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +443,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--autotune", action="store_true", help="run the library's autotuner before timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -369,6 +452,8 @@ def main():
     rank = _env_int("RANK", 0)
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, wl, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

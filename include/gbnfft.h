@@ -90,7 +90,9 @@ typedef enum {
   NFFT_OPT_MAX_SUBPROBLEM = 4,  /* points per subproblem (0 = default) */
   NFFT_OPT_RHS_CAPACITY = 5,    /* grids kept for right-hand sides processed together */
   NFFT_OPT_PROFILE = 6,         /* 1: record CUDA events around every stage */
-  NFFT_OPT_THREADS = 7          /* threads per block of the point kernels (0 = default) */
+  NFFT_OPT_THREADS = 7,         /* threads per block of the point kernels (0 = default) */
+  NFFT_OPT_SPREAD_THREADS = 8,  /* threads per block of spreading only (overrides 7) */
+  NFFT_OPT_INTERP_THREADS = 9   /* threads per block of interpolation only (overrides 7) */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -121,6 +123,9 @@ typedef struct {
   int threads;               /* threads per block of the point kernels */
   int64_t device_bytes;      /* device memory held by the plan (grids, sort buffers, tables) */
   double sigma[3];           /* actual n_t / N_t */
+  int max_subproblem;        /* points per subproblem in use */
+  int spread_threads;        /* NFFT_OPT_SPREAD_THREADS (0 = chosen per launch) */
+  int interp_threads;        /* NFFT_OPT_INTERP_THREADS (0 = chosen per launch) */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling
@@ -213,6 +218,14 @@ int nfft_get_info(const nfft_plan* plan, nfft_plan_info* info);
  * last reset; reset != 0 clears the totals afterwards. */
 int nfft_stage_times(nfft_plan* plan, double* ms, int64_t* launches, int reset);
 
+/* Autotuner: with the points set, time adjoint + forward for candidate
+ * layouts -- bin edges, points per subproblem, then the threads per block of
+ * spreading and of interpolation -- on synthetic values (median of `reps`
+ * runs each, CUDA events) and keep the fastest.  Sets the points again for
+ * the winner; allocates temporary buffers during the call.  *best_ms (may be
+ * NULL) gets the winner's adjoint + forward milliseconds. */
+int nfft_autotune(nfft_plan* plan, int reps, double* best_ms);
+
 /* Host-only parameter rule (no device needed): the oversampled size n_t for
  * each of the d bandwidths and the number of window taps per dimension. */
 int nfft_plan_params(int d, const int64_t* N, double sigma, int m, int window, int64_t* n_out, int* taps_out);
@@ -265,6 +278,9 @@ int nfft_batch_sync(nfft_batch* batch);
  * available: a batch fixes each item's right-hand sides).  Layout options
  * require nfft_batch_set_points again. */
 int nfft_batch_set_option(nfft_batch* batch, int option, int64_t value);
+
+/* The autotuner of nfft_autotune for a batch (whole-batch graph timings). */
+int nfft_batch_autotune(nfft_batch* batch, int reps, double* best_ms);
 
 /* Stage times with NFFT_OPT_PROFILE on: a whole adjoint graph is booked as
  * NFFT_STAGE_SPREAD, a whole forward graph as NFFT_STAGE_INTERP. */

@@ -31,7 +31,8 @@ FP32_MIXED = 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
 
 METHOD_AUTO, METHOD_TILED, METHOD_GLOBAL, METHOD_WARP = 0, 1, 2, 3
-OPT_METHOD, OPT_BIN_0, OPT_BIN_1, OPT_BIN_2, OPT_MAX_SUBPROBLEM, OPT_RHS_CAPACITY, OPT_PROFILE, OPT_THREADS = range(8)
+(OPT_METHOD, OPT_BIN_0, OPT_BIN_1, OPT_BIN_2, OPT_MAX_SUBPROBLEM, OPT_RHS_CAPACITY, OPT_PROFILE, OPT_THREADS,
+ OPT_SPREAD_THREADS, OPT_INTERP_THREADS) = range(10)
 STAGES = ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp")
 
 
@@ -52,6 +53,9 @@ class PlanInfo(ctypes.Structure):
         ("threads", ctypes.c_int),
         ("device_bytes", ctypes.c_int64),
         ("sigma", ctypes.c_double * 3),
+        ("max_subproblem", ctypes.c_int),
+        ("spread_threads", ctypes.c_int),
+        ("interp_threads", ctypes.c_int),
     ]
 
 
@@ -105,6 +109,8 @@ def _declare(lib):
         "nfft_batch_adjoint": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "nfft_batch_forward": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "nfft_batch_sync": (ctypes.c_int, [vp]),
+        "nfft_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "nfft_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "nfft_batch_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
         "nfft_batch_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), i64p, ctypes.c_int]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),

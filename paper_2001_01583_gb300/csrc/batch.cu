@@ -69,6 +69,11 @@ int nfft_batch_forward(nfft_batch* p, const void* const* fhat_dev, void* const* 
   return p->eng.forward_batch(fhat_dev, f_dev);
 }
 
+int nfft_batch_autotune(nfft_batch* p, int reps, double* best_ms) {
+  if (!p) return NFFT_ERR_INVALID_ARG;
+  return p->eng.autotune(reps, best_ms);
+}
+
 int nfft_batch_sync(nfft_batch* p) {
   if (!p) return NFFT_ERR_INVALID_ARG;
   return p->eng.sync();

@@ -1,118 +1,173 @@
-// Scaling kernels of Section 2, for every item of a batch in one launch
-// (blockIdx.y = item).
+// Scaling kernels of Section 2, for every item of a batch in one launch.
 //   adjoint step 3 ("scale", Algorithm 2): fhat(k) = ghat(k) / c_k(phi~), k in I_N,
 //     read from the oversampled spectrum at array index k mod n (crop);
 //   forward step 1 ("subdivide", Algorithm 5): ghat(k) = fhat(k) / c_k(phi~)
 //     on I_N and 0 on I_n \ I_N, written over the whole grid.
-// 1 / c_k is a product of per-dimension FP64 tables; the product is formed in
-// FP64 and rounded once to the data precision.
+// Work is cut into rows of the last (contiguous) dimension: a block of
+// kRowThreads x kRowsPerBlock threads takes kRowsPerBlock rows, decodes each
+// row's leading indices once and forms the product of their FP64 scaling
+// factors once; the threads then walk the row.  The blocks of all items form
+// one flat range (block_offsets: prefix sums of each item's blocks); a block
+// finds its item by binary search.  1 / c_k is a product of per-dimension
+// FP64 tables, formed in FP64 and rounded once to the data precision.
 #include "kernels.h"
 
 namespace gbnfft {
 
 namespace {
 
-template <typename Real>
-__global__ void k_deconv_crop(const ItemDev* __restrict__ items, void* out_override, int nrhs_override) {
-  using C = typename Cplx<Real>::type;
-  const ItemDev& it = items[blockIdx.y];
-  const int nrhs = out_override ? nrhs_override : it.nrhs;
-  C* fhat = static_cast<C*>(out_override ? out_override : it.out);
-  const C* grid = static_cast<const C*>(it.grid);
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= it.NN * nrhs) return;
-  const int d = it.geom.d;
-  const int r = (int)(e / it.NN);
-  int64_t rem = e - (int64_t)r * it.NN;
-  int a[kMaxDim];
-  for (int t = d - 1; t >= 0; --t) {
-    a[t] = (int)(rem % it.N[t]);
-    rem /= it.N[t];
+// This block's item and its first row (single item when offs is null).
+__device__ __forceinline__ int block_item(const int* offs, int n_items, int64_t& first_row) {
+  if (!offs) {
+    first_row = (int64_t)blockIdx.x * kRowsPerBlock;
+    return 0;
   }
-  int64_t flat = 0;
-  double factor = 1.0;
-  for (int t = 0; t < d; ++t) {
-    const int k = a[t] - it.N[t] / 2;          // k_t in [-N_t/2, N_t/2)
-    flat = flat * it.geom.n[t] + (k < 0 ? k + it.geom.n[t] : k);
-    factor *= it.inv_c[t][a[t]];
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = n_items;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid] <= b) lo = mid;
+    else hi = mid;
   }
-  const C g = grid[(int64_t)r * it.geom.grid_cells + flat];
-  const Real f = (Real)factor;
-  C o;
-  o.x = g.x * f;
-  o.y = g.y * f;
-  fhat[e] = o;
+  first_row = (int64_t)(b - offs[lo]) * kRowsPerBlock;
+  return lo;
+}
+
+// Leading indices of a row: row = (r * R0 + i0) * R1 + i1 over (rhs, dims < d-1).
+__device__ __forceinline__ void decode_row(int64_t row, int d, const int* ext, int& r, int* idx) {
+  int64_t rem = row;
+  for (int t = d - 2; t >= 0; --t) {
+    idx[t] = (int)(rem % ext[t]);
+    rem /= ext[t];
+  }
+  r = (int)rem;
 }
 
 template <typename Real>
-__global__ void k_pad_deconv(const ItemDev* __restrict__ items, const void* in_override, int nrhs_override) {
+__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+    k_deconv_crop(const ItemDev* __restrict__ items, const int* __restrict__ offs, int n_items, void* out_override,
+                  int nrhs_override) {
   using C = typename Cplx<Real>::type;
-  const ItemDev& it = items[blockIdx.y];
+  int64_t first_row;
+  const ItemDev& it = items[block_item(offs, n_items, first_row)];
+  const int nrhs = out_override ? nrhs_override : it.nrhs;
+  C* fhat = static_cast<C*>(out_override ? out_override : it.out);
+  const C* grid = static_cast<const C*>(it.grid);
+  const int d = it.geom.d;
+  const int Nl = it.N[d - 1], nl = it.geom.n[d - 1];
+  int64_t rows_per_rhs = 1;
+  for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.N[t];
+  const int64_t row = first_row + threadIdx.y;
+  if (row >= rows_per_rhs * nrhs) return;
+  int r, a[kMaxDim];
+  decode_row(row, d, it.N, r, a);
+  // grid row of the leading k's (k mod n) and their factor
+  int64_t grow = 0;
+  double lead = 1.0;
+  for (int t = 0; t < d - 1; ++t) {
+    const int k = a[t] - it.N[t] / 2;
+    grow = grow * it.geom.n[t] + (k < 0 ? k + it.geom.n[t] : k);
+    lead *= it.inv_c[t][a[t]];
+  }
+  const C* src = grid + (int64_t)r * it.geom.grid_cells + grow * nl;
+  C* dst = fhat + row * Nl;
+  const double* cl = it.inv_c[d - 1];
+  for (int x = threadIdx.x; x < Nl; x += kRowThreads) {
+    const int k = x - Nl / 2;
+    const C g = src[k < 0 ? k + nl : k];
+    const Real f = (Real)(lead * cl[x]);
+    C o;
+    o.x = g.x * f;
+    o.y = g.y * f;
+    dst[x] = o;
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+    k_pad_deconv(const ItemDev* __restrict__ items, const int* __restrict__ offs, int n_items,
+                 const void* in_override, int nrhs_override) {
+  using C = typename Cplx<Real>::type;
+  int64_t first_row;
+  const ItemDev& it = items[block_item(offs, n_items, first_row)];
   const int nrhs = in_override ? nrhs_override : it.nrhs;
   const C* fhat = static_cast<const C*>(in_override ? in_override : it.in);
   C* grid = static_cast<C*>(it.grid);
-  const int64_t cells = it.geom.grid_cells;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= cells * nrhs) return;
   const int d = it.geom.d;
-  const int r = (int)(e / cells);
-  int64_t rem = e - (int64_t)r * cells;
-  int l[kMaxDim];
-  for (int t = d - 1; t >= 0; --t) {
-    l[t] = (int)(rem % it.geom.n[t]);
-    rem /= it.geom.n[t];
-  }
+  const int Nl = it.N[d - 1], nl = it.geom.n[d - 1];
+  int64_t rows_per_rhs = 1;
+  for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.geom.n[t];
+  const int64_t row = first_row + threadIdx.y;
+  if (row >= rows_per_rhs * nrhs) return;
+  int r, l[kMaxDim];
+  decode_row(row, d, it.geom.n, r, l);
+  // the row's leading k's: inside I_N or not, their fhat row and factor
   bool inside = true;
-  int64_t flat = 0;
-  double factor = 1.0;
-  for (int t = 0; t < d; ++t) {
+  int64_t hrow = 0;
+  double lead = 1.0;
+  for (int t = 0; t < d - 1; ++t) {
     const int half = it.N[t] / 2;
     int k;
     if (l[t] < half) k = l[t];
     else if (l[t] >= it.geom.n[t] - half) k = l[t] - it.geom.n[t];
-    else { inside = false; break; }
+    else {
+      inside = false;
+      break;
+    }
     const int a = k + half;
-    flat = flat * it.N[t] + a;
-    factor *= it.inv_c[t][a];
+    hrow = hrow * it.N[t] + a;
+    lead *= it.inv_c[t][a];
   }
-  C o;
-  if (inside) {
-    const C h = fhat[(int64_t)r * it.NN + flat];
-    const Real f = (Real)factor;
-    o.x = h.x * f;
-    o.y = h.y * f;
-  } else {
-    o.x = (Real)0;
-    o.y = (Real)0;
+  C* dst = grid + row * nl;
+  const C zero = cmake<C>(0.0, 0.0);
+  if (!inside) {
+    for (int x = threadIdx.x; x < nl; x += kRowThreads) dst[x] = zero;
+    return;
   }
-  grid[e] = o;
+  const C* src = fhat + ((int64_t)r * (it.NN / Nl) + hrow) * Nl;
+  const double* cl = it.inv_c[d - 1];
+  const int half = Nl / 2;
+  for (int x = threadIdx.x; x < nl; x += kRowThreads) {
+    int a = -1;
+    if (x < half) a = x + half;
+    else if (x >= nl - half) a = x - nl + half;
+    C o = zero;
+    if (a >= 0) {
+      const C h = src[a];
+      const Real f = (Real)(lead * cl[a]);
+      o.x = h.x * f;
+      o.y = h.y * f;
+    }
+    dst[x] = o;
+  }
 }
 
 }  // namespace
 
+int64_t scale_blocks(int64_t rows) { return (rows + kRowsPerBlock - 1) / kRowsPerBlock; }
+
 template <typename Real>
-cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
-                               int nrhs, cudaStream_t st) {
-  (void)in;
-  if (max_elems <= 0 || n_items <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((max_elems + 255) / 256), (unsigned)n_items);
-  k_deconv_crop<Real><<<grid, 256, 0, st>>>(items, out, nrhs);
+cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+                               void* out, int nrhs, cudaStream_t st) {
+  if (blocks <= 0 || n_items <= 0) return cudaSuccess;
+  k_deconv_crop<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets, n_items,
+                                                                                     out, nrhs);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
-                              int nrhs, cudaStream_t st) {
-  (void)out;
-  if (max_elems <= 0 || n_items <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((max_elems + 255) / 256), (unsigned)n_items);
-  k_pad_deconv<Real><<<grid, 256, 0, st>>>(items, in, nrhs);
+cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+                              const void* in, int nrhs, cudaStream_t st) {
+  if (blocks <= 0 || n_items <= 0) return cudaSuccess;
+  k_pad_deconv<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets, n_items,
+                                                                                    in, nrhs);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_deconv_crop<float>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
-template cudaError_t launch_deconv_crop<double>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<float>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<double>(const ItemDev*, int, int64_t, const void*, void*, int, cudaStream_t);
+template cudaError_t launch_deconv_crop<float>(const ItemDev*, int, const int*, int64_t, void*, int, cudaStream_t);
+template cudaError_t launch_deconv_crop<double>(const ItemDev*, int, const int*, int64_t, void*, int, cudaStream_t);
+template cudaError_t launch_pad_deconv<float>(const ItemDev*, int, const int*, int64_t, const void*, int, cudaStream_t);
+template cudaError_t launch_pad_deconv<double>(const ItemDev*, int, const int*, int64_t, const void*, int,
+                                               cudaStream_t);
 
 }  // namespace gbnfft

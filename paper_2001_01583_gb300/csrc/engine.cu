@@ -303,6 +303,8 @@ int Engine::build_fft() {
 int Engine::release_layout() {
   free_dev(d_point_offsets);
   free_dev(d_bin_offsets);
+  free_dev(d_crop_blocks);
+  free_dev(d_pad_blocks);
   free_dev(bin_count);
   free_dev(bin_start);
   free_dev(sub_count);
@@ -376,8 +378,11 @@ int Engine::build_layout() {
     c.method = method;
   }
   // group items into kernel classes (stable by first appearance)
+  // (items with different right-hand-side counts get their own launch: the
+  // right-hand sides per pass size the shared memory of the whole launch)
   auto same = [&](int a, int b) {
     return specs[a].d == specs[b].d && ch[a].taps == ch[b].taps && specs[a].window == specs[b].window &&
+           (single || specs[a].nrhs == specs[b].nrhs) &&
            ch[a].method == ch[b].method && ch[a].bin[0] == ch[b].bin[0] && ch[a].bin[1] == ch[b].bin[1] &&
            ch[a].bin[2] == ch[b].bin[2];
   };
@@ -511,6 +516,22 @@ int Engine::build_layout() {
   const size_t rsize = precision == NFFT_FP64 ? 8 : 4;
   for (int t = 0; t < dmax; ++t) TRY(alloc_dev(delta[t], rsize * P, device_bytes));
   layout_bytes = device_bytes - before;
+  {
+    std::vector<int> cb(nitems + 1, 0), pb(nitems + 1, 0);
+    for (int k = 0; k < nitems; ++k) {
+      const ItemDev& it = items[k];
+      const int dl = it.geom.d - 1;
+      cb[k + 1] = cb[k] + (int)scale_blocks(it.NN / it.N[dl] * it.nrhs);
+      pb[k + 1] = pb[k] + (int)scale_blocks(it.geom.grid_cells / it.geom.n[dl] * it.nrhs);
+    }
+    crop_blocks = cb[nitems];
+    pad_blocks = pb[nitems];
+    TRY(alloc_dev(d_crop_blocks, sizeof(int) * (nitems + 1), device_bytes));
+    TRY(alloc_dev(d_pad_blocks, sizeof(int) * (nitems + 1), device_bytes));
+    layout_bytes += (int64_t)(2 * sizeof(int) * (nitems + 1));
+    CK(cudaMemcpy(d_crop_blocks, cb.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_pad_blocks, pb.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(d_point_offsets, pts_off.data(), sizeof(int64_t) * (nitems + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_bin_offsets, bin_off.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
   CK(cudaMemset(num_subs, 0, sizeof(int)));
@@ -669,8 +690,11 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
   int best_nw = 0, best_warps = 0;
   size_t best_smem = 0;
   const void* best_fn = nullptr;
+  const int topt = (spread ? spread_threads_opt : interp_threads_opt) > 0
+                       ? (spread ? spread_threads_opt : interp_threads_opt)
+                       : threads_opt;
   for (int nw = 1; nw <= 8; nw *= 2) {
-    if (threads_opt > 0 && 32 * nw != threads_opt) continue;
+    if (topt > 0 && 32 * nw != topt) continue;
     const void* fn = planes_kernel<Real>(W, nw, spread);
     if (!fn) continue;
     const size_t smem = smem_of(nw, np);
@@ -753,7 +777,10 @@ int Engine::run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, i
   if (pass > max_nrhs) pass = max_nrhs;
   a.rhs_per_pass = pass;
   const size_t smem = one * (size_t)pass;
-  const int threads = threads_opt > 0 ? threads_opt : 256;
+  const int topt = (spread ? spread_threads_opt : interp_threads_opt) > 0
+                       ? (spread ? spread_threads_opt : interp_threads_opt)
+                       : threads_opt;
+  const int threads = topt > 0 ? topt : 256;
   int per_sm = blocks_per_sm(fn, threads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)per_sm * num_sms;
@@ -808,6 +835,7 @@ int Engine::set_points_impl(const double* x_override) {
 
 int Engine::set_points_single(const double* x) {
   points_set = false;
+  last_x = x;
   const int s = precision == NFFT_FP64 ? set_points_impl<double>(x) : set_points_impl<float>(x);
   if (s == NFFT_OK) points_set = true;
   return s;
@@ -815,6 +843,7 @@ int Engine::set_points_single(const double* x) {
 
 int Engine::set_points_batch(const double* const* x) {
   points_set = false;
+  batch_x.assign(x, x + specs.size());
   for (size_t k = 0; k < items.size(); ++k) {
     items[k].x = x[order[k]];
     if (!items[k].x && items[k].M > 0) return NFFT_ERR_INVALID_ARG;
@@ -854,8 +883,9 @@ int Engine::adjoint_single(const void* f, void* fhat, int R) {
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
     void* out = static_cast<char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, 1, it.NN * nr, nullptr, out, nr, stream)
-                              : launch_deconv_crop<float>(d_items, 1, it.NN * nr, nullptr, out, nr, stream));
+    const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr);
+    CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, 1, nullptr, cblocks, out, nr, stream)
+                              : launch_deconv_crop<float>(d_items, 1, nullptr, cblocks, out, nr, stream));
     TRY(stage_end(&ev));
   }
   return NFFT_OK;
@@ -869,8 +899,9 @@ int Engine::forward_single(const void* fhat, void* f, int R) {
     EventPair ev{};
     TRY(stage_begin(NFFT_STAGE_PAD, &ev));
     const void* hin = static_cast<const char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, 1, fc.cells * nr, hin, nullptr, nr, stream)
-                              : launch_pad_deconv<float>(d_items, 1, fc.cells * nr, hin, nullptr, nr, stream));
+    const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr);
+    CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, 1, nullptr, pblocks, hin, nr, stream)
+                              : launch_pad_deconv<float>(d_items, 1, nullptr, pblocks, hin, nr, stream));
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
     TRY(run_fft(fc, nr, item_grid_offset[0], CUFFT_INVERSE));
@@ -901,9 +932,7 @@ int Engine::adjoint_table(bool in_graph) {
   for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_FORWARD));
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
-  int64_t max_elems = 0;
-  for (const auto& it : items) max_elems = std::max(max_elems, it.NN * it.nrhs);
-  CK(launch_deconv_crop<Real>(d_items, (int)items.size(), max_elems, nullptr, nullptr, 0, stream));
+  CK(launch_deconv_crop<Real>(d_items, (int)items.size(), d_crop_blocks, crop_blocks, nullptr, 0, stream));
   if (!in_graph) TRY(stage_end(&ev));
   return NFFT_OK;
 }
@@ -912,9 +941,7 @@ template <typename Real>
 int Engine::forward_table(bool in_graph) {
   EventPair ev{};
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_PAD, &ev));
-  int64_t max_elems = 0;
-  for (const auto& it : items) max_elems = std::max(max_elems, it.geom.grid_cells * it.nrhs);
-  CK(launch_pad_deconv<Real>(d_items, (int)items.size(), max_elems, nullptr, nullptr, 0, stream));
+  CK(launch_pad_deconv<Real>(d_items, (int)items.size(), d_pad_blocks, pad_blocks, nullptr, 0, stream));
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
   for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_INVERSE));
@@ -1143,8 +1170,12 @@ int Engine::set_option(int option, int64_t value) {
       profile = value != 0;
       return NFFT_OK;
     case NFFT_OPT_THREADS:
+    case NFFT_OPT_SPREAD_THREADS:
+    case NFFT_OPT_INTERP_THREADS:
       if (value != 0 && (value < 32 || value > 256 || value % 32 != 0)) return NFFT_ERR_INVALID_ARG;
-      threads_opt = (int)value;
+      (option == NFFT_OPT_THREADS ? threads_opt
+                                  : (option == NFFT_OPT_SPREAD_THREADS ? spread_threads_opt : interp_threads_opt)) =
+          (int)value;
       return NFFT_OK;
     default:
       return NFFT_ERR_INVALID_ARG;
@@ -1175,7 +1206,179 @@ int Engine::info(nfft_plan_info* out) const {
   out->rhs_capacity = single ? rhs_cap : s.nrhs;
   out->threads = threads_opt;
   out->device_bytes = device_bytes;
+  out->max_subproblem = max_sub;
+  out->spread_threads = spread_threads_opt;
+  out->interp_threads = interp_threads_opt;
   return NFFT_OK;
+}
+
+// ===========================================================================
+// autotuner
+
+namespace {
+// Deterministic complex test values (a hash of the index): the timings do not
+// depend on the values, but zeros would skip work.
+template <typename Real>
+__global__ void k_fill_values(typename Cplx<Real>::type* v, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 32);
+  h ^= h >> 15;
+  h *= 2246822519u;
+  h ^= h >> 13;
+  const Real re = (Real)((h & 0xffff) / 32768.0 - 1.0);
+  const Real im = (Real)(((h >> 16) & 0xffff) / 32768.0 - 1.0);
+  v[i].x = re;
+  v[i].y = im;
+}
+}  // namespace
+
+int Engine::reset_points() {
+  if (single) return set_points_single(last_x);
+  const std::vector<const double*> xs = batch_x;
+  return set_points_batch(xs.data());
+}
+
+int Engine::time_transforms(int reps, const std::vector<void*>& fin, const std::vector<void*>& fout,
+                            const std::vector<void*>& hin, const std::vector<void*>& hout, double* ms) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  std::vector<float> t;
+  for (int r = 0; r < reps + 1; ++r) {   // the first run warms up (and captures the graphs)
+    CK(cudaEventRecord(a, stream));
+    if (single) {
+      TRY(adjoint_single(fin[0], hout[0], 1));
+      TRY(forward_single(hin[0], fout[0], 1));
+    } else {
+      TRY(adjoint_batch(const_cast<const void* const*>(fin.data()), hout.data()));
+      TRY(forward_batch(const_cast<const void* const*>(hin.data()), fout.data()));
+    }
+    CK(cudaEventRecord(b, stream));
+    CK(cudaEventSynchronize(b));
+    float e = 0.f;
+    CK(cudaEventElapsedTime(&e, a, b));
+    if (r > 0) t.push_back(e);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(t.begin(), t.end());
+  *ms = t.empty() ? 0.0 : (double)t[t.size() / 2];
+  return NFFT_OK;
+}
+
+int Engine::autotune(int reps, double* best_ms) {
+  if (!points_set) return NFFT_ERR_NOT_READY;
+  if (reps < 1) reps = 3;
+  const bool was_profiling = profile;
+  profile = false;
+  // test buffers per item (user order): values in, results out
+  std::vector<void*> fin(specs.size()), fout(specs.size()), hin(specs.size()), hout(specs.size());
+  std::vector<void*> owned;
+  int st = NFFT_OK;
+  int64_t dummy = 0;
+  for (size_t i = 0; i < specs.size() && st == NFFT_OK; ++i) {
+    const ItemSpec& s = specs[i];
+    int64_t NN = 1;
+    for (int t = 0; t < s.d; ++t) NN *= s.N[t];
+    const int64_t R = single ? 1 : s.nrhs;
+    void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+    const int64_t sizes[4] = {R * std::max<int64_t>(s.M, 1), R * std::max<int64_t>(s.M, 1), R * NN, R * NN};
+    for (int k = 0; k < 4 && st == NFFT_OK; ++k) {
+      st = alloc_dev(p[k], (size_t)sizes[k] * csize, dummy);
+      if (st == NFFT_OK) owned.push_back(p[k]);
+    }
+    if (st != NFFT_OK) break;
+    for (int k = 0; k < 4; k += 2) {
+      const int64_t n = sizes[k];
+      if (precision == NFFT_FP64)
+        k_fill_values<double><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(static_cast<double2*>(p[k]), n);
+      else
+        k_fill_values<float><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(static_cast<float2*>(p[k]), n);
+    }
+    fin[i] = p[0];
+    fout[i] = p[1];
+    hin[i] = p[2];
+    hout[i] = p[3];
+  }
+  int dmax = 1;
+  for (const auto& s : specs) dmax = std::max(dmax, s.d);
+  struct Cand {
+    int bin[3];
+    int P;
+  };
+  std::vector<Cand> cands;
+  const int Ps[2] = {1024, 256};
+  if (dmax == 3) {
+    const int bins[][3] = {{8, 8, 16}, {8, 8, 8}, {4, 8, 16}, {8, 16, 16}, {8, 8, 32}, {4, 4, 32}};
+    for (const auto& b : bins)
+      for (int P : Ps) cands.push_back(Cand{{b[0], b[1], b[2]}, P});
+  } else if (dmax == 2) {
+    const int bins[][2] = {{32, 32}, {16, 32}, {32, 64}, {64, 64}, {16, 16}};
+    for (const auto& b : bins)
+      for (int P : Ps) cands.push_back(Cand{{b[0], b[1], 0}, P});
+  } else {
+    for (int b : {1024, 256, 4096})
+      for (int P : Ps) cands.push_back(Cand{{b, 0, 0}, P});
+  }
+  const int save_bin[3] = {bin_opt[0], bin_opt[1], bin_opt[2]};
+  const int save_P = max_sub_opt;
+  double best = 1e30;
+  Cand best_c = cands[0];
+  int best_sw = 0, best_iw = 0;
+  for (const Cand& c : cands) {
+    if (st != NFFT_OK) break;
+    for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? c.bin[t] : 0;
+    max_sub_opt = c.P;
+    spread_threads_opt = interp_threads_opt = 0;
+    CK(cudaStreamSynchronize(stream));
+    if (build_layout() != NFFT_OK) continue;   // e.g. a tile that does not fit
+    if (reset_points() != NFFT_OK) continue;
+    double ms = 0;
+    if (time_transforms(reps, fin, fout, hin, hout, &ms) != NFFT_OK) continue;
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  // warps per block for spreading and for interpolation, on the best layout
+  for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? best_c.bin[t] : 0;
+  max_sub_opt = best_c.P;
+  spread_threads_opt = interp_threads_opt = 0;
+  if (st == NFFT_OK) {
+    CK(cudaStreamSynchronize(stream));
+    st = build_layout();
+    if (st == NFFT_OK) st = reset_points();
+  }
+  if (st == NFFT_OK && dmax >= 2) {
+    for (int pass = 0; pass < 2; ++pass) {
+      int& opt = pass == 0 ? spread_threads_opt : interp_threads_opt;
+      int keep = 0;
+      for (int th : {64, 128, 256}) {
+        opt = th;
+        drop_graphs();
+        double ms = 0;
+        if (time_transforms(reps, fin, fout, hin, hout, &ms) != NFFT_OK) {
+          cudaGetLastError();
+          continue;
+        }
+        if (ms < best) {
+          best = ms;
+          keep = th;
+        }
+      }
+      opt = keep;
+      (pass == 0 ? best_sw : best_iw) = keep;
+    }
+    drop_graphs();
+  }
+  (void)save_bin;
+  (void)save_P;
+  CK(cudaStreamSynchronize(stream));
+  for (void* p : owned) cudaFree(p);
+  profile = was_profiling;
+  if (best_ms) *best_ms = best;
+  return st;
 }
 
 }  // namespace gbnfft

@@ -80,6 +80,9 @@ class Engine {
   int ewald(const void* q, double L, double alpha, double* out3);
   int ewald_sum(const void* S, double L, double alpha, double* sum_dev);
   int info(nfft_plan_info* out) const;
+  // Time candidate layouts on the points already set and keep the fastest
+  // (see nfft_autotune).  best_ms: adjoint + forward time of the winner.
+  int autotune(int reps, double* best_ms);
 
   // exposed for the C ABI
   int precision = 0;
@@ -107,6 +110,9 @@ class Engine {
   int stage_end(EventPair* ev);
   int capture_graphs();
   void drop_graphs();
+  int reset_points();
+  int time_transforms(int reps, const std::vector<void*>& fin, const std::vector<void*>& fout,
+                      const std::vector<void*>& hin, const std::vector<void*>& hout, double* ms);
 
   size_t csize = 16;
   int device = 0, num_sms = 1;
@@ -119,7 +125,11 @@ class Engine {
   int max_sub_opt = 0;
   int max_sub = 1024;
   int threads_opt = 0;
+  int spread_threads_opt = 0;
+  int interp_threads_opt = 0;
   int rhs_cap = 1;
+  const double* last_x = nullptr;      // single item: the points of the last set_points
+  std::vector<const double*> batch_x;  // batch: the points of the last set_points (user order)
   bool profile = false;
 
   // items (internal order: grouped by kernel class)
@@ -140,6 +150,9 @@ class Engine {
   int64_t max_subs_total = 0;
   int64_t* d_point_offsets = nullptr;
   int* d_bin_offsets = nullptr;
+  int* d_crop_blocks = nullptr;        // per-item block prefix sums of the scaling launches
+  int* d_pad_blocks = nullptr;
+  int64_t crop_blocks = 0, pad_blocks = 0;
   int* bin_count = nullptr;
   int* bin_start = nullptr;
   int* sub_count = nullptr;

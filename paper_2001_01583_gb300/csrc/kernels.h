@@ -101,14 +101,20 @@ size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile)
 // ---- scaling (deconv.cu) --------------------------------------------------
 // Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
 // Forward step 1 for every item: grid[r][l] = fhat[r][k] * inv_c(k) if l = k mod n, else 0.
-// One launch over all items (blockIdx.y = item); max_elems = max over items
-// of nrhs * |I_N| (crop) or nrhs * |I_n| (pad).  in/out/nrhs override the
-// item table when in != nullptr (single-item launches).
+// Work is cut into rows of the last dimension, kRowsPerBlock rows per block
+// of kRowThreads x kRowsPerBlock threads: an item has nrhs * |I_N| / N_last
+// rows to crop and nrhs * |I_n| / n_last rows to pad.  The blocks of all
+// items form one flat range of `blocks` blocks; block_offsets (device,
+// n_items + 1) are the prefix sums of each item's blocks (null for a single
+// item).  out / in and nrhs override the item table when non-null.
+constexpr int kRowThreads = 128;
+constexpr int kRowsPerBlock = 2;
+int64_t scale_blocks(int64_t rows);
 template <typename Real>
-cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
-                               int nrhs, cudaStream_t st);
+cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+                               void* out, int nrhs, cudaStream_t st);
 template <typename Real>
-cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, int64_t max_elems, const void* in, void* out,
-                              int nrhs, cudaStream_t st);
+cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+                              const void* in, int nrhs, cudaStream_t st);
 
 }  // namespace gbnfft

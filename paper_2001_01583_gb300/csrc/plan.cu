@@ -120,6 +120,11 @@ int nfft_ewald_reciprocal_sum(nfft_plan* p, const void* S_dev, double L, double 
   return p->eng.ewald_sum(S_dev, L, alpha, sum_dev);
 }
 
+int nfft_autotune(nfft_plan* p, int reps, double* best_ms) {
+  if (!p) return NFFT_ERR_INVALID_ARG;
+  return p->eng.autotune(reps, best_ms);
+}
+
 int nfft_sync(nfft_plan* p) {
   if (!p) return NFFT_ERR_INVALID_ARG;
   return p->eng.sync();

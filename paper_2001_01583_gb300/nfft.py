@@ -142,7 +142,16 @@ class Plan:
         return dict(d=inf.d, N=tuple(inf.N[:inf.d]), n=tuple(inf.n[:inf.d]), M=inf.M, m=inf.m, taps=inf.taps,
                     window=inf.window, precision=inf.precision, method=inf.method, bin=tuple(inf.bin[:inf.d]),
                     n_bins=inf.n_bins, rhs_capacity=inf.rhs_capacity, threads=inf.threads,
-                    device_bytes=inf.device_bytes, sigma=tuple(inf.sigma[:inf.d]))
+                    device_bytes=inf.device_bytes, sigma=tuple(inf.sigma[:inf.d]),
+                    max_subproblem=inf.max_subproblem, spread_threads=inf.spread_threads,
+                    interp_threads=inf.interp_threads)
+
+    def autotune(self, reps=3):
+        """Time candidate layouts on the points set and keep the fastest;
+        returns the winner's adjoint + forward milliseconds."""
+        ms = ctypes.c_double()
+        _lib.check(self._lib.nfft_autotune(self._h, int(reps), ctypes.byref(ms)), "nfft_autotune")
+        return ms.value
 
     def stage_times(self, reset=False):
         """Per-stage milliseconds and call counts (needs OPT_PROFILE on)."""
@@ -231,6 +240,11 @@ class Batch:
 
     def sync(self):
         _lib.check(self._lib.nfft_batch_sync(self._h), "nfft_batch_sync")
+
+    def autotune(self, reps=3):
+        ms = ctypes.c_double()
+        _lib.check(self._lib.nfft_batch_autotune(self._h, int(reps), ctypes.byref(ms)), "nfft_batch_autotune")
+        return ms.value
 
     def set_option(self, option, value):
         _lib.check(self._lib.nfft_batch_set_option(self._h, int(option), int(value)), "nfft_batch_set_option")

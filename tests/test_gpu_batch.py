@@ -131,3 +131,34 @@ def test_full_size_batch_workload_sampled():
             h = hs[i][r].cpu().numpy().astype(np.complex128)
             refb = ndft.forward(xs_np[i], h, N, jsel=js)
             assert ndft.rel_l2(B[i][r].cpu().numpy()[js], refb) <= 1e-6, (i, r)
+
+
+def test_autotuner_keeps_parity():
+    from paper_2001_01583_gb300 import Batch, Plan
+    N, M = (16, 16, 16), 30000
+    x = inputs.clustered_points(M, 3, 8, 0.03, seed=61)
+    f = inputs.complex_normal(M, seed=62)
+    fh = inputs.complex_normal(N, seed=63)
+    with Plan(N, M, 2.0, 4, "kaiser_bessel", "fp32") as p:
+        p.set_points(torch.from_numpy(x).cuda())
+        ms = p.autotune(reps=2)
+        info = p.info()
+        a = p.adjoint(torch.from_numpy(f).to(torch.complex64).cuda())
+        b = p.forward(torch.from_numpy(fh).to(torch.complex64).cuda())
+        p.sync()
+    assert ms > 0.0
+    assert info["max_subproblem"] in (256, 1024)
+    _elementwise(a.cpu().numpy(), S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL), FP32_ELEM)
+    _elementwise(b.cpu().numpy(), S.forward(x, fh, N, 2.0, 4, S.KAISER_BESSEL), FP32_ELEM)
+    items = ITEMS[:2]
+    xs = [inputs.uniform_points(it["M"], len(it["N"]), seed=70 + i) for i, it in enumerate(items)]
+    fs = [inputs.complex_normal((it["nrhs"], it["M"]), seed=80 + i) for i, it in enumerate(items)]
+    with Batch(items, "fp64") as bt:
+        bt.set_points([torch.from_numpy(v).cuda() for v in xs])
+        assert bt.autotune(reps=2) > 0.0
+        A = bt.adjoint([torch.from_numpy(v).cuda() for v in fs])
+        bt.sync()
+    for i, it in enumerate(items):
+        for r in range(it["nrhs"]):
+            _elementwise(A[i][r].cpu().numpy(), S.adjoint(xs[i], fs[i][r], it["N"], 2.0, it["m"], WIN[it["window"]]),
+                         1e-12)
