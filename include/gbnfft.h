@@ -286,6 +286,59 @@ int nfft_batch_autotune(nfft_batch* batch, int reps, double* best_ms);
  * NFFT_STAGE_SPREAD, a whole forward graph as NFFT_STAGE_INTERP. */
 int nfft_batch_stage_times(nfft_batch* batch, double* ms, int64_t* launches, int reset);
 
+/* ---- learned parameter picker ---------------------------------------------
+ * A small MLP, n_in -> n_hidden -> n_hidden -> n_out with ReLU, trained and
+ * run by the library's own kernels: FP16 weights (used by forward and
+ * backward), FP32 master weights (updated by Adam), FP32 accumulation.
+ * Loss: masked mean squared error sum mask (y - t)^2 / (2 sum mask).
+ * Parameters are flattened as W1 (n_hidden x n_in, row-major), b1, W2, b2,
+ * W3 (n_out x n_hidden), b3.  The paper has no such component: it is the
+ * parameter choice (sigma, m, window; Sections 2 and 4) made by a model. */
+typedef struct nfft_mlp nfft_mlp;
+
+#define NFFT_PICKER_FEATURES 8
+
+int nfft_mlp_create(nfft_mlp** out, int n_in, int n_hidden, int n_out, uint64_t seed, void* cuda_stream);
+int nfft_mlp_destroy(nfft_mlp* mlp);
+int nfft_mlp_num_params(const nfft_mlp* mlp, int64_t* n);
+/* Host FP32 parameters in / out (set_params also refreshes the FP16 copy and
+ * resets the Adam state; get_params with fp16_copy != 0 returns the FP16
+ * weights the kernels use, widened to float). */
+int nfft_mlp_set_params(nfft_mlp* mlp, const float* host);
+int nfft_mlp_get_params(nfft_mlp* mlp, float* host, int fp16_copy);
+/* y_dev (B x n_out) = network(x_dev (B x n_in)), device float arrays. */
+int nfft_mlp_forward(nfft_mlp* mlp, const float* x_dev, float* y_dev, int B);
+/* Gradient of the masked loss with respect to all parameters (FP32, device,
+ * n_params) and the loss (host float, may be NULL); no update. */
+int nfft_mlp_gradients(nfft_mlp* mlp, const float* x_dev, const float* t_dev, const float* mask_dev, int B,
+                       float* grad_dev, float* loss_host);
+/* One Adam step (beta 0.9 / 0.999) on a minibatch; loss_dev (device float,
+ * may be NULL) gets the minibatch loss before the step. */
+int nfft_mlp_train_step(nfft_mlp* mlp, const float* x_dev, const float* t_dev, const float* mask_dev, int B, float lr,
+                        float* loss_dev);
+
+/* Picker features of a problem: d, log2 N_0, log2 N_1, log2 N_2 (0 if
+ * unused), log10 M, cluster std (0 = uniform), log10 eps, log10(M / |I_N|). */
+int nfft_picker_features(int d, const int64_t* N, int64_t M, double cluster_std, double eps, double* features8);
+/* Attach the candidate table and the normalisation the network was trained
+ * with: n_out = 2 n_candidates; output c is the normalised predicted
+ * log10(error / eps) of candidate c, output n_candidates + c its normalised
+ * log10(cost); denormalised output = y * out_std + out_mean, normalised
+ * feature = (f - feat_mean) / feat_std.  A candidate qualifies when its
+ * predicted error is at most eps * err_margin (0 < err_margin <= 1). */
+int nfft_picker_configure(nfft_mlp* mlp, int n_candidates, const double* cand_sigma, const int* cand_m,
+                          const int* cand_window, const double* feat_mean, const double* feat_std,
+                          const double* out_mean, const double* out_std, double err_margin);
+/* The plain rule: Kaiser-Bessel, sigma = 2, m = ceil(ln(1/eps) / (2 pi sqrt(1 - 1/sigma))) in [2, 12]. */
+int nfft_rule_of_thumb(double eps, double* sigma, int* m, int* window);
+/* Choose (sigma, m, window) for a problem: the candidate with the lowest
+ * predicted cost among those valid for N and predicted to reach eps (see
+ * nfft_picker_configure);
+ * the rule of thumb (used_fallback = 1) when none qualifies or mlp is NULL
+ * or not configured.  Runs one forward pass on the device and waits. */
+int nfft_pick_params(nfft_mlp* mlp, int d, const int64_t* N, int64_t M, double cluster_std, double eps,
+                     double* sigma, int* m, int* window, int* used_fallback);
+
 /* Human-readable name of a status code (static string). */
 const char* nfft_status_string(int status);
 

@@ -113,6 +113,27 @@ def _declare(lib):
         "nfft_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "nfft_batch_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
         "nfft_batch_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), i64p, ctypes.c_int]),
+        "nfft_mlp_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_uint64, vp]),
+        "nfft_mlp_destroy": (ctypes.c_int, [vp]),
+        "nfft_mlp_num_params": (ctypes.c_int, [vp, i64p]),
+        "nfft_mlp_set_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "nfft_mlp_get_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+        "nfft_mlp_forward": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "nfft_mlp_gradients": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_float)]),
+        "nfft_mlp_train_step": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp]),
+        "nfft_picker_features": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                                ctypes.POINTER(ctypes.c_double)]),
+        "nfft_picker_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.c_double]),
+        "nfft_rule_of_thumb": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "nfft_pick_params": (ctypes.c_int, [vp, ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }
