@@ -3,20 +3,22 @@
 //     read from the oversampled spectrum at array index k mod n (crop);
 //   forward step 1 ("subdivide", Algorithm 5): ghat(k) = fhat(k) / c_k(phi~)
 //     on I_N and 0 on I_n \ I_N, written over the whole grid.
-// Work is cut into rows of the last (contiguous) dimension: a block of
-// kRowThreads x kRowsPerBlock threads takes kRowsPerBlock rows, decodes each
+// Work is cut into segments of rows of the last (contiguous) dimension (a
+// row longer than kSegment is cut into pieces): a block of kRowThreads x
+// kRowsPerBlock threads takes kRowsPerBlock segments, decodes each segment's
 // row's leading indices once and forms the product of their FP64 scaling
-// factors once; the threads then walk the row.  The blocks of all items form
-// one flat range (block_offsets: prefix sums of each item's blocks); a block
-// finds its item by binary search.  1 / c_k is a product of per-dimension
-// FP64 tables, formed in FP64 and rounded once to the data precision.
+// factors once; the threads then walk the segment.  The blocks of all items
+// form one flat range (block_offsets: prefix sums of each item's blocks); a
+// block finds its item by binary search.  1 / c_k is a product of
+// per-dimension FP64 tables, formed in FP64 and rounded once to the data
+// precision.
 #include "kernels.h"
 
 namespace gbnfft {
 
 namespace {
 
-// This block's item and its first row (single item when offs is null).
+// This block's item and its first segment (single item when offs is null).
 __device__ __forceinline__ int block_item(const int* offs, int n_items, int64_t& first_row) {
   if (!offs) {
     first_row = (int64_t)blockIdx.x * kRowsPerBlock;
@@ -57,8 +59,11 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   const int Nl = it.N[d - 1], nl = it.geom.n[d - 1];
   int64_t rows_per_rhs = 1;
   for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.N[t];
-  const int64_t row = first_row + threadIdx.y;
-  if (row >= rows_per_rhs * nrhs) return;
+  const int segs = (Nl + kSegment - 1) / kSegment;
+  const int64_t seg = first_row + threadIdx.y;
+  if (seg >= rows_per_rhs * nrhs * segs) return;
+  const int64_t row = segs == 1 ? seg : seg / segs;
+  const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(Nl, x0 + kSegment);
   int r, a[kMaxDim];
   decode_row(row, d, it.N, r, a);
   // grid row of the leading k's (k mod n) and their factor
@@ -72,7 +77,7 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   const C* src = grid + (int64_t)r * it.geom.grid_cells + grow * nl;
   C* dst = fhat + row * Nl;
   const double* cl = it.inv_c[d - 1];
-  for (int x = threadIdx.x; x < Nl; x += kRowThreads) {
+  for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
     const int k = x - Nl / 2;
     const C g = src[k < 0 ? k + nl : k];
     const Real f = (Real)(lead * cl[x]);
@@ -97,8 +102,11 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   const int Nl = it.N[d - 1], nl = it.geom.n[d - 1];
   int64_t rows_per_rhs = 1;
   for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.geom.n[t];
-  const int64_t row = first_row + threadIdx.y;
-  if (row >= rows_per_rhs * nrhs) return;
+  const int segs = (nl + kSegment - 1) / kSegment;
+  const int64_t seg = first_row + threadIdx.y;
+  if (seg >= rows_per_rhs * nrhs * segs) return;
+  const int64_t row = segs == 1 ? seg : seg / segs;
+  const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(nl, x0 + kSegment);
   int r, l[kMaxDim];
   decode_row(row, d, it.geom.n, r, l);
   // the row's leading k's: inside I_N or not, their fhat row and factor
@@ -121,13 +129,13 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   C* dst = grid + row * nl;
   const C zero = cmake<C>(0.0, 0.0);
   if (!inside) {
-    for (int x = threadIdx.x; x < nl; x += kRowThreads) dst[x] = zero;
+    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) dst[x] = zero;
     return;
   }
   const C* src = fhat + ((int64_t)r * (it.NN / Nl) + hrow) * Nl;
   const double* cl = it.inv_c[d - 1];
   const int half = Nl / 2;
-  for (int x = threadIdx.x; x < nl; x += kRowThreads) {
+  for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
     int a = -1;
     if (x < half) a = x + half;
     else if (x >= nl - half) a = x - nl + half;
@@ -144,7 +152,10 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
 
 }  // namespace
 
-int64_t scale_blocks(int64_t rows) { return (rows + kRowsPerBlock - 1) / kRowsPerBlock; }
+int64_t scale_blocks(int64_t rows, int64_t row_length) {
+  const int64_t segs = rows * ((row_length + kSegment - 1) / kSegment);
+  return (segs + kRowsPerBlock - 1) / kRowsPerBlock;
+}
 
 template <typename Real>
 cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,

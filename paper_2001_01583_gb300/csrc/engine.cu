@@ -356,21 +356,45 @@ int Engine::build_layout() {
       return cells * csize;
     };
     const bool explicit_bins = bin_opt[0] > 0 || bin_opt[1] > 0 || bin_opt[2] > 0;
-    while (tile_bytes(c.bin) > budget && !explicit_bins) {
+    auto halve_largest = [&](int* bin) {
       int tmax = 0;
       for (int t = 1; t < s.d; ++t)
-        if (c.bin[t] > c.bin[tmax]) tmax = t;
-      if (c.bin[tmax] <= 2) break;
-      c.bin[tmax] /= 2;
+        if (bin[t] > bin[tmax]) tmax = t;
+      if (bin[tmax] <= 2) return false;
+      bin[tmax] /= 2;
+      return true;
+    };
+    // 3-D shared-tile kernels: the padded tile plus the kernel's tables must
+    // fit one block (wide windows: one block of two warps per SM at least)
+    auto planes_fit = [&](const int* bin) {
+      int tile[3];
+      for (int t = 0; t < 3; ++t) tile[t] = bin[t] + c.taps - 1;
+      const size_t wt = (size_t)tile[0] * tile[1] * choose_pitch(tile[2], c.taps, (int)csize) * csize;
+      if (c.taps <= 16) return wt + 32768 <= budget;
+      const size_t tables = precision == NFFT_FP64 ? planes_table_bytes_f64(c.taps, 64, 1, 2, tile)
+                                                   : planes_table_bytes_f32(c.taps, 64, 1, 2, tile);
+      return wt + tables <= smem_optin;
+    };
+    bool planes = false;
+    if (s.d == 3 && c.taps <= kMaxPlaneTaps) {
+      int pb[3] = {c.bin[0], c.bin[1], c.bin[2]};
+      while (!planes_fit(pb) && !explicit_bins && halve_largest(pb)) {
+      }
+      if (planes_fit(pb)) {
+        planes = true;
+        for (int t = 0; t < 3; ++t) c.bin[t] = pb[t];
+      }
     }
+    if (!planes)
+      while (tile_bytes(c.bin) > budget && !explicit_bins && halve_largest(c.bin)) {
+      }
     for (int t = 0; t < 3; ++t) c.tile[t] = t < s.d ? c.bin[t] + c.taps - 1 : 1;
     c.pitch = choose_pitch(c.tile[s.d - 1], c.taps, (int)csize);
     size_t rows = 1;
     for (int t = 0; t + 1 < s.d; ++t) rows *= (size_t)c.tile[t];
     const size_t wtile = rows * (size_t)c.pitch * csize;
     const bool tiled_ok = tile_bytes(c.bin) <= budget && c.taps <= (s.d == 3 ? 26 : 32);
-    const bool warp_ok = s.d >= 2 && c.taps <= 16 &&
-                         (s.d == 3 ? wtile + 32768 <= budget : 2 * wtile + 4096 <= budget);
+    const bool warp_ok = s.d == 3 ? planes : (s.d == 2 && c.taps <= 16 && 2 * wtile + 4096 <= budget);
     int method = method_opt;
     if (method == NFFT_METHOD_AUTO) method = warp_ok ? NFFT_METHOD_WARP : (tiled_ok ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
     if (method == NFFT_METHOD_TILED && !tiled_ok) return NFFT_ERR_UNSUPPORTED;
@@ -521,8 +545,8 @@ int Engine::build_layout() {
     for (int k = 0; k < nitems; ++k) {
       const ItemDev& it = items[k];
       const int dl = it.geom.d - 1;
-      cb[k + 1] = cb[k] + (int)scale_blocks(it.NN / it.N[dl] * it.nrhs);
-      pb[k + 1] = pb[k] + (int)scale_blocks(it.geom.grid_cells / it.geom.n[dl] * it.nrhs);
+      cb[k + 1] = cb[k] + (int)scale_blocks(it.NN / it.N[dl] * it.nrhs, it.N[dl]);
+      pb[k + 1] = pb[k] + (int)scale_blocks(it.geom.grid_cells / it.geom.n[dl] * it.nrhs, it.geom.n[dl]);
     }
     crop_blocks = cb[nitems];
     pad_blocks = pb[nitems];
@@ -883,7 +907,7 @@ int Engine::adjoint_single(const void* f, void* fhat, int R) {
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
     void* out = static_cast<char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr);
+    const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr, it.N[it.geom.d - 1]);
     CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, 1, nullptr, cblocks, out, nr, stream)
                               : launch_deconv_crop<float>(d_items, 1, nullptr, cblocks, out, nr, stream));
     TRY(stage_end(&ev));
@@ -899,7 +923,7 @@ int Engine::forward_single(const void* fhat, void* f, int R) {
     EventPair ev{};
     TRY(stage_begin(NFFT_STAGE_PAD, &ev));
     const void* hin = static_cast<const char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr);
+    const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr, fc.n[fc.d - 1]);
     CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, 1, nullptr, pblocks, hin, nr, stream)
                               : launch_pad_deconv<float>(d_items, 1, nullptr, pblocks, hin, nr, stream));
     TRY(stage_end(&ev));

@@ -93,6 +93,7 @@ const void* wpp_kernel_f32(int d, int taps, bool spread);
 const void* wpp_kernel_f64(int d, int taps, bool spread);
 // 3-D shared-tile kernels (points_planes.cuh): plane-owner spreading (warps
 // a power of two dividing the taps) and point-group interpolation.
+constexpr int kMaxPlaneTaps = 26;   // widest window of the 3-D shared-tile kernels
 const void* planes_kernel_f32(int taps, int warps, bool spread);
 const void* planes_kernel_f64(int taps, int warps, bool spread);
 size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile);
@@ -101,15 +102,18 @@ size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile)
 // ---- scaling (deconv.cu) --------------------------------------------------
 // Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
 // Forward step 1 for every item: grid[r][l] = fhat[r][k] * inv_c(k) if l = k mod n, else 0.
-// Work is cut into rows of the last dimension, kRowsPerBlock rows per block
-// of kRowThreads x kRowsPerBlock threads: an item has nrhs * |I_N| / N_last
-// rows to crop and nrhs * |I_n| / n_last rows to pad.  The blocks of all
-// items form one flat range of `blocks` blocks; block_offsets (device,
-// n_items + 1) are the prefix sums of each item's blocks (null for a single
-// item).  out / in and nrhs override the item table when non-null.
+// Work is cut into segments: rows of the last dimension, rows longer than
+// kSegment elements cut into pieces of kSegment; kRowsPerBlock segments per
+// block of kRowThreads x kRowsPerBlock threads.  An item has nrhs * |I_N| /
+// N_last rows of length N_last to crop and nrhs * |I_n| / n_last rows of
+// length n_last to pad.  The blocks of all items form one flat range of
+// `blocks` blocks; block_offsets (device, n_items + 1) are the prefix sums
+// of each item's blocks (null for a single item).  out / in and nrhs
+// override the item table when non-null.
 constexpr int kRowThreads = 128;
 constexpr int kRowsPerBlock = 2;
-int64_t scale_blocks(int64_t rows);
+constexpr int kSegment = 4096;
+int64_t scale_blocks(int64_t rows, int64_t row_length);
 template <typename Real>
 cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
                                void* out, int nrhs, cudaStream_t st);

@@ -1,4 +1,4 @@
-// Instantiations of the 3-D shared-tile kernels for float.
+// Instantiations of the 3-D shared-tile kernels for float, windows of up to 16 taps (wider: planes_f32_w*.cu).
 #include "points_planes.cuh"
 
 namespace gbnfft {
@@ -9,28 +9,37 @@ namespace gbnfft {
 #define GBNFFT_PLANE_INTERP(W, R) \
   case W:                         \
     return reinterpret_cast<const void*>(&k_interp_groups<W, R>);
+#define GBNFFT_PLANE_BYTES(W, R) \
+  case W:                        \
+    return plane_table_bytes<W, R>(bp, np, nw, tile);
+
+const void* planes_kernel_f32_w18_22(int taps, int warps, bool spread);
+size_t planes_table_bytes_f32_w18_22(int taps, int bp, int np, int nw, const int* tile);
+const void* planes_kernel_f32_w24_26(int taps, int warps, bool spread);
+size_t planes_table_bytes_f32_w24_26(int taps, int bp, int np, int nw, const int* tile);
 
 const void* planes_kernel_f32(int taps, int warps, bool spread) {
+  if (taps >= 24) return planes_kernel_f32_w24_26(taps, warps, spread);
+  if (taps >= 18) return planes_kernel_f32_w18_22(taps, warps, spread);
   if (spread) {
     switch (taps * 100 + warps) {
-      GBNFFT_PLANE_SPREAD_CASES(GBNFFT_PLANE_SPREAD, float)
+      GBNFFT_PLANE_SPREAD_CASES_NARROW(GBNFFT_PLANE_SPREAD, float)
       default:
         return nullptr;
     }
   }
   switch (taps) {
-    GBNFFT_PLANE_TAPS(GBNFFT_PLANE_INTERP, float)
+    GBNFFT_PLANE_TAPS_NARROW(GBNFFT_PLANE_INTERP, float)
     default:
       return nullptr;
   }
 }
 
 size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile) {
+  if (taps >= 24) return planes_table_bytes_f32_w24_26(taps, bp, np, nw, tile);
+  if (taps >= 18) return planes_table_bytes_f32_w18_22(taps, bp, np, nw, tile);
   switch (taps) {
-#define GBNFFT_PLANE_BYTES(W, R) \
-  case W:                        \
-    return plane_table_bytes<W, R>(bp, np, nw, tile);
-    GBNFFT_PLANE_TAPS(GBNFFT_PLANE_BYTES, float)
+    GBNFFT_PLANE_TAPS_NARROW(GBNFFT_PLANE_BYTES, float)
     default:
       return 0;
   }

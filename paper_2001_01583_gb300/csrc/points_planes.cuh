@@ -7,10 +7,11 @@
 // table lookups.  The wrapped grid index of every tile row and column is
 // tabulated once per subproblem for the tile load / flush.
 //
-// spread ("plane owner"): warp w of NW (a power of two dividing W) owns the
-//   tile planes z = w (mod NW), so for every point each warp updates exactly
-//   W/NW of the point's W planes, and no two warps ever write the same cell:
-//   plain shared-memory loads and stores, no atomics, one tile per block.
+// spread ("plane owner"): warp w of NW (a power of two) owns the tile planes
+//   z = w (mod NW), so for every point each warp updates ceil(W/NW) or
+//   floor(W/NW) of the point's W planes, and no two warps ever write the
+//   same cell: plain shared-memory loads and stores, no atomics, one tile
+//   per block.
 //   Inside a plane, lane (ix, q) = (lane % W, lane / W) takes cell ix of rows
 //   q, q + Q, ... (Q = 32 / W).  After the subproblem the tile is added to
 //   the grid once (vector atomics: halos of neighbouring bins overlap).
@@ -120,8 +121,9 @@ template <int W, int NW, typename Real>
 __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real> a, WppLayout lay) {
   using C = typename Cplx<Real>::type;
   using S = PlaneShape<W>;
-  static_assert(W % NW == 0 && (NW & (NW - 1)) == 0, "warps must be a power of two dividing the taps");
-  constexpr int TAPS = W / NW;   // planes of every point this warp updates
+  static_assert((NW & (NW - 1)) == 0 && NW <= 8, "warps per block must be a power of two, at most 8");
+  constexpr int TAPS = (W + NW - 1) / NW;   // at most this many planes of a point per warp
+  constexpr bool EVEN = W % NW == 0;        // every warp takes exactly TAPS planes
   constexpr int BP = 32 * NW;    // points per batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
 #pragma unroll
             for (int u = 0; u < TAPS; ++u) {
               const int i = i0 + u * NW;
+              if (!EVEN && i >= W) break;
               const Real wzx = w[i] * wx;
               const Real vr = v.x * wzx, vi = v.y * wzx;
               C* plane = tr + i * T1 * pitch;
@@ -323,11 +326,21 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
   }
 }
 
-// (taps, warps) pairs instantiated for spreading: warps a power of two dividing the taps.
-#define GBNFFT_PLANE_SPREAD_CASES(X, R)                                                                    \
+// (taps, warps) pairs instantiated for spreading: up to 16 taps the warps
+// divide the taps; wider windows take 2, 4 or 8 warps (one block per SM);
+// in FP64 only 18 and 20 taps (wider tiles do not fit shared memory).
+#define GBNFFT_PLANE_SPREAD_CASES_NARROW(X, R)                                                             \
   X(2, 1, R) X(2, 2, R) X(4, 1, R) X(4, 2, R) X(4, 4, R) X(6, 1, R) X(6, 2, R) X(8, 1, R) X(8, 2, R)      \
       X(8, 4, R) X(8, 8, R) X(10, 1, R) X(10, 2, R) X(12, 1, R) X(12, 2, R) X(12, 4, R) X(14, 1, R)       \
           X(14, 2, R) X(16, 1, R) X(16, 2, R) X(16, 4, R) X(16, 8, R)
-#define GBNFFT_PLANE_TAPS(X, R) X(2, R) X(4, R) X(6, R) X(8, R) X(10, R) X(12, R) X(14, R) X(16, R)
+#define GBNFFT_PLANE_TAPS_NARROW(X, R) X(2, R) X(4, R) X(6, R) X(8, R) X(10, R) X(12, R) X(14, R) X(16, R)
+// wide windows, split over translation units to keep each compile short
+#define GBNFFT_PLANE_SPREAD_CASES_W18_22(X, R) \
+  X(18, 2, R) X(18, 4, R) X(18, 8, R) X(20, 2, R) X(20, 4, R) X(20, 8, R) X(22, 2, R) X(22, 4, R)
+#define GBNFFT_PLANE_TAPS_W18_22(X, R) X(18, R) X(20, R) X(22, R)
+#define GBNFFT_PLANE_SPREAD_CASES_W24_26(X, R) X(24, 2, R) X(24, 4, R) X(26, 2, R) X(26, 4, R)
+#define GBNFFT_PLANE_TAPS_W24_26(X, R) X(24, R) X(26, R)
+#define GBNFFT_PLANE_SPREAD_CASES_W18_20(X, R) X(18, 2, R) X(18, 4, R) X(20, 2, R) X(20, 4, R)
+#define GBNFFT_PLANE_TAPS_W18_20(X, R) X(18, R) X(20, R)
 
 }  // namespace gbnfft

@@ -124,6 +124,90 @@ def test_against_oracles(d, N, M, window, m, precision, method):
     assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= eb * 1.01 + slack
 
 
+# ---- wide windows: the 3-D shared-tile kernels up to 26 taps ----------------
+WIDE = [
+    # N, M, window, m, precision, clustered (taps: Kaiser-Bessel 2m, Gaussian 2m + 2)
+    ((36, 30, 28), 3000, "kaiser_bessel", 9, "fp32", False),    # 18 taps
+    ((30, 36, 28), 2500, "gaussian", 9, "fp32", False),         # 20
+    ((32, 28, 30), 1200, "gaussian", 10, "fp32", False),        # 22
+    ((32, 32, 28), 1000, "kaiser_bessel", 12, "fp32", False),   # 24
+    ((30, 32, 34), 800, "gaussian", 12, "fp32", False),         # 26
+    ((32, 32, 32), 4000, "kaiser_bessel", 9, "fp32", True),     # 18, dense clusters
+    ((28, 30, 26), 1500, "kaiser_bessel", 9, "fp64", False),    # 18
+    ((30, 28, 26), 1500, "gaussian", 9, "fp64", False),         # 20
+]
+
+
+def _amplification(N, n, m, window):
+    """Per-frequency factor c_0 / c_k of the deconvolution (Section 2) on
+    I_N (C order) and its rms: rounding on the grid reaches the adjoint's
+    output multiplied by it, and the forward's input is multiplied by it
+    before the FFT.  It grows with m (about 3 per dimension at the edge of
+    I_N for m = 4, 11 for m = 9, 25 for m = 12)."""
+    w = [np.abs(v) for v in S.scaling_weights(WIN[window], m, list(N), list(n))]
+    amp = np.ones(())
+    for wt in w:
+        amp = np.multiply.outer(amp, wt.max() / wt)
+    return amp, float(np.sqrt(np.mean(amp ** 2)))
+
+
+@pytest.mark.parametrize("N,M,window,m,precision,clustered", WIDE)
+def test_wide_windows_3d(N, M, window, m, precision, clustered):
+    if clustered:
+        x = inputs.clustered_points(M, 3, 4, 0.03, seed=31)
+    else:
+        x = inputs.uniform_points(M, 3, seed=32)
+    f = inputs.complex_normal(M, seed=33)
+    fh = inputs.complex_normal(N, seed=34)
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, precision)
+    assert info["method"] == 3
+    sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
+    sb = S.forward(x, fh, N, 2.0, m, WIN[window])
+    if precision == "fp64":
+        _elementwise(a, sa, 1e-12)
+        _elementwise(b, sb, 1e-12)
+        return
+    # FP32: grid-stage rounding is scaled by c_0 / c_k; compare the adjoint
+    # with that factor taken out, and the forward against the bar times the
+    # factor's rms
+    amp, amp_rms = _amplification(N, info["n"], m, window)
+    err_a = np.max(np.abs(a - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2))
+    assert err_a <= FP32_ELEM, err_a
+    _elementwise(b, sb, FP32_ELEM * amp_rms)
+    assert ndft.rel_l2(a, sa) <= FP32_L2 * amp_rms and ndft.rel_l2(b, sb) <= FP32_L2 * amp_rms
+
+
+# ---- rows longer than one scaling segment (4096 elements) --------------------
+@pytest.mark.parametrize("N,M", [((20000,), 3000), ((8, 5000), 2000)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_long_rows(N, M, precision):
+    d = len(N)
+    x = inputs.uniform_points(M, d, seed=41)
+    f = inputs.complex_normal(M, seed=42)
+    fh = inputs.complex_normal(N, seed=43)
+    a, b, info = _run(N, x, f, fh, 2.0, 3, "kaiser_bessel", precision)
+    assert info["n"][-1] > 2 * 4096
+    tol = 1e-12 if precision == "fp64" else FP32_ELEM
+    _elementwise(a, S.adjoint(x, f, N, 2.0, 3, S.KAISER_BESSEL), tol)
+    _elementwise(b, S.forward(x, fh, N, 2.0, 3, S.KAISER_BESSEL), tol)
+
+
+def test_long_rows_in_a_batch():
+    from paper_2001_01583_gb300 import Batch
+    items = [dict(N=(9000,), M=500, m=3), dict(N=(16, 16, 16), M=800, m=3), dict(N=(6, 9000), M=700, m=3)]
+    xs = [inputs.uniform_points(it["M"], len(it["N"]), seed=50 + i) for i, it in enumerate(items)]
+    fs = [inputs.complex_normal((1, it["M"]), seed=60 + i) for i, it in enumerate(items)]
+    hs = [inputs.complex_normal((1,) + it["N"], seed=70 + i) for i, it in enumerate(items)]
+    with Batch(items, "fp64") as bt:
+        bt.set_points([torch.from_numpy(v).cuda() for v in xs])
+        A = bt.adjoint([torch.from_numpy(v).cuda() for v in fs])
+        B = bt.forward([torch.from_numpy(v).cuda() for v in hs])
+        bt.sync()
+    for i, it in enumerate(items):
+        _elementwise(A[i][0].cpu().numpy(), S.adjoint(xs[i], fs[i][0], it["N"], 2.0, 3, S.KAISER_BESSEL), 1e-12)
+        _elementwise(B[i][0].cpu().numpy(), S.forward(xs[i], hs[i][0], it["N"], 2.0, 3, S.KAISER_BESSEL), 1e-12)
+
+
 def test_3d_config_accuracy_target_small():
     # the 3-D target: Kaiser-Bessel m = 4, sigma = 2, rel-l2 1e-6 in FP32
     N, M = (32, 32, 32), 20000
