@@ -9,7 +9,8 @@ interpolate).  Units: a transform of M points counts M nonuniform points, so a
 step processes 2 sets x 2 transforms x M points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config|small] [--no-cpu-baseline]
+                  [--workload config|small|batch|1d|fluorite|picker]
+                  [--precision fp32|fp64] [--autotune] [--no-cpu-baseline]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  Prints one JSON line (rank 0).  Under torchrun
@@ -42,6 +43,15 @@ WORKLOADS = {
                   name="batched 3-D adjoint+forward NFFT: 512 transforms, N from {32^3, 64^3}, M log-uniform in "
                        "[1e3, 1e5], plus one 64^3 point set with M=2e5 and 16 right-hand sides; Kaiser-Bessel m=4, "
                        "sigma=2; one CUDA-graph launch per direction"),
+    "1d": dict(N=(256,), M=1024, sets=("uniform",), extra=True,
+               name="1-D plain FP64 NFFT, N=256, M=1024, Gaussian m=6, sigma=2, adjoint+forward (launch-latency "
+                    "bound)"),
+    "fluorite": dict(N=(128, 128, 128), M=12 * 32 ** 3, sets=("fluorite",), extra=True,
+                     name="Ewald reciprocal energy of fluorite, 32^3 cells (393216 ions), N=128^3, Kaiser-Bessel m=6, "
+                          "sigma=2: set_points + adjoint NFFT of the charges + weighted mode sum"),
+    "picker": dict(N=(256, 256, 256), M=30_000_000, sets=("clustered64",), extra=True,
+                   name="3-D adjoint+forward NFFT, N=256^3, M=3e7 points in 64 Gaussian clusters (std 0.01), eps=1e-5, "
+                        "window parameters from the learned picker, mixed FP32"),
     "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",),
                   name="3-D adjoint+forward NFFT, N=64^3, M=5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
                        "(profiling case: the same grid and bins, half the points, one set)"),
@@ -178,8 +188,13 @@ def _oracle_sample(wl, seconds_target=15.0):
     and the forward at the same points.  Returns (points/s, threads, text)."""
     from oracle import ndft
     from paper_2001_01583_gb300 import inputs
-    N, M = wl["N"], wl["M"]
-    x = inputs.uniform_points(M, 3, seed=0)
+    # the batch samples its largest item (N = 64^3, M = 1e5)
+    N, M = wl["N"] or (64, 64, 64), wl["M"] or 100000
+    if "fluorite" in wl["sets"]:
+        r, _, L = inputs.fluorite(32)
+        x = inputs.box_points(r, L)
+    else:
+        x = inputs.uniform_points(M, len(N), seed=0)
     f = inputs.complex_normal(M, seed=1)
     fh = inputs.complex_normal(N, seed=2)
     threads = ndft.threads_used(0)
@@ -193,8 +208,8 @@ def _oracle_sample(wl, seconds_target=15.0):
     ndft.adjoint(x[:ms], f[:ms], N)
     ndft.forward(x[:ms], fh, N)
     dt = time.perf_counter() - t0
-    return 2 * ms / dt, threads, "direct NDFT adjoint (all of I_N = %s) + forward at the first %d uniform points, " \
-                                 "FP64, %d threads, %.1f s" % ("x".join(map(str, N)), ms, threads, dt)
+    return 2 * ms / dt, threads, "direct NDFT adjoint (all of I_N = %s) + forward at the first %d of the workload's " \
+                                 "points, FP64, %d threads, %.1f s" % ("x".join(map(str, N)), ms, threads, dt)
 
 
 def run_reference(args, wl, rank, world):
@@ -435,6 +450,119 @@ def run_batch(args, wl, rank, world):
     return 0
 
 
+def _timed(step, stream, dev, steps, warmup, flush):
+    """Device ms per step (CUDA events on the stream, L2 flushed between
+    steps outside the events) and the clocks seen meanwhile."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    return float(np.sum([a.elapsed_time(b) for a, b in ev])) / steps, clocks
+
+
+def run_extra(args, wl, rank, world):
+    """The other configurations: 1-D FP64, the fluorite Ewald energy, and
+    the large clustered problem with picked window parameters."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_01583_gb300 import Plan, _lib, inputs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.load()
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    N, M = wl["N"], wl["M"]
+    extra, points_per_step, launches = {}, 0, 0
+    prec = args.precision
+    if args.workload == "1d":
+        prec = "fp64"
+        x = torch.from_numpy(inputs.uniform_points(M, 1, seed=100 * rank)).to(dev)
+        f = torch.from_numpy(inputs.complex_normal(M, seed=100 * rank + 1)).to(dev)
+        fh = torch.from_numpy(inputs.complex_normal(N, seed=100 * rank + 2)).to(dev)
+        plan = Plan(N, M, 2.0, 6, "gaussian", "fp64", stream=stream)
+        oa, of = torch.empty((1,) + N, dtype=torch.complex128, device=dev), torch.empty((1, M), dtype=torch.complex128,
+                                                                                          device=dev)
+
+        def step():
+            plan.set_points(x)
+            plan.adjoint(f, out=oa)
+            plan.forward(fh, out=of)
+        points_per_step, launches = 2 * M, 10
+        plans = [plan]
+    elif args.workload == "fluorite":
+        r, q, L = inputs.fluorite(32)
+        xq = torch.from_numpy(inputs.box_points(r, L)).to(dev)
+        qd = torch.from_numpy(q.astype(np.complex128 if prec == "fp64" else np.complex64)).to(dev)
+        plan = Plan(N, len(q), 2.0, 6, "kaiser_bessel", prec, stream=stream)
+        out = {}
+
+        def step():
+            plan.set_points(xq)
+            out["e"] = plan.ewald_reciprocal(qd, L, 0.6)
+        points_per_step, launches = len(q), 9
+        plans = [plan]
+    else:   # picker
+        from paper_2001_01583_gb300 import picker
+        eps, std = 1e-5, 0.01
+        pk = picker.load_default(stream=stream)
+        s_, m_, w_, fb = pk.pick(N, M, std, eps)
+        rs, rm, rw = picker.rule_of_thumb(eps)
+        x = torch.from_numpy(inputs.clustered_points(M, 3, 64, std, seed=100 * rank)).to(dev)
+        f = torch.from_numpy(inputs.complex_normal(M, seed=100 * rank + 1, dtype=np.complex64)).to(dev)
+        fh = torch.from_numpy(inputs.complex_normal(N, seed=100 * rank + 2, dtype=np.complex64)).to(dev)
+        oa = torch.empty((1,) + N, dtype=torch.complex64, device=dev)
+        of = torch.empty((1, M), dtype=torch.complex64, device=dev)
+        plans = [Plan(N, M, s_, m_, w_, "fp32", stream=stream), Plan(N, M, rs, rm, rw, "fp32", stream=stream)]
+
+        def make(p):
+            def st():
+                p.set_points(x)
+                p.adjoint(f, out=oa)
+                p.forward(fh, out=of)
+            return st
+        ms_rule, _ = _timed(make(plans[1]), stream, dev, max(2, args.steps // 2), args.warmup, flush)
+        step = make(plans[0])
+        points_per_step, launches = 2 * M, 12
+        extra = {"picked": {"sigma": s_, "m": m_, "window": "gaussian" if w_ == 0 else "kaiser_bessel",
+                            "fallback": fb}, "rule_of_thumb": {"sigma": rs, "m": rm, "window": "kaiser_bessel"},
+                 "rule_ms_per_step": ms_rule, "eps": eps}
+    ms, clocks = _timed(step, stream, dev, args.steps, args.warmup, flush)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = t.item()
+    if args.workload == "fluorite":
+        extra = {"reciprocal_energy": out["e"], "alpha": 0.6, "L": float(L)}
+    cfg = {"workload": wl["name"], "points_per_step_per_gpu": points_per_step, "precision": prec,
+           "l2": "flushed between timed steps (512 MB write outside the step events)",
+           "parallelism": "independent replicas x%d" % world}
+    cfg.update(extra)
+    line = {"metric": METRIC, "value": points_per_step * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic", "config": cfg, "gpu_launches": launches * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,12 +580,14 @@ def main():
     rank = _env_int("RANK", 0)
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
-    if args.workload == "batch":
-        return run_batch(args, wl, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
+        if args.workload == "batch":
+            return run_batch(args, wl, rank, world)
+        if wl.get("extra"):
+            return run_extra(args, wl, rank, world)
         return run_ours(args, wl, rank, world)
     finally:
         if world > 1:

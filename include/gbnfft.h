@@ -76,9 +76,12 @@ typedef enum {
   NFFT_METHOD_TILED = 1,  /* bin-sorted points, per-subproblem shared-memory tile */
   NFFT_METHOD_GLOBAL = 2, /* one thread per point, atomics straight into the grid
                              (the paper's spread kernel, Section 3) */
-  NFFT_METHOD_WARP = 3    /* d = 2, 3 and up to 16 taps: one warp per point, lanes
-                             on distinct cells; spreading into warp-private
-                             shared-memory tiles without atomics */
+  NFFT_METHOD_WARP = 3,   /* d = 2 (up to 16 taps): one warp per point, lanes on
+                             distinct cells, warp-private shared-memory tiles;
+                             d = 3 (up to 26 taps): one shared tile per block,
+                             spreading by plane-owner warps without atomics */
+  NFFT_METHOD_GRID_WARP = 4 /* one warp per point straight on the grid (vector
+                             atomics / gathers, no tile), every subproblem */
 } nfft_method;
 
 /* Options for nfft_set_option. */
@@ -92,7 +95,12 @@ typedef enum {
   NFFT_OPT_PROFILE = 6,         /* 1: record CUDA events around every stage */
   NFFT_OPT_THREADS = 7,         /* threads per block of the point kernels (0 = default) */
   NFFT_OPT_SPREAD_THREADS = 8,  /* threads per block of spreading only (overrides 7) */
-  NFFT_OPT_INTERP_THREADS = 9   /* threads per block of interpolation only (overrides 7) */
+  NFFT_OPT_INTERP_THREADS = 9,  /* threads per block of interpolation only (overrides 7) */
+  NFFT_OPT_SPARSE_POINTS = 10   /* with NFFT_METHOD_AUTO: subproblems of fewer points
+                                   than this run on the NFFT_METHOD_GRID_WARP
+                                   kernels, the rest on the tiled ones (0 =
+                                   automatic: 2 tile cells per window cell,
+                                   -1 = never) */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -126,6 +134,7 @@ typedef struct {
   int max_subproblem;        /* points per subproblem in use */
   int spread_threads;        /* NFFT_OPT_SPREAD_THREADS (0 = chosen per launch) */
   int interp_threads;        /* NFFT_OPT_INTERP_THREADS (0 = chosen per launch) */
+  int sparse_points;         /* subproblems below this many points go to the grid-warp kernels */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling

@@ -5,11 +5,13 @@
 //     on I_N and 0 on I_n \ I_N, written over the whole grid.
 // Work is cut into segments of rows of the last (contiguous) dimension (a
 // row longer than kSegment is cut into pieces): a block of kRowThreads x
-// kRowsPerBlock threads takes kRowsPerBlock segments, decodes each segment's
-// row's leading indices once and forms the product of their FP64 scaling
-// factors once; the threads then walk the segment.  The blocks of all items
-// form one flat range (block_offsets: prefix sums of each item's blocks); a
-// block finds its item by binary search.  1 / c_k is a product of
+// kRowsPerBlock threads takes kSegsPerBlock consecutive segments of one item
+// of a batch (kRowsPerBlock of a single item);
+// per segment it decodes the row's leading indices once and forms the
+// product of their FP64 scaling factors once, then the threads walk the
+// segment.  The blocks of all items form one flat range (block_offsets:
+// prefix sums of each item's blocks; block_items: each block's item, built
+// on the host, so a block finds its item with one load).  1 / c_k is a product of
 // per-dimension FP64 tables, formed in FP64 and rounded once to the data
 // precision.
 #include "kernels.h"
@@ -18,21 +20,16 @@ namespace gbnfft {
 
 namespace {
 
-// This block's item and its first segment (single item when offs is null).
-__device__ __forceinline__ int block_item(const int* offs, int n_items, int64_t& first_row) {
+// This block's item and its first segment: blocks of a batch map to items
+// through block_items (host-built), single items have no tables.
+__device__ __forceinline__ int block_item(const int* offs, const int* block_items, int64_t& first_seg) {
   if (!offs) {
-    first_row = (int64_t)blockIdx.x * kRowsPerBlock;
+    first_seg = (int64_t)blockIdx.x * kRowsPerBlock;
     return 0;
   }
-  const int b = (int)blockIdx.x;
-  int lo = 0, hi = n_items;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (offs[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  first_row = (int64_t)(b - offs[lo]) * kRowsPerBlock;
-  return lo;
+  const int item = block_items[blockIdx.x];
+  first_seg = (int64_t)(blockIdx.x - offs[item]) * kSegsPerBlock;
+  return item;
 }
 
 // Leading indices of a row: row = (r * R0 + i0) * R1 + i1 over (rhs, dims < d-1).
@@ -47,11 +44,11 @@ __device__ __forceinline__ void decode_row(int64_t row, int d, const int* ext, i
 
 template <typename Real>
 __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
-    k_deconv_crop(const ItemDev* __restrict__ items, const int* __restrict__ offs, int n_items, void* out_override,
-                  int nrhs_override) {
+    k_deconv_crop(const ItemDev* __restrict__ items, const int* __restrict__ offs,
+                  const int* __restrict__ block_items, void* out_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
-  int64_t first_row;
-  const ItemDev& it = items[block_item(offs, n_items, first_row)];
+  int64_t first;
+  const ItemDev& it = items[block_item(offs, block_items, first)];
   const int nrhs = out_override ? nrhs_override : it.nrhs;
   C* fhat = static_cast<C*>(out_override ? out_override : it.out);
   const C* grid = static_cast<const C*>(it.grid);
@@ -60,41 +57,45 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   int64_t rows_per_rhs = 1;
   for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.N[t];
   const int segs = (Nl + kSegment - 1) / kSegment;
-  const int64_t seg = first_row + threadIdx.y;
-  if (seg >= rows_per_rhs * nrhs * segs) return;
-  const int64_t row = segs == 1 ? seg : seg / segs;
-  const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(Nl, x0 + kSegment);
-  int r, a[kMaxDim];
-  decode_row(row, d, it.N, r, a);
-  // grid row of the leading k's (k mod n) and their factor
-  int64_t grow = 0;
-  double lead = 1.0;
-  for (int t = 0; t < d - 1; ++t) {
-    const int k = a[t] - it.N[t] / 2;
-    grow = grow * it.geom.n[t] + (k < 0 ? k + it.geom.n[t] : k);
-    lead *= it.inv_c[t][a[t]];
-  }
-  const C* src = grid + (int64_t)r * it.geom.grid_cells + grow * nl;
-  C* dst = fhat + row * Nl;
+  const int64_t total = rows_per_rhs * nrhs * segs;
   const double* cl = it.inv_c[d - 1];
-  for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
-    const int k = x - Nl / 2;
-    const C g = src[k < 0 ? k + nl : k];
-    const Real f = (Real)(lead * cl[x]);
-    C o;
-    o.x = g.x * f;
-    o.y = g.y * f;
-    dst[x] = o;
+  const int per_block = offs ? kSegsPerBlock : kRowsPerBlock;
+  for (int sb = threadIdx.y; sb < per_block; sb += kRowsPerBlock) {
+    const int64_t seg = first + sb;
+    if (seg >= total) break;
+    const int64_t row = segs == 1 ? seg : seg / segs;
+    const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(Nl, x0 + kSegment);
+    int r, a[kMaxDim];
+    decode_row(row, d, it.N, r, a);
+    // grid row of the leading k's (k mod n) and their factor
+    int64_t grow = 0;
+    double lead = 1.0;
+    for (int t = 0; t < d - 1; ++t) {
+      const int k = a[t] - it.N[t] / 2;
+      grow = grow * it.geom.n[t] + (k < 0 ? k + it.geom.n[t] : k);
+      lead *= it.inv_c[t][a[t]];
+    }
+    const C* src = grid + (int64_t)r * it.geom.grid_cells + grow * nl;
+    C* dst = fhat + row * Nl;
+    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
+      const int k = x - Nl / 2;
+      const C g = src[k < 0 ? k + nl : k];
+      const Real f = (Real)(lead * cl[x]);
+      C o;
+      o.x = g.x * f;
+      o.y = g.y * f;
+      dst[x] = o;
+    }
   }
 }
 
 template <typename Real>
 __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
-    k_pad_deconv(const ItemDev* __restrict__ items, const int* __restrict__ offs, int n_items,
-                 const void* in_override, int nrhs_override) {
+    k_pad_deconv(const ItemDev* __restrict__ items, const int* __restrict__ offs,
+                 const int* __restrict__ block_items, const void* in_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
-  int64_t first_row;
-  const ItemDev& it = items[block_item(offs, n_items, first_row)];
+  int64_t first;
+  const ItemDev& it = items[block_item(offs, block_items, first)];
   const int nrhs = in_override ? nrhs_override : it.nrhs;
   const C* fhat = static_cast<const C*>(in_override ? in_override : it.in);
   C* grid = static_cast<C*>(it.grid);
@@ -103,82 +104,90 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   int64_t rows_per_rhs = 1;
   for (int t = 0; t < d - 1; ++t) rows_per_rhs *= it.geom.n[t];
   const int segs = (nl + kSegment - 1) / kSegment;
-  const int64_t seg = first_row + threadIdx.y;
-  if (seg >= rows_per_rhs * nrhs * segs) return;
-  const int64_t row = segs == 1 ? seg : seg / segs;
-  const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(nl, x0 + kSegment);
-  int r, l[kMaxDim];
-  decode_row(row, d, it.geom.n, r, l);
-  // the row's leading k's: inside I_N or not, their fhat row and factor
-  bool inside = true;
-  int64_t hrow = 0;
-  double lead = 1.0;
-  for (int t = 0; t < d - 1; ++t) {
-    const int half = it.N[t] / 2;
-    int k;
-    if (l[t] < half) k = l[t];
-    else if (l[t] >= it.geom.n[t] - half) k = l[t] - it.geom.n[t];
-    else {
-      inside = false;
-      break;
-    }
-    const int a = k + half;
-    hrow = hrow * it.N[t] + a;
-    lead *= it.inv_c[t][a];
-  }
-  C* dst = grid + row * nl;
-  const C zero = cmake<C>(0.0, 0.0);
-  if (!inside) {
-    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) dst[x] = zero;
-    return;
-  }
-  const C* src = fhat + ((int64_t)r * (it.NN / Nl) + hrow) * Nl;
+  const int64_t total = rows_per_rhs * nrhs * segs;
   const double* cl = it.inv_c[d - 1];
   const int half = Nl / 2;
-  for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
-    int a = -1;
-    if (x < half) a = x + half;
-    else if (x >= nl - half) a = x - nl + half;
-    C o = zero;
-    if (a >= 0) {
-      const C h = src[a];
-      const Real f = (Real)(lead * cl[a]);
-      o.x = h.x * f;
-      o.y = h.y * f;
+  const C zero = cmake<C>(0.0, 0.0);
+  const int per_block = offs ? kSegsPerBlock : kRowsPerBlock;
+  for (int sb = threadIdx.y; sb < per_block; sb += kRowsPerBlock) {
+    const int64_t seg = first + sb;
+    if (seg >= total) break;
+    const int64_t row = segs == 1 ? seg : seg / segs;
+    const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(nl, x0 + kSegment);
+    int r, l[kMaxDim];
+    decode_row(row, d, it.geom.n, r, l);
+    // the row's leading k's: inside I_N or not, their fhat row and factor
+    bool inside = true;
+    int64_t hrow = 0;
+    double lead = 1.0;
+    for (int t = 0; t < d - 1; ++t) {
+      const int ht = it.N[t] / 2;
+      int k;
+      if (l[t] < ht) k = l[t];
+      else if (l[t] >= it.geom.n[t] - ht) k = l[t] - it.geom.n[t];
+      else {
+        inside = false;
+        break;
+      }
+      const int a = k + ht;
+      hrow = hrow * it.N[t] + a;
+      lead *= it.inv_c[t][a];
     }
-    dst[x] = o;
+    C* dst = grid + row * nl;
+    if (!inside) {
+      for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) dst[x] = zero;
+      continue;
+    }
+    const C* src = fhat + ((int64_t)r * (it.NN / Nl) + hrow) * Nl;
+    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
+      int a = -1;
+      if (x < half) a = x + half;
+      else if (x >= nl - half) a = x - nl + half;
+      C o = zero;
+      if (a >= 0) {
+        const C h = src[a];
+        const Real f = (Real)(lead * cl[a]);
+        o.x = h.x * f;
+        o.y = h.y * f;
+      }
+      dst[x] = o;
+    }
   }
 }
 
 }  // namespace
 
-int64_t scale_blocks(int64_t rows, int64_t row_length) {
+int64_t scale_blocks(int64_t rows, int64_t row_length, bool batched) {
   const int64_t segs = rows * ((row_length + kSegment - 1) / kSegment);
-  return (segs + kRowsPerBlock - 1) / kRowsPerBlock;
+  const int per_block = batched ? kSegsPerBlock : kRowsPerBlock;
+  return (segs + per_block - 1) / per_block;
 }
 
 template <typename Real>
-cudaError_t launch_deconv_crop(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+cudaError_t launch_deconv_crop(const ItemDev* items, const int* block_offsets, const int* block_items, int64_t blocks,
                                void* out, int nrhs, cudaStream_t st) {
-  if (blocks <= 0 || n_items <= 0) return cudaSuccess;
-  k_deconv_crop<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets, n_items,
-                                                                                     out, nrhs);
+  if (blocks <= 0) return cudaSuccess;
+  k_deconv_crop<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets,
+                                                                                     block_items, out, nrhs);
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_pad_deconv(const ItemDev* items, int n_items, const int* block_offsets, int64_t blocks,
+cudaError_t launch_pad_deconv(const ItemDev* items, const int* block_offsets, const int* block_items, int64_t blocks,
                               const void* in, int nrhs, cudaStream_t st) {
-  if (blocks <= 0 || n_items <= 0) return cudaSuccess;
-  k_pad_deconv<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets, n_items,
-                                                                                    in, nrhs);
+  if (blocks <= 0) return cudaSuccess;
+  k_pad_deconv<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets,
+                                                                                    block_items, in, nrhs);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_deconv_crop<float>(const ItemDev*, int, const int*, int64_t, void*, int, cudaStream_t);
-template cudaError_t launch_deconv_crop<double>(const ItemDev*, int, const int*, int64_t, void*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<float>(const ItemDev*, int, const int*, int64_t, const void*, int, cudaStream_t);
-template cudaError_t launch_pad_deconv<double>(const ItemDev*, int, const int*, int64_t, const void*, int,
+template cudaError_t launch_deconv_crop<float>(const ItemDev*, const int*, const int*, int64_t, void*, int,
+                                               cudaStream_t);
+template cudaError_t launch_deconv_crop<double>(const ItemDev*, const int*, const int*, int64_t, void*, int,
+                                                cudaStream_t);
+template cudaError_t launch_pad_deconv<float>(const ItemDev*, const int*, const int*, int64_t, const void*, int,
+                                              cudaStream_t);
+template cudaError_t launch_pad_deconv<double>(const ItemDev*, const int*, const int*, int64_t, const void*, int,
                                                cudaStream_t);
 
 }  // namespace gbnfft

@@ -332,7 +332,7 @@ int Engine::build_layout() {
   const size_t budget = smem_optin < kSmemBudget ? smem_optin : kSmemBudget;
 
   struct Choice {
-    int bin[3], tile[3], pitch, method, taps;
+    int bin[3], tile[3], pitch, method, taps, sparse;
   };
   std::vector<Choice> ch(nitems);
   for (int i = 0; i < nitems; ++i) {
@@ -399,7 +399,24 @@ int Engine::build_layout() {
     if (method == NFFT_METHOD_AUTO) method = warp_ok ? NFFT_METHOD_WARP : (tiled_ok ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
     if (method == NFFT_METHOD_TILED && !tiled_ok) return NFFT_ERR_UNSUPPORTED;
     if (method == NFFT_METHOD_WARP && !warp_ok) return NFFT_ERR_UNSUPPORTED;
+    const bool gm_ok = (precision == NFFT_FP64 ? gm_kernel_f64(s.d, c.taps, true) : gm_kernel_f32(s.d, c.taps, true)) !=
+                       nullptr;
+    if (method == NFFT_METHOD_GRID_WARP && !gm_ok) return NFFT_ERR_UNSUPPORTED;
     c.method = method;
+    // with AUTO, subproblems too small to pay for a tile go to the grid-warp
+    // kernels: below 2 tile cells (flushed or loaded per subproblem) per
+    // window cell (updated or read per point)
+    c.sparse = 0;
+    if (method_opt == NFFT_METHOD_AUTO && gm_ok && sparse_opt >= 0 &&
+        (method == NFFT_METHOD_WARP || method == NFFT_METHOD_TILED)) {
+      double cells = 1.0, foot = 1.0;
+      for (int t = 0; t < s.d; ++t) {
+        cells *= c.tile[t];
+        foot *= c.taps;
+      }
+      const int autoval = (int)std::ceil(2.0 * cells / foot);
+      c.sparse = sparse_opt > 0 ? sparse_opt : std::max(1, std::min(autoval, max_sub));
+    }
   }
   // group items into kernel classes (stable by first appearance)
   // (items with different right-hand-side counts get their own launch: the
@@ -407,7 +424,8 @@ int Engine::build_layout() {
   auto same = [&](int a, int b) {
     return specs[a].d == specs[b].d && ch[a].taps == ch[b].taps && specs[a].window == specs[b].window &&
            (single || specs[a].nrhs == specs[b].nrhs) &&
-           ch[a].method == ch[b].method && ch[a].bin[0] == ch[b].bin[0] && ch[a].bin[1] == ch[b].bin[1] &&
+           ch[a].method == ch[b].method && ch[a].sparse == ch[b].sparse && ch[a].bin[0] == ch[b].bin[0] &&
+           ch[a].bin[1] == ch[b].bin[1] &&
            ch[a].bin[2] == ch[b].bin[2];
   };
   std::vector<int> rep;
@@ -503,6 +521,7 @@ int Engine::build_layout() {
         kc.tile[t] = c.tile[t];
       }
       kc.pitch = c.pitch;
+      kc.sparse_points = c.sparse;
       kc.item_begin = k;
       kc.bin_begin = bin_off[k];
       kc.max_nrhs = 0;
@@ -545,16 +564,25 @@ int Engine::build_layout() {
     for (int k = 0; k < nitems; ++k) {
       const ItemDev& it = items[k];
       const int dl = it.geom.d - 1;
-      cb[k + 1] = cb[k] + (int)scale_blocks(it.NN / it.N[dl] * it.nrhs, it.N[dl]);
-      pb[k + 1] = pb[k] + (int)scale_blocks(it.geom.grid_cells / it.geom.n[dl] * it.nrhs, it.geom.n[dl]);
+      cb[k + 1] = cb[k] + (int)scale_blocks(it.NN / it.N[dl] * it.nrhs, it.N[dl], true);
+      pb[k + 1] = pb[k] + (int)scale_blocks(it.geom.grid_cells / it.geom.n[dl] * it.nrhs, it.geom.n[dl], true);
     }
     crop_blocks = cb[nitems];
     pad_blocks = pb[nitems];
-    TRY(alloc_dev(d_crop_blocks, sizeof(int) * (nitems + 1), device_bytes));
-    TRY(alloc_dev(d_pad_blocks, sizeof(int) * (nitems + 1), device_bytes));
-    layout_bytes += (int64_t)(2 * sizeof(int) * (nitems + 1));
-    CK(cudaMemcpy(d_crop_blocks, cb.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_pad_blocks, pb.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
+    // [prefix sums (nitems + 1) | item of every block], for crop and for pad
+    auto table = [&](const std::vector<int>& pre, int64_t blocks) {
+      std::vector<int> t(pre);
+      t.reserve((size_t)(nitems + 1 + blocks));
+      for (int k = 0; k < nitems; ++k)
+        for (int b = pre[k]; b < pre[k + 1]; ++b) t.push_back(k);
+      return t;
+    };
+    const std::vector<int> ct = table(cb, crop_blocks), pt = table(pb, pad_blocks);
+    TRY(alloc_dev(d_crop_blocks, sizeof(int) * ct.size(), device_bytes));
+    TRY(alloc_dev(d_pad_blocks, sizeof(int) * pt.size(), device_bytes));
+    layout_bytes += (int64_t)(sizeof(int) * (ct.size() + pt.size()));
+    CK(cudaMemcpy(d_crop_blocks, ct.data(), sizeof(int) * ct.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_pad_blocks, pt.data(), sizeof(int) * pt.size(), cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(d_point_offsets, pts_off.data(), sizeof(int64_t) * (nitems + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_bin_offsets, bin_off.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice));
@@ -686,14 +714,37 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.out = out;
   a.nrhs = nrhs;
   const int max_nrhs = in ? nrhs : kc.max_nrhs;
-  switch (kc.method) {
-    case NFFT_METHOD_WARP:
-      return kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs);
-    case NFFT_METHOD_TILED:
-      return run_tiled<Real>(kc, a, spread, max_nrhs);
-    default:
-      return run_global<Real>(kc, a, spread);
-  }
+  a.sub_min_count = 0;
+  a.sub_max_count = INT_MAX;
+  if (kc.method == NFFT_METHOD_GRID_WARP) return run_gm<Real>(kc, a, spread);
+  if (kc.method == NFFT_METHOD_GLOBAL) return run_global<Real>(kc, a, spread);
+  // tiled kernels take the subproblems of at least sparse_points points,
+  // the grid-warp kernels the rest
+  a.sub_min_count = kc.sparse_points;
+  const int st = kc.method == NFFT_METHOD_WARP
+                     ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
+                     : run_tiled<Real>(kc, a, spread, max_nrhs);
+  if (st != NFFT_OK || kc.sparse_points <= 0) return st;
+  a.sub_min_count = 0;
+  a.sub_max_count = kc.sparse_points;
+  return run_gm<Real>(kc, a, spread);
+}
+
+// One warp per point straight on the grid; warps take whole subproblems.
+template <typename Real>
+int Engine::run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread) {
+  const void* fn = precision == NFFT_FP64 ? gm_kernel_f64(kc.d, kc.taps, spread) : gm_kernel_f32(kc.d, kc.taps, spread);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = 1;
+  const int threads = 32 * kGmWarpsHost;
+  const int per_sm = std::max(1, blocks_per_sm(fn, threads, 0));
+  int64_t blocks = (int64_t)per_sm * num_sms;
+  const int64_t need = (kc.max_subs + kGmWarpsHost - 1) / kGmWarpsHost;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a};
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, 0, stream));
+  return NFFT_OK;
 }
 
 // 3-D: one shared tile per block.  Spreading splits the tile's planes among
@@ -907,9 +958,9 @@ int Engine::adjoint_single(const void* f, void* fhat, int R) {
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
     void* out = static_cast<char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr, it.N[it.geom.d - 1]);
-    CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, 1, nullptr, cblocks, out, nr, stream)
-                              : launch_deconv_crop<float>(d_items, 1, nullptr, cblocks, out, nr, stream));
+    const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr, it.N[it.geom.d - 1], false);
+    CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, nullptr, nullptr, cblocks, out, nr, stream)
+                              : launch_deconv_crop<float>(d_items, nullptr, nullptr, cblocks, out, nr, stream));
     TRY(stage_end(&ev));
   }
   return NFFT_OK;
@@ -923,9 +974,9 @@ int Engine::forward_single(const void* fhat, void* f, int R) {
     EventPair ev{};
     TRY(stage_begin(NFFT_STAGE_PAD, &ev));
     const void* hin = static_cast<const char*>(fhat) + (int64_t)r0 * it.NN * (int64_t)csize;
-    const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr, fc.n[fc.d - 1]);
-    CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, 1, nullptr, pblocks, hin, nr, stream)
-                              : launch_pad_deconv<float>(d_items, 1, nullptr, pblocks, hin, nr, stream));
+    const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr, fc.n[fc.d - 1], false);
+    CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, nullptr, nullptr, pblocks, hin, nr, stream)
+                              : launch_pad_deconv<float>(d_items, nullptr, nullptr, pblocks, hin, nr, stream));
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
     TRY(run_fft(fc, nr, item_grid_offset[0], CUFFT_INVERSE));
@@ -956,7 +1007,8 @@ int Engine::adjoint_table(bool in_graph) {
   for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_FORWARD));
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
-  CK(launch_deconv_crop<Real>(d_items, (int)items.size(), d_crop_blocks, crop_blocks, nullptr, 0, stream));
+  CK(launch_deconv_crop<Real>(d_items, d_crop_blocks, d_crop_blocks + items.size() + 1, crop_blocks, nullptr, 0,
+                              stream));
   if (!in_graph) TRY(stage_end(&ev));
   return NFFT_OK;
 }
@@ -965,7 +1017,8 @@ template <typename Real>
 int Engine::forward_table(bool in_graph) {
   EventPair ev{};
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_PAD, &ev));
-  CK(launch_pad_deconv<Real>(d_items, (int)items.size(), d_pad_blocks, pad_blocks, nullptr, 0, stream));
+  CK(launch_pad_deconv<Real>(d_items, d_pad_blocks, d_pad_blocks + items.size() + 1, pad_blocks, nullptr, 0,
+                             stream));
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
   for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_INVERSE));
@@ -1155,8 +1208,12 @@ int Engine::set_stream(cudaStream_t s) {
 int Engine::set_option(int option, int64_t value) {
   switch (option) {
     case NFFT_OPT_METHOD:
-      if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_WARP) return NFFT_ERR_INVALID_ARG;
+      if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_GRID_WARP) return NFFT_ERR_INVALID_ARG;
       method_opt = (int)value;
+      break;
+    case NFFT_OPT_SPARSE_POINTS:
+      if (value < -1 || value > (1 << 20)) return NFFT_ERR_INVALID_ARG;
+      sparse_opt = (int)value;
       break;
     case NFFT_OPT_BIN_0:
     case NFFT_OPT_BIN_1:
@@ -1232,6 +1289,7 @@ int Engine::info(nfft_plan_info* out) const {
   out->device_bytes = device_bytes;
   out->max_subproblem = max_sub;
   out->spread_threads = spread_threads_opt;
+  out->sparse_points = kclasses.empty() ? 0 : kclasses[0].sparse_points;
   out->interp_threads = interp_threads_opt;
   return NFFT_OK;
 }

@@ -39,6 +39,7 @@ struct KClass {
   int bin_begin, bin_end;     // global bin range
   int max_nrhs;
   int64_t max_subs;           // bound on the class's subproblems
+  int sparse_points;          // subproblems below this many points: grid-warp kernels (0: none)
 };
 
 struct FClass {
@@ -99,6 +100,7 @@ class Engine {
   template <typename Real> int run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
   template <typename Real> int run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
   template <typename Real> int run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
+  template <typename Real> int run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
   template <typename Real> int run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
   template <typename Real> int adjoint_table(bool in_graph);
   template <typename Real> int forward_table(bool in_graph);
@@ -123,6 +125,7 @@ class Engine {
   int method_opt = NFFT_METHOD_AUTO;
   int bin_opt[3] = {0, 0, 0};
   int max_sub_opt = 0;
+  int sparse_opt = 0;   // NFFT_OPT_SPARSE_POINTS
   int max_sub = 1024;
   int threads_opt = 0;
   int spread_threads_opt = 0;
@@ -150,7 +153,7 @@ class Engine {
   int64_t max_subs_total = 0;
   int64_t* d_point_offsets = nullptr;
   int* d_bin_offsets = nullptr;
-  int* d_crop_blocks = nullptr;        // per-item block prefix sums of the scaling launches
+  int* d_crop_blocks = nullptr;        // scaling launches: per-item block prefix sums, then each block's item
   int* d_pad_blocks = nullptr;
   int64_t crop_blocks = 0, pad_blocks = 0;
   int* bin_count = nullptr;

@@ -18,6 +18,8 @@ size_t planes_table_bytes_f32_w18_22(int taps, int bp, int np, int nw, const int
 const void* planes_kernel_f32_w24_26(int taps, int warps, bool spread);
 size_t planes_table_bytes_f32_w24_26(int taps, int bp, int np, int nw, const int* tile);
 
+const void* planes_spread_f32_uneven(int taps, int warps);
+
 const void* planes_kernel_f32(int taps, int warps, bool spread) {
   if (taps >= 24) return planes_kernel_f32_w24_26(taps, warps, spread);
   if (taps >= 18) return planes_kernel_f32_w18_22(taps, warps, spread);
@@ -25,7 +27,7 @@ const void* planes_kernel_f32(int taps, int warps, bool spread) {
     switch (taps * 100 + warps) {
       GBNFFT_PLANE_SPREAD_CASES_NARROW(GBNFFT_PLANE_SPREAD, float)
       default:
-        return nullptr;
+        return planes_spread_f32_uneven(taps, warps);
     }
   }
   switch (taps) {

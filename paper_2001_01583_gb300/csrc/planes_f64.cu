@@ -16,13 +16,15 @@ namespace gbnfft {
 const void* planes_kernel_f64_w18_20(int taps, int warps, bool spread);
 size_t planes_table_bytes_f64_w18_20(int taps, int bp, int np, int nw, const int* tile);
 
+const void* planes_spread_f64_uneven(int taps, int warps);
+
 const void* planes_kernel_f64(int taps, int warps, bool spread) {
   if (taps >= 18) return planes_kernel_f64_w18_20(taps, warps, spread);
   if (spread) {
     switch (taps * 100 + warps) {
       GBNFFT_PLANE_SPREAD_CASES_NARROW(GBNFFT_PLANE_SPREAD, double)
       default:
-        return nullptr;
+        return planes_spread_f64_uneven(taps, warps);
     }
   }
   switch (taps) {

@@ -25,6 +25,8 @@
 
 namespace gbnfft {
 
+constexpr int kLoadRows = 8;   // tile rows a warp loads at once (loads in flight)
+
 template <int W>
 struct PlaneShape {
   static constexpr int Q = (32 / W) > 0 ? (32 / W) : 1;   // rows of a plane per pass
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
+    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;   // block-uniform
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
+    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;   // block-uniform
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -247,14 +251,31 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
     for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
       const int np = min(a.rhs_per_pass, call.nrhs - r0);
       __syncthreads();
-      // load the tile: a warp per row, lanes along the row
-      for (int e = warp; e < np * rows; e += nw) {
-        const int r = e / rows;
-        const int row = e - r * rows;
-        const int z = row / T1, y = row - z * T1;
-        const int64_t gb = (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
-        C* dst = s.tile + r * tile_elems + row * pitch;
-        for (int x = lane; x < T2; x += 32) dst[x] = grid_in[gb + s.gx[x]];
+      // load the tile: a warp takes kLoadRows rows at a time, lanes along
+      // the rows, all loads issued before the shared-memory stores
+      for (int e0 = warp * kLoadRows; e0 < np * rows; e0 += nw * kLoadRows) {
+        for (int x = lane; x < T2; x += 32) {
+          const int64_t gx = s.gx[x];
+          C v[kLoadRows];
+#pragma unroll
+          for (int u = 0; u < kLoadRows; ++u) {
+            const int e = e0 + u;
+            if (e < np * rows) {
+              const int r = e / rows;
+              const int row = e - r * rows;
+              const int z = row / T1, y = row - z * T1;
+              v[u] = grid_in[(int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y] + gx];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kLoadRows; ++u) {
+            const int e = e0 + u;
+            if (e < np * rows) {
+              const int r = e / rows;
+              s.tile[r * tile_elems + (e - r * rows) * pitch + x] = v[u];
+            }
+          }
+        }
       }
       for (int pb = 0; pb < sub.count; pb += bp) {
         const int nb = min(bp, sub.count - pb);
@@ -334,6 +355,9 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
       X(8, 4, R) X(8, 8, R) X(10, 1, R) X(10, 2, R) X(12, 1, R) X(12, 2, R) X(12, 4, R) X(14, 1, R)       \
           X(14, 2, R) X(16, 1, R) X(16, 2, R) X(16, 4, R) X(16, 8, R)
 #define GBNFFT_PLANE_TAPS_NARROW(X, R) X(2, R) X(4, R) X(6, R) X(8, R) X(10, R) X(12, R) X(14, R) X(16, R)
+// narrow windows with more warps than divide the taps (more warps per SM)
+#define GBNFFT_PLANE_SPREAD_CASES_UNEVEN(X, R) \
+  X(6, 4, R) X(10, 4, R) X(10, 8, R) X(12, 8, R) X(14, 4, R) X(14, 8, R)
 // wide windows, split over translation units to keep each compile short
 #define GBNFFT_PLANE_SPREAD_CASES_W18_22(X, R) \
   X(18, 2, R) X(18, 4, R) X(18, 8, R) X(20, 2, R) X(20, 4, R) X(20, 8, R) X(22, 2, R) X(22, 4, R)

@@ -99,14 +99,14 @@ CASES = [
 
 @pytest.mark.parametrize("d,N,M,window,m", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("method", ["tiled", "global", "warp"])
+@pytest.mark.parametrize("method", ["tiled", "global", "warp", "grid_warp"])
 def test_against_oracles(d, N, M, window, m, precision, method):
     if method == "warp" and d == 1:
         pytest.skip("the warp-per-point kernels cover d = 2, 3")
     x = inputs.uniform_points(M, d, seed=5 + d)
     f = inputs.complex_normal(M, seed=6)
     fh = inputs.complex_normal(N, seed=7)
-    meth = {"tiled": 1, "global": 2, "warp": 3}[method]
+    meth = {"tiled": 1, "global": 2, "warp": 3, "grid_warp": 4}[method]
     a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, method=meth)
     assert info["method"] == meth
     sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
@@ -175,6 +175,50 @@ def test_wide_windows_3d(N, M, window, m, precision, clustered):
     assert err_a <= FP32_ELEM, err_a
     _elementwise(b, sb, FP32_ELEM * amp_rms)
     assert ndft.rel_l2(a, sa) <= FP32_L2 * amp_rms and ndft.rel_l2(b, sb) <= FP32_L2 * amp_rms
+
+
+# ---- plane-owner spreading with more warps than divide the taps -------------
+@pytest.mark.parametrize("m,warps,precision", [(3, 4, "fp64"), (5, 4, "fp64"), (5, 8, "fp64"), (7, 4, "fp64"),
+                                               (6, 8, "fp32"), (7, 8, "fp32"), (9, 8, "fp32")])
+def test_plane_spread_uneven_warps(m, warps, precision):
+    N, M = (24, 20, 26), 2500
+    x = inputs.clustered_points(M, 3, 6, 0.05, seed=81)
+    f = inputs.complex_normal(M, seed=82)
+    fh = inputs.complex_normal(N, seed=83)
+    a, b, info = _run(N, x, f, fh, 2.0, m, "kaiser_bessel", precision, method=3, spread_threads=32 * warps)
+    assert info["method"] == 3 and info["spread_threads"] == 32 * warps
+    sa = S.adjoint(x, f, N, 2.0, m, S.KAISER_BESSEL)
+    if precision == "fp64":
+        _elementwise(a, sa, 1e-12)
+    else:
+        amp, _ = _amplification(N, info["n"], m, "kaiser_bessel")
+        assert np.max(np.abs(a - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2)) <= FP32_ELEM
+
+
+# ---- sparse subproblems on the grid-warp kernels, dense ones on tiles --------
+@pytest.mark.parametrize("N,M,window,m", [((40, 36, 32), 3000, "kaiser_bessel", 4), ((30, 28, 34), 2000, "gaussian", 6),
+                                          ((96, 80), 3000, "kaiser_bessel", 5), ((2000,), 3000, "gaussian", 3),
+                                          ((32, 30, 28), 1500, "kaiser_bessel", 10)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sparse_and_dense_subproblems_mixed(N, M, window, m, precision):
+    d = len(N)
+    # dense clusters plus a uniform sprinkle: bins of both kinds in one set
+    x = np.concatenate([inputs.clustered_points(M - M // 4, d, 3, 0.02, seed=91),
+                        inputs.uniform_points(M // 4, d, seed=92)])
+    f = inputs.complex_normal(M, seed=93)
+    fh = inputs.complex_normal(N, seed=94)
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, sparse_points=40, max_subproblem=256)
+    assert info["sparse_points"] == 40
+    sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
+    sb = S.forward(x, fh, N, 2.0, m, WIN[window])
+    if precision == "fp64":
+        _elementwise(a, sa, 1e-12)
+        _elementwise(b, sb, 1e-12)
+    else:
+        amp, amp_rms = _amplification(N, info["n"], m, window)
+        err_a = np.max(np.abs(a - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2))
+        assert err_a <= FP32_ELEM, err_a
+        _elementwise(b, sb, FP32_ELEM * amp_rms)
 
 
 # ---- rows longer than one scaling segment (4096 elements) --------------------
