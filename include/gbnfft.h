@@ -96,11 +96,14 @@ typedef enum {
   NFFT_OPT_THREADS = 7,         /* threads per block of the point kernels (0 = default) */
   NFFT_OPT_SPREAD_THREADS = 8,  /* threads per block of spreading only (overrides 7) */
   NFFT_OPT_INTERP_THREADS = 9,  /* threads per block of interpolation only (overrides 7) */
-  NFFT_OPT_SPARSE_POINTS = 10   /* with NFFT_METHOD_AUTO: subproblems of fewer points
-                                   than this run on the NFFT_METHOD_GRID_WARP
-                                   kernels, the rest on the tiled ones (0 =
-                                   automatic: 2 tile cells per window cell,
-                                   -1 = never) */
+  NFFT_OPT_SPARSE_POINTS = 10,  /* with NFFT_METHOD_AUTO: spreading subproblems of
+                                   fewer points than this run on the
+                                   NFFT_METHOD_GRID_WARP kernel, the rest on the
+                                   tiled one (0 = automatic: one point per
+                                   W^d / 2 tile cells, -1 = never) */
+  NFFT_OPT_SPARSE_POINTS_INTERP = 11 /* the same for interpolation (0 = automatic:
+                                   one point per W^d / 5 tile cells; gathers
+                                   need no atomics, so the split sits higher) */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -134,7 +137,8 @@ typedef struct {
   int max_subproblem;        /* points per subproblem in use */
   int spread_threads;        /* NFFT_OPT_SPREAD_THREADS (0 = chosen per launch) */
   int interp_threads;        /* NFFT_OPT_INTERP_THREADS (0 = chosen per launch) */
-  int sparse_points;         /* subproblems below this many points go to the grid-warp kernels */
+  int sparse_points;         /* spreading subproblems below this many points use the grid-warp kernel */
+  int sparse_points_interp;  /* the same for interpolation */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling

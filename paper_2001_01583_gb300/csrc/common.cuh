@@ -41,6 +41,8 @@ struct WindowDev {
   int taps;                 // W
   double b[kMaxDim];        // shape parameter per dimension
   double kb_norm[kMaxDim];  // 1 / (1 - exp(-2 b m)) per dimension
+  float bf[kMaxDim];        // the same two, rounded to float once (FP32 kernels)
+  float kb_normf[kMaxDim];
 };
 
 // psi(u) = phi(u / n) / phi(0) for the distance u (in cells).
@@ -54,7 +56,7 @@ __device__ __forceinline__ Real window_psi(const WindowDev& w, int t, Real u);
 
 template <>
 __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, float u) {
-  const float b = (float)w.b[t];
+  const float b = w.bf[t];
   if (w.kind == 0) return expf(-(u * u) / b);
   const float m = (float)w.m;
   const float u2 = u * u;
@@ -63,7 +65,7 @@ __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, fl
   const float z = sqrtf(m2 - u2);
   const float e = expf(-b * u2 / (z + m));
   const float s = -expm1f(-2.0f * b * z) / z;
-  return e * m * s * (float)w.kb_norm[t];
+  return e * m * s * w.kb_normf[t];
 }
 
 template <>

@@ -4,16 +4,15 @@
 //   forward step 1 ("subdivide", Algorithm 5): ghat(k) = fhat(k) / c_k(phi~)
 //     on I_N and 0 on I_n \ I_N, written over the whole grid.
 // Work is cut into segments of rows of the last (contiguous) dimension (a
-// row longer than kSegment is cut into pieces): a block of kRowThreads x
-// kRowsPerBlock threads takes kSegsPerBlock consecutive segments of one item
-// of a batch (kRowsPerBlock of a single item);
-// per segment it decodes the row's leading indices once and forms the
-// product of their FP64 scaling factors once, then the threads walk the
-// segment.  The blocks of all items form one flat range (block_offsets:
-// prefix sums of each item's blocks; block_items: each block's item, built
-// on the host, so a block finds its item with one load).  1 / c_k is a product of
-// per-dimension FP64 tables, formed in FP64 and rounded once to the data
-// precision.
+// row longer than kSegment is cut into pieces); a warp takes one segment at
+// a time: it decodes the row's leading indices once and forms the product of
+// their FP64 scaling factors once, then the lanes walk the segment.  A block
+// of kScaleWarps warps takes kSegsPerBlock consecutive segments of one item
+// of a batch (kScaleWarps of a single item).  The blocks of all items form
+// one flat range (block_offsets: prefix sums of each item's blocks;
+// block_items: each block's item, built on the host, so a block finds its
+// item with one load).  1 / c_k is a product of per-dimension FP64 tables,
+// formed in FP64 and rounded once to the data precision.
 #include "kernels.h"
 
 namespace gbnfft {
@@ -24,7 +23,7 @@ namespace {
 // through block_items (host-built), single items have no tables.
 __device__ __forceinline__ int block_item(const int* offs, const int* block_items, int64_t& first_seg) {
   if (!offs) {
-    first_seg = (int64_t)blockIdx.x * kRowsPerBlock;
+    first_seg = (int64_t)blockIdx.x * kScaleWarps;
     return 0;
   }
   const int item = block_items[blockIdx.x];
@@ -32,21 +31,25 @@ __device__ __forceinline__ int block_item(const int* offs, const int* block_item
   return item;
 }
 
-// Leading indices of a row: row = (r * R0 + i0) * R1 + i1 over (rhs, dims < d-1).
-__device__ __forceinline__ void decode_row(int64_t row, int d, const int* ext, int& r, int* idx) {
-  int64_t rem = row;
+// Leading indices of a row: row = (r * R0 + i0) * R1 + i1 over (rhs, dims < d-1)
+// (rows of one launch item stay below 2^31: 32-bit arithmetic).
+__device__ __forceinline__ void decode_row(uint32_t row, int d, const int* ext, int& r, int* idx) {
+  uint32_t rem = row;
   for (int t = d - 2; t >= 0; --t) {
-    idx[t] = (int)(rem % ext[t]);
-    rem /= ext[t];
+    const uint32_t e = (uint32_t)ext[t];
+    const uint32_t q = rem / e;
+    idx[t] = (int)(rem - q * e);
+    rem = q;
   }
   r = (int)rem;
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+__global__ void __launch_bounds__(32 * kScaleWarps)
     k_deconv_crop(const ItemDev* __restrict__ items, const int* __restrict__ offs,
                   const int* __restrict__ block_items, void* out_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t first;
   const ItemDev& it = items[block_item(offs, block_items, first)];
   const int nrhs = out_override ? nrhs_override : it.nrhs;
@@ -59,12 +62,12 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   const int segs = (Nl + kSegment - 1) / kSegment;
   const int64_t total = rows_per_rhs * nrhs * segs;
   const double* cl = it.inv_c[d - 1];
-  const int per_block = offs ? kSegsPerBlock : kRowsPerBlock;
-  for (int sb = threadIdx.y; sb < per_block; sb += kRowsPerBlock) {
+  const int per_block = offs ? kSegsPerBlock : kScaleWarps;
+  for (int sb = warp; sb < per_block; sb += kScaleWarps) {
     const int64_t seg = first + sb;
     if (seg >= total) break;
-    const int64_t row = segs == 1 ? seg : seg / segs;
-    const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(Nl, x0 + kSegment);
+    const uint32_t row = segs == 1 ? (uint32_t)seg : (uint32_t)(seg / segs);
+    const int x0 = (int)(seg - (int64_t)row * segs) * kSegment, x1 = min(Nl, x0 + kSegment);
     int r, a[kMaxDim];
     decode_row(row, d, it.N, r, a);
     // grid row of the leading k's (k mod n) and their factor
@@ -76,8 +79,8 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
       lead *= it.inv_c[t][a[t]];
     }
     const C* src = grid + (int64_t)r * it.geom.grid_cells + grow * nl;
-    C* dst = fhat + row * Nl;
-    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
+    C* dst = fhat + (int64_t)row * Nl;
+    for (int x = x0 + lane; x < x1; x += 32) {
       const int k = x - Nl / 2;
       const C g = src[k < 0 ? k + nl : k];
       const Real f = (Real)(lead * cl[x]);
@@ -90,10 +93,11 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+__global__ void __launch_bounds__(32 * kScaleWarps)
     k_pad_deconv(const ItemDev* __restrict__ items, const int* __restrict__ offs,
                  const int* __restrict__ block_items, const void* in_override, int nrhs_override) {
   using C = typename Cplx<Real>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t first;
   const ItemDev& it = items[block_item(offs, block_items, first)];
   const int nrhs = in_override ? nrhs_override : it.nrhs;
@@ -108,12 +112,12 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
   const double* cl = it.inv_c[d - 1];
   const int half = Nl / 2;
   const C zero = cmake<C>(0.0, 0.0);
-  const int per_block = offs ? kSegsPerBlock : kRowsPerBlock;
-  for (int sb = threadIdx.y; sb < per_block; sb += kRowsPerBlock) {
+  const int per_block = offs ? kSegsPerBlock : kScaleWarps;
+  for (int sb = warp; sb < per_block; sb += kScaleWarps) {
     const int64_t seg = first + sb;
     if (seg >= total) break;
-    const int64_t row = segs == 1 ? seg : seg / segs;
-    const int x0 = (int)(seg - row * segs) * kSegment, x1 = min(nl, x0 + kSegment);
+    const uint32_t row = segs == 1 ? (uint32_t)seg : (uint32_t)(seg / segs);
+    const int x0 = (int)(seg - (int64_t)row * segs) * kSegment, x1 = min(nl, x0 + kSegment);
     int r, l[kMaxDim];
     decode_row(row, d, it.geom.n, r, l);
     // the row's leading k's: inside I_N or not, their fhat row and factor
@@ -133,13 +137,13 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
       hrow = hrow * it.N[t] + a;
       lead *= it.inv_c[t][a];
     }
-    C* dst = grid + row * nl;
+    C* dst = grid + (int64_t)row * nl;
     if (!inside) {
-      for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) dst[x] = zero;
+      for (int x = x0 + lane; x < x1; x += 32) dst[x] = zero;
       continue;
     }
     const C* src = fhat + ((int64_t)r * (it.NN / Nl) + hrow) * Nl;
-    for (int x = x0 + threadIdx.x; x < x1; x += kRowThreads) {
+    for (int x = x0 + lane; x < x1; x += 32) {
       int a = -1;
       if (x < half) a = x + half;
       else if (x >= nl - half) a = x - nl + half;
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
 
 int64_t scale_blocks(int64_t rows, int64_t row_length, bool batched) {
   const int64_t segs = rows * ((row_length + kSegment - 1) / kSegment);
-  const int per_block = batched ? kSegsPerBlock : kRowsPerBlock;
+  const int per_block = batched ? kSegsPerBlock : kScaleWarps;
   return (segs + per_block - 1) / per_block;
 }
 
@@ -167,8 +171,7 @@ template <typename Real>
 cudaError_t launch_deconv_crop(const ItemDev* items, const int* block_offsets, const int* block_items, int64_t blocks,
                                void* out, int nrhs, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
-  k_deconv_crop<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets,
-                                                                                     block_items, out, nrhs);
+  k_deconv_crop<Real><<<(unsigned)blocks, 32 * kScaleWarps, 0, st>>>(items, block_offsets, block_items, out, nrhs);
   return cudaGetLastError();
 }
 
@@ -176,8 +179,7 @@ template <typename Real>
 cudaError_t launch_pad_deconv(const ItemDev* items, const int* block_offsets, const int* block_items, int64_t blocks,
                               const void* in, int nrhs, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
-  k_pad_deconv<Real><<<(unsigned)blocks, dim3(kRowThreads, kRowsPerBlock), 0, st>>>(items, block_offsets,
-                                                                                    block_items, in, nrhs);
+  k_pad_deconv<Real><<<(unsigned)blocks, 32 * kScaleWarps, 0, st>>>(items, block_offsets, block_items, in, nrhs);
   return cudaGetLastError();
 }
 

@@ -332,7 +332,7 @@ int Engine::build_layout() {
   const size_t budget = smem_optin < kSmemBudget ? smem_optin : kSmemBudget;
 
   struct Choice {
-    int bin[3], tile[3], pitch, method, taps, sparse;
+    int bin[3], tile[3], pitch, method, taps, sparse, sparse_interp;
   };
   std::vector<Choice> ch(nitems);
   for (int i = 0; i < nitems; ++i) {
@@ -404,18 +404,23 @@ int Engine::build_layout() {
     if (method == NFFT_METHOD_GRID_WARP && !gm_ok) return NFFT_ERR_UNSUPPORTED;
     c.method = method;
     // with AUTO, subproblems too small to pay for a tile go to the grid-warp
-    // kernels: below 2 tile cells (flushed or loaded per subproblem) per
-    // window cell (updated or read per point)
-    c.sparse = 0;
-    if (method_opt == NFFT_METHOD_AUTO && gm_ok && sparse_opt >= 0 &&
-        (method == NFFT_METHOD_WARP || method == NFFT_METHOD_TILED)) {
+    // kernels: spreading below one point per W^d / 2 tile cells (the grid-warp
+    // spread is bound by its atomics), interpolation below one point per
+    // W^d / 5 tile cells (its gathers are cheaper than a tile load)
+    c.sparse = c.sparse_interp = 0;
+    if (method_opt == NFFT_METHOD_AUTO && gm_ok && (method == NFFT_METHOD_WARP || method == NFFT_METHOD_TILED)) {
       double cells = 1.0, foot = 1.0;
       for (int t = 0; t < s.d; ++t) {
         cells *= c.tile[t];
         foot *= c.taps;
       }
-      const int autoval = (int)std::ceil(2.0 * cells / foot);
-      c.sparse = sparse_opt > 0 ? sparse_opt : std::max(1, std::min(autoval, max_sub));
+      auto pick = [&](int opt, double per_cell) {
+        if (opt < 0) return 0;
+        if (opt > 0) return opt;
+        return std::max(1, std::min((int)std::ceil(per_cell * cells / foot), max_sub));
+      };
+      c.sparse = pick(sparse_opt, 2.0);
+      c.sparse_interp = pick(sparse_interp_opt, 5.0);
     }
   }
   // group items into kernel classes (stable by first appearance)
@@ -424,7 +429,8 @@ int Engine::build_layout() {
   auto same = [&](int a, int b) {
     return specs[a].d == specs[b].d && ch[a].taps == ch[b].taps && specs[a].window == specs[b].window &&
            (single || specs[a].nrhs == specs[b].nrhs) &&
-           ch[a].method == ch[b].method && ch[a].sparse == ch[b].sparse && ch[a].bin[0] == ch[b].bin[0] &&
+           ch[a].method == ch[b].method && ch[a].sparse == ch[b].sparse &&
+           ch[a].sparse_interp == ch[b].sparse_interp && ch[a].bin[0] == ch[b].bin[0] &&
            ch[a].bin[1] == ch[b].bin[1] &&
            ch[a].bin[2] == ch[b].bin[2];
   };
@@ -487,6 +493,8 @@ int Engine::build_layout() {
       const double b = shape_param(s.window, s.m, sig);
       w.b[t] = b;
       w.kb_norm[t] = 1.0 / (1.0 - std::exp(-2.0 * b * s.m));
+      w.bf[t] = (float)w.b[t];
+      w.kb_normf[t] = (float)w.kb_norm[t];
       if (t < s.d) {
         const auto key = std::make_tuple(s.window, s.N[t], (int64_t)g.n[t], s.m, 0);
         auto f = table_cache.find(key);
@@ -522,6 +530,7 @@ int Engine::build_layout() {
       }
       kc.pitch = c.pitch;
       kc.sparse_points = c.sparse;
+      kc.sparse_points_interp = c.sparse_interp;
       kc.item_begin = k;
       kc.bin_begin = bin_off[k];
       kc.max_nrhs = 0;
@@ -718,19 +727,20 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.sub_max_count = INT_MAX;
   if (kc.method == NFFT_METHOD_GRID_WARP) return run_gm<Real>(kc, a, spread);
   if (kc.method == NFFT_METHOD_GLOBAL) return run_global<Real>(kc, a, spread);
-  // tiled kernels take the subproblems of at least sparse_points points,
-  // the grid-warp kernels the rest
-  a.sub_min_count = kc.sparse_points;
+  // tiled kernels take the subproblems of at least `split` points, the
+  // grid-warp kernels the rest
+  const int split = spread ? kc.sparse_points : kc.sparse_points_interp;
+  a.sub_min_count = split;
   const int st = kc.method == NFFT_METHOD_WARP
                      ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
                      : run_tiled<Real>(kc, a, spread, max_nrhs);
-  if (st != NFFT_OK || kc.sparse_points <= 0) return st;
+  if (st != NFFT_OK || split <= 0) return st;
   a.sub_min_count = 0;
-  a.sub_max_count = kc.sparse_points;
+  a.sub_max_count = split;
   return run_gm<Real>(kc, a, spread);
 }
 
-// One warp per point straight on the grid; warps take whole subproblems.
+// One warp per point straight on the grid; kGmSplitHost warps share a subproblem.
 template <typename Real>
 int Engine::run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread) {
   const void* fn = precision == NFFT_FP64 ? gm_kernel_f64(kc.d, kc.taps, spread) : gm_kernel_f32(kc.d, kc.taps, spread);
@@ -739,7 +749,7 @@ int Engine::run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread) {
   const int threads = 32 * kGmWarpsHost;
   const int per_sm = std::max(1, blocks_per_sm(fn, threads, 0));
   int64_t blocks = (int64_t)per_sm * num_sms;
-  const int64_t need = (kc.max_subs + kGmWarpsHost - 1) / kGmWarpsHost;
+  const int64_t need = (kc.max_subs * kGmSplitHost + kGmWarpsHost - 1) / kGmWarpsHost;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
@@ -1212,8 +1222,9 @@ int Engine::set_option(int option, int64_t value) {
       method_opt = (int)value;
       break;
     case NFFT_OPT_SPARSE_POINTS:
+    case NFFT_OPT_SPARSE_POINTS_INTERP:
       if (value < -1 || value > (1 << 20)) return NFFT_ERR_INVALID_ARG;
-      sparse_opt = (int)value;
+      (option == NFFT_OPT_SPARSE_POINTS ? sparse_opt : sparse_interp_opt) = (int)value;
       break;
     case NFFT_OPT_BIN_0:
     case NFFT_OPT_BIN_1:
@@ -1290,6 +1301,7 @@ int Engine::info(nfft_plan_info* out) const {
   out->max_subproblem = max_sub;
   out->spread_threads = spread_threads_opt;
   out->sparse_points = kclasses.empty() ? 0 : kclasses[0].sparse_points;
+  out->sparse_points_interp = kclasses.empty() ? 0 : kclasses[0].sparse_points_interp;
   out->interp_threads = interp_threads_opt;
   return NFFT_OK;
 }

@@ -39,7 +39,8 @@ struct KClass {
   int bin_begin, bin_end;     // global bin range
   int max_nrhs;
   int64_t max_subs;           // bound on the class's subproblems
-  int sparse_points;          // subproblems below this many points: grid-warp kernels (0: none)
+  int sparse_points;          // spreading subproblems below this many points: grid-warp kernel (0: none)
+  int sparse_points_interp;   // the same for interpolation
 };
 
 struct FClass {
@@ -125,7 +126,8 @@ class Engine {
   int method_opt = NFFT_METHOD_AUTO;
   int bin_opt[3] = {0, 0, 0};
   int max_sub_opt = 0;
-  int sparse_opt = 0;   // NFFT_OPT_SPARSE_POINTS
+  int sparse_opt = 0;          // NFFT_OPT_SPARSE_POINTS
+  int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP
   int max_sub = 1024;
   int threads_opt = 0;
   int spread_threads_opt = 0;

@@ -88,6 +88,7 @@ const void* global_kernel_f64(bool spread);
 // Warp-per-point kernels straight on the grid (points_gm.cuh), any d, taps 2..26 even;
 // blocks of kGmWarpsHost warps.
 constexpr int kGmWarpsHost = 8;
+constexpr int kGmSplitHost = 4;   // warps sharing one subproblem
 const void* gm_kernel_f32(int d, int taps, bool spread);
 const void* gm_kernel_f64(int d, int taps, bool spread);
 
@@ -111,17 +112,17 @@ size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile)
 // Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.
 // Forward step 1 for every item: grid[r][l] = fhat[r][k] * inv_c(k) if l = k mod n, else 0.
 // Work is cut into segments: rows of the last dimension, rows longer than
-// kSegment elements cut into pieces of kSegment.  A block of kRowThreads x
-// kRowsPerBlock threads takes kSegsPerBlock consecutive segments of one item
-// of a batch (kRowsPerBlock segments of a single item: block_offsets null).  An item has nrhs * |I_N| / N_last rows of length N_last to crop and
-// nrhs * |I_n| / n_last rows of length n_last to pad.  The blocks of all
-// items form one flat range of `blocks` blocks; block_offsets (device,
-// n_items + 1) are the prefix sums of each item's blocks and block_items
-// (device, `blocks`) each block's item (both null for a single item).
-// out / in and nrhs override the item table when non-null.
-constexpr int kRowThreads = 128;
-constexpr int kRowsPerBlock = 2;
-constexpr int kSegsPerBlock = 16;
+// kSegment elements cut into pieces of kSegment; a warp takes a segment at a
+// time.  A block of kScaleWarps warps takes kSegsPerBlock consecutive
+// segments of one item of a batch (kScaleWarps segments of a single item:
+// block_offsets null).  An item has nrhs * |I_N| / N_last rows of length
+// N_last to crop and nrhs * |I_n| / n_last rows of length n_last to pad.
+// The blocks of all items form one flat range of `blocks` blocks;
+// block_offsets (device, n_items + 1) are the prefix sums of each item's
+// blocks and block_items (device, `blocks`) each block's item (both null for
+// a single item).  out / in and nrhs override the item table when non-null.
+constexpr int kScaleWarps = 8;
+constexpr int kSegsPerBlock = 32;
 constexpr int kSegment = 4096;
 int64_t scale_blocks(int64_t rows, int64_t row_length, bool batched);
 template <typename Real>

@@ -4,8 +4,8 @@
 //
 // A shared tile pays for zeroing, loading and flushing (b + W - 1)^d cells
 // per subproblem; with a few points per bin that costs more than the points'
-// own W^d cell updates.  Here a warp takes a whole subproblem and handles its
-// points one after another, with no tile and no block barrier:
+// own W^d cell updates.  Here kGmSplit warps share a subproblem, each taking
+// every kGmSplit-th point, with no tile and no block barrier:
 //   - lanes split the point's d * W window weights into a per-warp table;
 //   - lanes cover one plane of the point's footprint (W x W cells, the last
 //     two dimensions; W cells in 1-D) in ceil(W^2 / 32) passes, lanes along
@@ -29,6 +29,7 @@ struct GmShape {
 };
 
 constexpr int kGmWarps = kGmWarpsHost;   // warps per block
+constexpr int kGmSplit = kGmSplitHost;   // warps sharing one subproblem's points
 
 __device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -86,10 +87,12 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Rea
   Real* wt = wt_all[warp];
   int lo, hi;
   launch_subs(a, lo, hi);
-  const int stride = gridDim.x * kGmWarps;
-  for (int sp = lo + blockIdx.x * kGmWarps + warp; sp < hi; sp += stride) {
+  const int64_t stride = (int64_t)gridDim.x * kGmWarps;
+  const int64_t work = (int64_t)(hi - lo) * kGmSplit;
+  for (int64_t wi = (int64_t)blockIdx.x * kGmWarps + warp; wi < work; wi += stride) {
+    const int sp = lo + (int)(wi / kGmSplit), part = (int)(wi % kGmSplit);
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;
+    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count || part >= sub.count) continue;
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Rea
     int bc[kMaxDim];
     bin_coords(sub.bin, g, bc);
     const int64_t plane_cells = D == 3 ? (int64_t)g.n[1] * g.n[2] : 0;
-    for (int pp = 0; pp < sub.count; ++pp) {
+    for (int pp = part; pp < sub.count; pp += kGmSplit) {
       const int idx = sub.start + pp;
       const int j = a.pts.perm[idx];
       GmPoint<D, W, Real> q;
@@ -138,10 +141,12 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_interp_gm(PointKernelArgs<Rea
   Real* wt = wt_all[warp];
   int lo, hi;
   launch_subs(a, lo, hi);
-  const int stride = gridDim.x * kGmWarps;
-  for (int sp = lo + blockIdx.x * kGmWarps + warp; sp < hi; sp += stride) {
+  const int64_t stride = (int64_t)gridDim.x * kGmWarps;
+  const int64_t work = (int64_t)(hi - lo) * kGmSplit;
+  for (int64_t wi = (int64_t)blockIdx.x * kGmWarps + warp; wi < work; wi += stride) {
+    const int sp = lo + (int)(wi / kGmSplit), part = (int)(wi % kGmSplit);
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;
+    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count || part >= sub.count) continue;
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_interp_gm(PointKernelArgs<Rea
     int bc[kMaxDim];
     bin_coords(sub.bin, g, bc);
     const int64_t plane_cells = D == 3 ? (int64_t)g.n[1] * g.n[2] : 0;
-    for (int pp = 0; pp < sub.count; ++pp) {
+    for (int pp = part; pp < sub.count; pp += kGmSplit) {
       const int idx = sub.start + pp;
       const int j = a.pts.perm[idx];
       GmPoint<D, W, Real> q;

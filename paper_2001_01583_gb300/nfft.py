@@ -144,7 +144,7 @@ class Plan:
                     n_bins=inf.n_bins, rhs_capacity=inf.rhs_capacity, threads=inf.threads,
                     device_bytes=inf.device_bytes, sigma=tuple(inf.sigma[:inf.d]),
                     max_subproblem=inf.max_subproblem, spread_threads=inf.spread_threads,
-                    sparse_points=inf.sparse_points,
+                    sparse_points=inf.sparse_points, sparse_points_interp=inf.sparse_points_interp,
                     interp_threads=inf.interp_threads)
 
     def autotune(self, reps=3):

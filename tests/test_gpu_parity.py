@@ -207,8 +207,9 @@ def test_sparse_and_dense_subproblems_mixed(N, M, window, m, precision):
                         inputs.uniform_points(M // 4, d, seed=92)])
     f = inputs.complex_normal(M, seed=93)
     fh = inputs.complex_normal(N, seed=94)
-    a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, sparse_points=40, max_subproblem=256)
-    assert info["sparse_points"] == 40
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, precision, sparse_points=40, sparse_points_interp=60,
+                      max_subproblem=256)
+    assert info["sparse_points"] == 40 and info["sparse_points_interp"] == 60
     sa = S.adjoint(x, f, N, 2.0, m, WIN[window])
     sb = S.forward(x, fh, N, 2.0, m, WIN[window])
     if precision == "fp64":

@@ -10,8 +10,11 @@ library's kernels: FP16 weights, FP32 accumulation).
   loss;
 - the error labels of those runs agree with the direct NDFT oracle;
 - the shipped picker: on held-out problems its choices reach the requested
-  eps against the direct NDFT oracle, and cost in total no more than the
-  rule of thumb;
+  eps against the direct NDFT oracle where the rule of thumb misses it in
+  some cases, and cost in total no more than the rule of thumb;
+- on a grid-dominated problem (N = 256^3, M = 1e6, eps = 1e-5) its choice
+  reaches eps at sampled frequencies and runs at least 1.5x faster than the
+  rule of thumb's;
 - applied to N = 256^3, M = 3e7 points in 64 Gaussian clusters of std 0.01,
   FP32, eps = 1e-5: error at sampled frequencies against the oracle <= eps
   and time <= the rule of thumb's.
@@ -140,33 +143,42 @@ def _held_out(count, seed, budget=2e7):
 
 
 def test_picker_reaches_eps_on_held_out_problems():
+    """Picks reach eps on every held-out case; the rule of thumb misses some
+    (its estimate ignores constant factors), and the picks cost no more."""
     from paper_2001_01583_gb300 import Plan, picker
     pk = picker.load_default()
     cm = picker.CostModel(pk.meta["cost_coef"])
-    rows, fails, cost_pick, cost_rule = [], [], 0.0, 0.0
+    rows, fails, rule_misses, cost_pick, cost_rule = [], [], 0, 0.0, 0.0
     for pb in _held_out(12, seed=90000):
         x = picker.problem_points(pb)
         f = inputs.complex_normal((1, pb["M"]), seed=pb["seed"] + 7)[0]
         exact = ndft.adjoint(x, f, pb["N"])
         xd = torch.from_numpy(x).cuda()
         fd = torch.from_numpy(f).cuda()
-        for eps in (1e-9, 1e-6, 1e-4):
-            s, m, w, fb = pk.pick(pb["N"], pb["M"], pb["std"], eps)
+
+        def err_of(s, m, w):
             with Plan(pb["N"], pb["M"], s, m, w, "fp64") as p:
                 p.set_points(xd)
-                err = ndft.rel_l2(p.adjoint(fd).cpu().numpy(), exact)
+                return ndft.rel_l2(p.adjoint(fd).cpu().numpy(), exact)
+
+        for eps in (1e-9, 1e-7, 1e-4):
+            s, m, w, fb = pk.pick(pb["N"], pb["M"], pb["std"], eps)
             rs, rm, rw = picker.rule_of_thumb(eps)
+            err, err_rule = err_of(s, m, w), err_of(rs, rm, rw)
             c_pick, c_rule = cm(pb["N"], pb["M"], s, m, w), cm(pb["N"], pb["M"], rs, rm, rw)
             cost_pick += c_pick
             cost_rule += c_rule
-            rows.append((pb["N"], pb["M"], pb["std"], eps, (s, m, w, fb), err, c_pick / c_rule))
+            rule_misses += int(not err_rule <= eps)
+            rows.append((pb["N"], pb["M"], pb["std"], eps, (s, m, w, fb), err, err_rule, c_pick / c_rule))
             if not err <= eps:
                 fails.append(rows[-1])
     for r in rows:
-        print("N=%s M=%d std=%.3f eps=%.0e pick=%s err=%.2e cost/rule=%.2f" % r)
-    print("total cost picked / rule of thumb: %.3f" % (cost_pick / cost_rule))
+        print("N=%s M=%d std=%.3f eps=%.0e pick=%s err=%.2e rule err=%.2e cost/rule=%.2f" % r)
+    print("rule of thumb misses eps in %d of %d cases; picks in %d; total cost picked / rule %.3f"
+          % (rule_misses, len(rows), len(fails), cost_pick / cost_rule))
     assert not fails, fails
-    assert cost_pick <= cost_rule
+    assert rule_misses >= 1
+    assert cost_pick <= cost_rule * 1.0001
 
 
 def _timed_adjoint_sampled(N, M, params, xd, fd, ks, reps=5):
@@ -186,6 +198,31 @@ def _timed_adjoint_sampled(N, M, params, xd, fd, ks, reps=5):
         h = [n // 2 for n in N]
         got = out[ks[:, 0] + h[0], ks[:, 1] + h[1], ks[:, 2] + h[2]].cpu().numpy()
     return float(np.median(times)), got
+
+
+def test_picker_beats_rule_on_grid_dominated_problem():
+    """N = 256^3, M = 1e6 (M / |I_N| = 0.06), eps = 1e-5: the grid dominates,
+    and a smaller oversampling with a wider window reaches eps faster."""
+    from paper_2001_01583_gb300 import picker
+    N, M, eps = (256, 256, 256), 1_000_000, 1e-5
+    pk = picker.load_default()
+    picked = pk.pick(N, M, 0.0, eps)
+    rule = picker.rule_of_thumb(eps)
+    assert not picked[3]
+    x = inputs.uniform_points(M, 3, seed=4040)
+    f = inputs.complex_normal(M, seed=4041, dtype=np.complex64)
+    rng = np.random.default_rng(4)
+    ks = np.stack([rng.integers(-128, 128, size=48) for _ in range(3)], axis=1)
+    ref = ndft.adjoint(x, f.astype(np.complex128), N, ksel=ks)
+    xd = torch.from_numpy(x).cuda()
+    fd = torch.from_numpy(f).cuda()
+    t_pick, got_pick = _timed_adjoint_sampled(N, M, picked[:3], xd, fd, ks)
+    t_rule, got_rule = _timed_adjoint_sampled(N, M, rule, xd, fd, ks)
+    e_pick, e_rule = ndft.rel_l2(got_pick, ref), ndft.rel_l2(got_rule, ref)
+    print("picked %s: %.3f ms, sampled error %.2e; rule %s: %.3f ms, sampled error %.2e"
+          % (picked, t_pick, e_pick, rule, t_rule, e_rule))
+    assert e_pick <= eps
+    assert t_pick * 1.5 <= t_rule
 
 
 def test_picker_on_large_clustered_problem():
