@@ -243,6 +243,13 @@ int nfft_autotune(nfft_plan* plan, int reps, double* best_ms);
  * each of the d bandwidths and the number of window taps per dimension. */
 int nfft_plan_params(int d, const int64_t* N, double sigma, int m, int window, int64_t* n_out, int* taps_out);
 
+/* Host-only: how much the scaling step (Section 2, 1/c_k) amplifies
+ * rounding on the oversampled grid.  With a_t(k) = c_t(0) / c_t(k_t) per
+ * dimension, *rms (may be NULL) = prod_t sqrt(mean over I_N of a_t^2) and
+ * *peak (may be NULL) = prod_t max a_t (at the edge of I_N).  Frequencies are
+ * subsampled to at most 4097 per dimension.  FP32 errors scale with *rms. */
+int nfft_deconv_amplification(int d, const int64_t* N, double sigma, int m, int window, double* rms, double* peak);
+
 /* ---- batches ------------------------------------------------------------
  * Many independent transforms of uneven sizes (and items with several
  * right-hand sides sharing one point set), set up once and run together:
@@ -338,19 +345,23 @@ int nfft_picker_features(int d, const int64_t* N, int64_t M, double cluster_std,
  * log10(error / eps) of candidate c, output n_candidates + c its normalised
  * log10(cost); denormalised output = y * out_std + out_mean, normalised
  * feature = (f - feat_mean) / feat_std.  A candidate qualifies when its
- * predicted error is at most eps * err_margin (0 < err_margin <= 1). */
+ * predicted error is at most eps * err_margin (0 < err_margin <= 1).  The
+ * network predicts the window's error (FP64 runs); for the FP32 form a
+ * candidate must also have fp32_floor * (nfft_deconv_amplification rms) at
+ * most eps * err_margin: the rounding of the FP32 grid stage, amplified by
+ * the scaling step. */
 int nfft_picker_configure(nfft_mlp* mlp, int n_candidates, const double* cand_sigma, const int* cand_m,
                           const int* cand_window, const double* feat_mean, const double* feat_std,
-                          const double* out_mean, const double* out_std, double err_margin);
+                          const double* out_mean, const double* out_std, double err_margin, double fp32_floor);
 /* The plain rule: Kaiser-Bessel, sigma = 2, m = ceil(ln(1/eps) / (2 pi sqrt(1 - 1/sigma))) in [2, 12]. */
 int nfft_rule_of_thumb(double eps, double* sigma, int* m, int* window);
-/* Choose (sigma, m, window) for a problem: the candidate with the lowest
- * predicted cost among those valid for N and predicted to reach eps (see
- * nfft_picker_configure);
- * the rule of thumb (used_fallback = 1) when none qualifies or mlp is NULL
- * or not configured.  Runs one forward pass on the device and waits. */
+/* Choose (sigma, m, window) for a problem solved in `precision`
+ * (nfft_precision): the candidate with the lowest predicted cost among those
+ * valid for N and predicted to reach eps (see nfft_picker_configure); the
+ * rule of thumb (used_fallback = 1) when none qualifies or mlp is NULL or not
+ * configured.  Runs one forward pass on the device and waits. */
 int nfft_pick_params(nfft_mlp* mlp, int d, const int64_t* N, int64_t M, double cluster_std, double eps,
-                     double* sigma, int* m, int* window, int* used_fallback);
+                     int precision, double* sigma, int* m, int* window, int* used_fallback);
 
 /* Human-readable name of a status code (static string). */
 const char* nfft_status_string(int status);

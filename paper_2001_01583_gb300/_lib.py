@@ -130,12 +130,14 @@ def _declare(lib):
                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                                 ctypes.c_double]),
+                                                 ctypes.c_double, ctypes.c_double]),
         "nfft_rule_of_thumb": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "nfft_pick_params": (ctypes.c_int, [vp, ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
-                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "nfft_deconv_amplification": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }

@@ -49,28 +49,10 @@ double bessel_i0(double x) {
   return sum;
 }
 
-double shape_param(int window, int m, double sigma) {
-  if (window == NFFT_GAUSSIAN) return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * M_PI);
-  return M_PI * (2.0 - 1.0 / sigma);
-}
-
-// 1 / c_k for k = -N/2 .. N/2-1 of one dimension, with the kernels' window
-// normalisation psi = phi / phi(0):  inv_c(k) = phi(0) / (n phihat(k)).
-//   Gaussian:       phi(0) = (pi b)^(-1/2),        n phihat(k) = exp(-b (pi k / n)^2)
-//   Kaiser-Bessel:  phi(0) = sinh(b m) / (pi m),   n phihat(k) = I0(m sqrt(b^2 - (2 pi k / n)^2))
+// The table of 1 / c_k (inv_c_at below) over k = -N/2 .. N/2-1.
 std::vector<double> scaling_table(int window, int m, int64_t N, int64_t n, double b) {
   std::vector<double> out((size_t)N);
-  for (int64_t a = 0; a < N; ++a) {
-    const double k = (double)(a - N / 2);
-    if (window == NFFT_GAUSSIAN) {
-      const double t = M_PI * k / (double)n;
-      out[(size_t)a] = std::exp(b * t * t) / std::sqrt(M_PI * b);
-    } else {
-      const double w = 2.0 * M_PI * k / (double)n;
-      const double arg = m * std::sqrt(b * b - w * w);
-      out[(size_t)a] = std::sinh(b * m) / (M_PI * m * bessel_i0(arg));
-    }
-  }
+  for (int64_t a = 0; a < N; ++a) out[(size_t)a] = inv_c_at(window, m, n, b, (double)(a - N / 2));
   return out;
 }
 
@@ -161,6 +143,26 @@ size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* t
 }
 
 }  // namespace
+
+double shape_param(int window, int m, double sigma) {
+  if (window == NFFT_GAUSSIAN) return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * M_PI);
+  return M_PI * (2.0 - 1.0 / sigma);
+}
+
+// 1 / c_k for k = -N/2 .. N/2-1 of one dimension, with the kernels' window
+// normalisation psi = phi / phi(0):  inv_c(k) = phi(0) / (n phihat(k)).
+//   Gaussian:       phi(0) = (pi b)^(-1/2),        n phihat(k) = exp(-b (pi k / n)^2)
+//   Kaiser-Bessel:  phi(0) = sinh(b m) / (pi m),   n phihat(k) = I0(m sqrt(b^2 - (2 pi k / n)^2))
+double inv_c_at(int window, int m, int64_t n, double b, double k) {
+  if (window == NFFT_GAUSSIAN) {
+    const double t = M_PI * k / (double)n;
+    return std::exp(b * t * t) / std::sqrt(M_PI * b);
+  }
+  const double w = 2.0 * M_PI * k / (double)n;
+  const double arg = m * std::sqrt(b * b - w * w);
+  return std::sinh(b * m) / (M_PI * m * bessel_i0(arg));
+}
+
 
 // ===========================================================================
 // parameters shared with nfft_plan_params
@@ -376,7 +378,9 @@ int Engine::build_layout() {
       return wt + tables <= smem_optin;
     };
     bool planes = false;
-    if (s.d == 3 && c.taps <= kMaxPlaneTaps) {
+    const bool planes_built = (precision == NFFT_FP64 ? planes_kernel_f64(c.taps, 2, true)
+                                                      : planes_kernel_f32(c.taps, 2, true)) != nullptr;
+    if (s.d == 3 && c.taps <= kMaxPlaneTaps && planes_built) {
       int pb[3] = {c.bin[0], c.bin[1], c.bin[2]};
       while (!planes_fit(pb) && !explicit_bins && halve_largest(pb)) {
       }

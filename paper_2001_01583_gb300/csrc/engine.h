@@ -61,6 +61,9 @@ struct EventPair {
 int64_t oversampled_size(int64_t N, double sigma);
 int window_taps(int window, int m);
 int validate_spec(const ItemSpec& s, int precision);
+double shape_param(int window, int m, double sigma);
+// 1 / c_k of one dimension at frequency k (kernels' normalisation psi = phi / phi(0)).
+double inv_c_at(int window, int m, int64_t n, double b, double k);
 
 class Engine {
  public:

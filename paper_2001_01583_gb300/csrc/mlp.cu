@@ -223,6 +223,7 @@ struct nfft_mlp {
   std::vector<int> cand_m, cand_window;
   std::vector<double> feat_mean, feat_std, out_mean, out_std;
   double err_margin = 0.5;    // qualify when predicted error <= eps * err_margin
+  double fp32_floor = 0.0;    // FP32 rounding floor per unit of scaling amplification
   float* xq = nullptr;        // one query on the device
   float* yq = nullptr;
 };
@@ -390,10 +391,10 @@ int nfft_mlp_train_step(nfft_mlp* p, const float* x_dev, const float* t_dev, con
 
 int nfft_picker_configure(nfft_mlp* p, int n_candidates, const double* cand_sigma, const int* cand_m,
                           const int* cand_window, const double* feat_mean, const double* feat_std,
-                          const double* out_mean, const double* out_std, double err_margin) {
+                          const double* out_mean, const double* out_std, double err_margin, double fp32_floor) {
   if (!p || n_candidates < 1 || 2 * n_candidates != p->d.n_out || p->d.n_in != NFFT_PICKER_FEATURES)
     return NFFT_ERR_INVALID_ARG;
-  if (!(err_margin > 0.0) || err_margin > 1.0) return NFFT_ERR_INVALID_ARG;
+  if (!(err_margin > 0.0) || err_margin > 1.0 || !(fp32_floor >= 0.0)) return NFFT_ERR_INVALID_ARG;
   if (!cand_sigma || !cand_m || !cand_window || !feat_mean || !feat_std || !out_mean || !out_std)
     return NFFT_ERR_INVALID_ARG;
   p->cand_sigma.assign(cand_sigma, cand_sigma + n_candidates);
@@ -404,6 +405,7 @@ int nfft_picker_configure(nfft_mlp* p, int n_candidates, const double* cand_sigm
   p->out_mean.assign(out_mean, out_mean + p->d.n_out);
   p->out_std.assign(out_std, out_std + p->d.n_out);
   p->err_margin = err_margin;
+  p->fp32_floor = fp32_floor;
   p->configured = true;
   return NFFT_OK;
 }
@@ -441,9 +443,10 @@ int nfft_rule_of_thumb(double eps, double* sigma, int* m, int* window) {
   return NFFT_OK;
 }
 
-int nfft_pick_params(nfft_mlp* p, int d, const int64_t* N, int64_t M, double cluster_std, double eps, double* sigma,
-                     int* m, int* window, int* used_fallback) {
+int nfft_pick_params(nfft_mlp* p, int d, const int64_t* N, int64_t M, double cluster_std, double eps, int precision,
+                     double* sigma, int* m, int* window, int* used_fallback) {
   if (!sigma || !m || !window) return NFFT_ERR_INVALID_ARG;
+  if (precision != NFFT_FP64 && precision != NFFT_FP32_MIXED) return NFFT_ERR_INVALID_ARG;
   double f[NFFT_PICKER_FEATURES];
   const int s = nfft_picker_features(d, N, M, cluster_std, eps, f);
   if (s != NFFT_OK) return s;
@@ -467,6 +470,14 @@ int nfft_pick_params(nfft_mlp* p, int d, const int64_t* N, int64_t M, double clu
       for (int t = 0; t < d; ++t)
         if (std::ceil(p->cand_sigma[c] * (double)N[t]) < 2.0 * p->cand_m[c] + 2.0) ok = false;
       if (!ok) continue;
+      if (precision == NFFT_FP32_MIXED) {
+        // the FP32 grid's rounding, amplified by the scaling step
+        double amp = 0.0;
+        if (nfft_deconv_amplification(d, N, p->cand_sigma[c], p->cand_m[c], p->cand_window[c], &amp, nullptr) !=
+                NFFT_OK ||
+            p->fp32_floor * amp > eps * p->err_margin)
+          continue;
+      }
       const double err = y[c] * p->out_std[c] + p->out_mean[c];              // predicted log10(error / eps)
       const double cost = y[K + c] * p->out_std[K + c] + p->out_mean[K + c];  // predicted log10(cost)
       if (err <= std::log10(p->err_margin) && (best < 0 || cost < best_cost)) {

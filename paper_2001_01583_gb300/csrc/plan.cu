@@ -53,6 +53,36 @@ int nfft_plan_params(int d, const int64_t* N, double sigma, int m, int window, i
   return NFFT_OK;
 }
 
+int nfft_deconv_amplification(int d, const int64_t* N, double sigma, int m, int window, double* rms, double* peak) {
+  int64_t n[3] = {1, 1, 1};
+  int taps = 0;
+  const int st = nfft_plan_params(d, N, sigma, m, window, n, &taps);
+  if (st != NFFT_OK) return st;
+  double r = 1.0, x = 1.0;
+  for (int t = 0; t < d; ++t) {
+    const double b = shape_param(window, m, (double)n[t] / (double)N[t]);
+    const double c0 = inv_c_at(window, m, n[t], b, 0.0);
+    // at most 4097 frequencies per dimension (all of them up to N_t = 4096)
+    const int64_t step = N[t] > 4096 ? (N[t] + 4095) / 4096 : 1;
+    double s2 = 0.0, mx = 0.0;
+    int64_t cnt = 0;
+    for (int64_t a = 0; a < N[t]; a += step) {
+      const double v = inv_c_at(window, m, n[t], b, (double)(a - N[t] / 2)) / c0;
+      s2 += v * v;
+      mx = v > mx ? v : mx;
+      ++cnt;
+    }
+    // the edge frequency -N_t/2 carries the maximum
+    const double edge = inv_c_at(window, m, n[t], b, (double)(-N[t] / 2)) / c0;
+    mx = edge > mx ? edge : mx;
+    r *= std::sqrt(s2 / (double)cnt);
+    x *= mx;
+  }
+  if (rms) *rms = r;
+  if (peak) *peak = x;
+  return NFFT_OK;
+}
+
 int nfft_plan_create(nfft_plan** out, int d, const int64_t* N, int64_t M, double sigma, int m, int window,
                      int precision, void* cuda_stream) {
   if (!out) return NFFT_ERR_INVALID_ARG;

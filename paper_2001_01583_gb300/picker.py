@@ -9,7 +9,10 @@ eps and the log10 of the transform's cost.  The library's own kernels train
 and evaluate it (nfft_mlp_*: FP16 weights, FP32 accumulation, Adam on FP32
 master weights), and nfft_pick_params takes the cheapest candidate predicted
 to reach eps with a margin, or the rule of thumb (Kaiser-Bessel, sigma = 2,
-m = ceil(ln(1/eps) / (2 pi sqrt(1 - 1/sigma)))) when none qualifies.
+m = ceil(ln(1/eps) / (2 pi sqrt(1 - 1/sigma)))) when none qualifies.  For the
+FP32 form a candidate must also keep the FP32 rounding floor, which the
+scaling step amplifies by c_0 / c_k (large for small sigma and large m),
+below eps: floor = kappa * rms(c_0 / c_k), kappa fitted to FP32 runs.
 
 Training data are runs of the plain method itself: FP64 adjoint transforms
 (Eq. 5) of random problems with every candidate, each error measured against
@@ -160,19 +163,43 @@ def rule_of_thumb(eps):
     return s.value, m.value, w.value
 
 
+def amplification(N, sigma, m, window):
+    """rms over I_N of c_0 / c_k (the scaling step's amplification of grid
+    rounding), from the library's host rule nfft_deconv_amplification."""
+    lib = _lib.load()
+    Narr = (ctypes.c_int64 * len(N))(*[int(v) for v in N])
+    rms = ctypes.c_double()
+    _lib.check(lib.nfft_deconv_amplification(len(N), Narr, float(sigma), int(m), int(window), ctypes.byref(rms), None),
+               "nfft_deconv_amplification")
+    return rms.value
+
+
 def valid(N, sigma, m):
     """The picker's validity rule for a candidate (as in nfft_pick_params):
     ceil(sigma N_t) >= 2m + 2 in every dimension."""
     return all(math.ceil(sigma * n) >= 2 * m + 2 for n in N)
 
 
+DEFAULT_BINS = {1: (1024,), 2: (32, 32), 3: (8, 8, 16)}
+
+
 def cost_terms(N, M, sigma, m, window):
-    """Work terms of one adjoint: M taps^d (window evaluations and cell
-    updates), P log2 P (FFT of P = prod n_t cells), P (grid clear, scaling),
-    M (sort, per-point work), 1 (launches)."""
+    """Work terms of one adjoint: cell updates M taps^d split by where they
+    run (dense bins on shared tiles, sparse bins on grid atomics: at uniform
+    density, a bin is sparse below one point per taps^d / 2 tile cells, the
+    library's default split), M d taps (window evaluations), P log2 P (FFT
+    of P = prod n_t cells), P (grid clear, scaling), M (sort, per-point
+    work), 1 (launches)."""
     n, taps = plan_params(N, sigma, m, window)
     P = float(np.prod(n))
-    return np.array([float(M) * taps ** len(N), P * math.log2(max(P, 2.0)), P, float(M), 1.0])
+    d = len(N)
+    bins = [min(b, nt) for b, nt in zip(DEFAULT_BINS[d], n)]
+    per_bin = float(M) * float(np.prod(bins)) / P
+    tile = float(np.prod([b + taps - 1 for b in bins]))
+    sparse = per_bin < 2.0 * tile / taps ** d
+    updates = float(M) * taps ** d
+    return np.array([0.0 if sparse else updates, updates if sparse else 0.0, float(M) * d * taps,
+                     P * math.log2(max(P, 2.0)), P, float(M), 1.0])
 
 
 class CostModel:
@@ -299,6 +326,43 @@ def measure_errors(pb, candidates=CANDIDATES, precision="fp64"):
     return errs
 
 
+def measure_errors_fp32(pb, candidates=CANDIDATES):
+    """Relative l2 error of the FP32 adjoint of every valid candidate
+    against the FP64 reference run; NaN where invalid."""
+    N, M = pb["N"], pb["M"]
+    ok = [i for i, (s, m, w) in enumerate(candidates) if valid(N, s, m)]
+    x = torch.from_numpy(problem_points(pb)).cuda()
+    f64 = inputs.complex_normal((1, M), seed=pb["seed"] + 7)
+    s, m, w = REFERENCE
+    with Plan(N, M, s, m, w, "fp64") as p:
+        p.set_points(x)
+        ref = p.adjoint(torch.from_numpy(f64[0]).cuda())
+        p.sync()
+    f = torch.from_numpy(f64.astype(np.complex64)).cuda()
+    items = [dict(N=N, M=M, sigma=candidates[i][0], m=candidates[i][1], window=candidates[i][2]) for i in ok]
+    errs = np.full(len(candidates), np.nan)
+    with Batch(items, "fp32") as b:
+        b.set_points([x] * len(items))
+        A = b.adjoint([f] * len(items))
+        b.sync()
+        rnorm = torch.linalg.vector_norm(ref).item()
+        for j, i in enumerate(ok):
+            errs[i] = torch.linalg.vector_norm(A[j][0].to(torch.complex128) - ref).item() / rnorm
+    return errs
+
+
+def fit_fp32_floor(problems, errors64, errors32, quantile=0.95):
+    """FP32 rounding floor per unit of scaling amplification: a high quantile
+    of err32 / amplification over runs whose FP64 (window) error is far
+    below their FP32 error."""
+    ratios = []
+    for pb, e64, e32 in zip(problems, errors64, errors32):
+        for c, (s, m, w) in enumerate(CANDIDATES):
+            if np.isfinite(e32[c]) and np.isfinite(e64[c]) and e64[c] < 0.1 * e32[c]:
+                ratios.append(e32[c] / amplification(pb["N"], s, m, w))
+    return float(np.quantile(ratios, quantile)), len(ratios)
+
+
 def generate_runs(problems, log=None):
     """Error table (problems x candidates) from plain-method runs."""
     E = np.full((len(problems), len(CANDIDATES)), np.nan)
@@ -366,31 +430,35 @@ def sample_cost_problems(count, seed):
 class Picker:
     """The trained network with its normalisation and candidate table."""
 
-    def __init__(self, mlp, feat_mean, feat_std, out_mean, out_std, err_margin=0.5, meta=None):
+    def __init__(self, mlp, feat_mean, feat_std, out_mean, out_std, err_margin=0.5, meta=None, fp32_floor=0.0):
         self.mlp = mlp
         self.feat_mean = np.asarray(feat_mean, dtype=np.float64)
         self.feat_std = np.asarray(feat_std, dtype=np.float64)
         self.out_mean = np.asarray(out_mean, dtype=np.float64)
         self.out_std = np.asarray(out_std, dtype=np.float64)
         self.meta = dict(meta or {})
+        self.fp32_floor = float(fp32_floor)
         self.configure(err_margin)
 
-    def configure(self, err_margin):
+    def configure(self, err_margin, fp32_floor=None):
         self.err_margin = float(err_margin)
+        if fp32_floor is not None:
+            self.fp32_floor = float(fp32_floor)
         K = len(CANDIDATES)
         dbl = lambda a: (ctypes.c_double * len(a))(*[float(v) for v in a])
         _lib.check(self.mlp._lib.nfft_picker_configure(
             self.mlp._h, K, dbl([c[0] for c in CANDIDATES]), (ctypes.c_int * K)(*[c[1] for c in CANDIDATES]),
             (ctypes.c_int * K)(*[c[2] for c in CANDIDATES]), dbl(self.feat_mean), dbl(self.feat_std),
-            dbl(self.out_mean), dbl(self.out_std), self.err_margin), "nfft_picker_configure")
+            dbl(self.out_mean), dbl(self.out_std), self.err_margin, self.fp32_floor), "nfft_picker_configure")
 
-    def pick(self, N, M, cluster_std, eps):
-        """(sigma, m, window, used_fallback) for a problem."""
+    def pick(self, N, M, cluster_std, eps, precision="fp32"):
+        """(sigma, m, window, used_fallback) for a problem solved in `precision`."""
         N = tuple(int(v) for v in N)
         Narr = (ctypes.c_int64 * 3)(*(list(N) + [1] * (3 - len(N))))
+        prec = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         s, m, w, fb = ctypes.c_double(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _lib.check(self.mlp._lib.nfft_pick_params(self.mlp._h, len(N), Narr, int(M), float(cluster_std), float(eps),
-                                                  ctypes.byref(s), ctypes.byref(m), ctypes.byref(w),
+                                                  prec, ctypes.byref(s), ctypes.byref(m), ctypes.byref(w),
                                                   ctypes.byref(fb)), "nfft_pick_params")
         return s.value, m.value, w.value, bool(fb.value)
 
@@ -409,7 +477,7 @@ class Picker:
         return dict(format="gbnfft-picker-1", n_in=self.mlp.n_in, n_hidden=self.mlp.n_hidden, n_out=self.mlp.n_out,
                     candidates=[list(c) for c in CANDIDATES], feat_mean=self.feat_mean.tolist(),
                     feat_std=self.feat_std.tolist(), out_mean=self.out_mean.tolist(), out_std=self.out_std.tolist(),
-                    err_margin=self.err_margin, epoch=epoch,
+                    err_margin=self.err_margin, fp32_floor=self.fp32_floor, epoch=epoch,
                     params_f32_b64=base64.b64encode(w.astype("<f4").tobytes()).decode("ascii"), meta=self.meta)
 
     def save(self, path, epoch=None):
@@ -425,7 +493,8 @@ class Picker:
             raise ValueError("%s: not a checkpoint of this picker" % path)
         mlp = MLP(st["n_in"], st["n_hidden"], st["n_out"], stream=stream)
         mlp.set_params(np.frombuffer(base64.b64decode(st["params_f32_b64"]), dtype="<f4"))
-        pk = cls(mlp, st["feat_mean"], st["feat_std"], st["out_mean"], st["out_std"], st["err_margin"], st["meta"])
+        pk = cls(mlp, st["feat_mean"], st["feat_std"], st["out_mean"], st["out_std"], st["err_margin"], st["meta"],
+                 st.get("fp32_floor", 0.0))
         pk.epoch = st.get("epoch")
         return pk
 
@@ -488,7 +557,7 @@ def choose_margin(picker, problems, errors, eps_list, margins=(0.5, 0.35, 0.25, 
         bad = 0
         for p, pb in enumerate(problems):
             for eps in eps_list:
-                s, m, w, fb = picker.pick(pb["N"], pb["M"], pb["std"], eps)
+                s, m, w, fb = picker.pick(pb["N"], pb["M"], pb["std"], eps, precision="fp64")
                 if fb:
                     continue
                 c = CANDIDATES.index((s, m, w))
@@ -506,6 +575,7 @@ def main(argv=None):
     ap.add_argument("--val-problems", type=int, default=40)
     ap.add_argument("--eps-per-problem", type=int, default=12)
     ap.add_argument("--cost-problems", type=int, default=600)
+    ap.add_argument("--fp32-problems", type=int, default=40)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", required=True)
@@ -537,8 +607,13 @@ def main(argv=None):
     pk = Picker(mlp, fm, fs, om, osd, 0.5, meta)
     losses = train(pk, X, T, W, epochs=args.epochs, seed=args.seed, log=log)
     margin = choose_margin(pk, val, Ev, eps_list=[1e-9, 1e-7, 1e-5, 1e-4, 1e-3])
-    pk.configure(margin)
-    pk.meta.update(final_loss=losses[-1], first_loss=losses[0], err_margin=margin, seconds=time.time() - t0)
+    sub = probs[:args.fp32_problems]
+    E32 = [measure_errors_fp32(pb) for pb in sub]
+    floor, n_fit = fit_fp32_floor(sub, E[:len(sub)], E32)
+    pk.configure(margin, floor)
+    log("fp32 floor %.3g per unit amplification (%d runs)" % (floor, n_fit))
+    pk.meta.update(final_loss=losses[-1], first_loss=losses[0], err_margin=margin, fp32_floor=floor,
+                   fp32_floor_runs=n_fit, seconds=time.time() - t0)
     pk.save(args.out, epoch=args.epochs)
     log("saved %s: loss %.5f -> %.5f, margin %.2f, %.1f s" % (args.out, losses[0], losses[-1], margin,
                                                             time.time() - t0))

@@ -136,6 +136,10 @@ WIDE = [
     ((28, 30, 26), 1500, "kaiser_bessel", 9, "fp64", False),    # 18
     ((30, 28, 26), 1500, "gaussian", 9, "fp64", False),         # 20
 ]
+# FP64 tiles of 22 to 26 taps do not fit shared memory: those windows run on
+# the other kernels (the thread-per-point tiled one, or global atomics)
+WIDE_FP64_OTHER = [((26, 28, 24), 600, "kaiser_bessel", 11), ((24, 26, 28), 500, "kaiser_bessel", 12),
+                   ((28, 24, 26), 400, "gaussian", 12)]
 
 
 def _amplification(N, n, m, window):
@@ -220,6 +224,17 @@ def test_sparse_and_dense_subproblems_mixed(N, M, window, m, precision):
         err_a = np.max(np.abs(a - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2))
         assert err_a <= FP32_ELEM, err_a
         _elementwise(b, sb, FP32_ELEM * amp_rms)
+
+
+@pytest.mark.parametrize("N,M,window,m", WIDE_FP64_OTHER)
+def test_wide_windows_fp64_without_plane_kernels(N, M, window, m):
+    x = inputs.uniform_points(M, 3, seed=35)
+    f = inputs.complex_normal(M, seed=36)
+    fh = inputs.complex_normal(N, seed=37)
+    a, b, info = _run(N, x, f, fh, 2.0, m, window, "fp64")
+    assert info["method"] in (1, 2)
+    _elementwise(a, S.adjoint(x, f, N, 2.0, m, WIN[window]), 1e-12)
+    _elementwise(b, S.forward(x, fh, N, 2.0, m, WIN[window]), 1e-12)
 
 
 # ---- rows longer than one scaling segment (4096 elements) --------------------

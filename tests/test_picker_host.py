@@ -34,10 +34,12 @@ def test_pick_without_network_falls_back():
     lib = _lib.load()
     N = (ctypes.c_int64 * 3)(64, 64, 64)
     s, m, w, fb = ctypes.c_double(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    assert lib.nfft_pick_params(None, 3, N, 10 ** 6, 0.0, 1e-7, ctypes.byref(s), ctypes.byref(m), ctypes.byref(w),
-                                ctypes.byref(fb)) == _lib.OK
+    assert lib.nfft_pick_params(None, 3, N, 10 ** 6, 0.0, 1e-7, _lib.FP32_MIXED, ctypes.byref(s), ctypes.byref(m),
+                                ctypes.byref(w), ctypes.byref(fb)) == _lib.OK
     assert (s.value, m.value, w.value, fb.value) == picker.rule_of_thumb(1e-7) + (1,)
-    assert lib.nfft_pick_params(None, 3, N, 10 ** 6, 0.0, -1.0, ctypes.byref(s), ctypes.byref(m), ctypes.byref(w),
+    assert lib.nfft_pick_params(None, 3, N, 10 ** 6, 0.0, -1.0, _lib.FP64, ctypes.byref(s), ctypes.byref(m),
+                                ctypes.byref(w), ctypes.byref(fb)) == _lib.ERR_INVALID_ARG
+    assert lib.nfft_pick_params(None, 3, N, 10 ** 6, 0.0, 1e-7, 7, ctypes.byref(s), ctypes.byref(m), ctypes.byref(w),
                                 ctypes.byref(fb)) == _lib.ERR_INVALID_ARG
 
 
@@ -54,15 +56,19 @@ def test_candidates_and_validity():
 def test_cost_terms_and_fit():
     t = picker.cost_terms((64, 64, 64), 10 ** 6, 2.0, 4, _lib.KAISER_BESSEL)
     P = 128.0 ** 3
-    assert np.allclose(t, [1e6 * 8 ** 3, P * math.log2(P), P, 1e6, 1.0])
+    # 488 points per 8 x 8 x 16 bin: dense
+    assert np.allclose(t, [1e6 * 8 ** 3, 0.0, 1e6 * 3 * 8, P * math.log2(P), P, 1e6, 1.0])
     tg = picker.cost_terms((64, 64, 64), 10 ** 6, 2.0, 4, _lib.GAUSSIAN)
-    assert tg[0] == 1e6 * 10 ** 3
+    assert tg[0] == 1e6 * 10 ** 3 and tg[2] == 1e6 * 3 * 10
+    # 2e4 points: 10 per bin, below 2 * 15 * 15 * 23 / 512 = 20.2: sparse
+    ts = picker.cost_terms((64, 64, 64), 20000, 2.0, 4, _lib.KAISER_BESSEL)
+    assert ts[0] == 0.0 and ts[1] == 20000 * 8 ** 3
     # the fit recovers a known nonnegative model from exact data
     rng = np.random.default_rng(0)
-    coef = np.array([2e-9, 3e-10, 0.0, 1e-7, 0.02])
+    coef = np.array([2e-9, 9e-9, 5e-9, 3e-10, 0.0, 1e-7, 0.02])
     rows = [picker.cost_terms((int(n),) * 3, int(M), s, m, w)
-            for n, M, s, m, w in zip(rng.choice([16, 32, 64, 128], 40), 10 ** rng.uniform(3, 7, 40),
-                                     rng.choice([1.25, 1.5, 2.0], 40), rng.integers(2, 9, 40), rng.integers(0, 2, 40))]
+            for n, M, s, m, w in zip(rng.choice([16, 32, 64, 128], 60), 10 ** rng.uniform(3, 7, 60),
+                                     rng.choice([1.25, 1.5, 2.0], 60), rng.integers(2, 9, 60), rng.integers(0, 2, 60))]
     times = np.array(rows) @ coef
     model = picker.CostModel.fit(rows, times)
     assert np.allclose(np.array(rows) @ model.coef, times, rtol=1e-6)
@@ -75,3 +81,23 @@ def test_normalisers_ignore_unlabelled_outputs():
     fm, fs, om, osd = picker.normalisers(X, T, W)
     assert np.allclose(fm, [2.0, 5.0]) and np.allclose(fs, [1.0, 1.0])
     assert np.allclose(om, [3.0, 7.0]) and np.allclose(osd, [1.0, 1.0])
+
+
+def test_deconvolution_amplification_against_oracle():
+    """rms and peak of c_0 / c_k over I_N from the library's host rule agree
+    with the oracle's transforms of the windows (its n_t phi_hat)."""
+    from oracle import nfft_steps as S
+    lib = _lib.load()
+    for N, sigma, m, window in [((64,), 2.0, 4, _lib.KAISER_BESSEL), ((36, 30), 1.25, 5, _lib.KAISER_BESSEL),
+                                ((32, 28, 24), 1.5, 6, _lib.GAUSSIAN), ((20, 16, 18), 2.0, 12, _lib.GAUSSIAN)]:
+        Narr = (ctypes.c_int64 * len(N))(*N)
+        rms, peak = ctypes.c_double(), ctypes.c_double()
+        assert lib.nfft_deconv_amplification(len(N), Narr, sigma, m, window, ctypes.byref(rms),
+                                             ctypes.byref(peak)) == _lib.OK
+        n = [S.oversampled_size(v, sigma, m) for v in N]
+        r, p = 1.0, 1.0
+        for wt in S.scaling_weights(window, m, list(N), n):
+            a = np.abs(wt).max() / np.abs(wt)
+            r *= np.sqrt(np.mean(a ** 2))
+            p *= a.max()
+        assert abs(rms.value / r - 1) < 1e-9 and abs(peak.value / p - 1) < 1e-9, (N, rms.value, r, peak.value, p)
