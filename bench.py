@@ -288,6 +288,7 @@ def run_ours(args, wl, rank, world):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    launches0 = sum(p.info()["kernel_launches"] for p in plans)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with torch.cuda.stream(stream):
@@ -297,6 +298,7 @@ def run_ours(args, wl, rank, world):
             step()
             ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    launches_timed = sum(p.info()["kernel_launches"] for p in plans) - launches0
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -362,8 +364,6 @@ def run_ours(args, wl, rank, world):
         v, threads, desc = _oracle_sample(wl)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
-    # kernels of this library per set and step: 6 in set_points, spread + scale, subdivide + interpolate
-    launches_per_step = len(xs) * (6 + 2 + 2)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
@@ -372,7 +372,7 @@ def run_ours(args, wl, rank, world):
                        "l2": "flushed between timed steps (512 MB write outside the step events)",
                        "parallelism": "independent replicas x%d" % world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches_timed,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -420,6 +420,7 @@ def run_batch(args, wl, rank, world):
     if world > 1:
         dist.barrier()
     sampler.start()
+    launches0 = b.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -429,6 +430,7 @@ def run_batch(args, wl, rank, world):
             b.forward(hs, outs_f)
             ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    launches_timed = b.kernel_launches() - launches0
     clocks = sampler.stop()
     ms = float(np.sum([x.elapsed_time(y) for x, y in ev])) / args.steps
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -443,22 +445,24 @@ def run_batch(args, wl, rank, world):
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points, "items": len(items),
                        "precision": args.precision, "autotuned": bool(args.autotune),
                        "l2": "flushed between timed steps (512 MB write outside the step events)"},
-            "gpu_launches": None, "clocks": clocks}
+            "gpu_launches": launches_timed, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
     return 0
 
 
-def _timed(step, stream, dev, steps, warmup, flush):
+def _timed(step, stream, dev, steps, warmup, flush, plans=()):
     """Device ms per step (CUDA events on the stream, L2 flushed between
-    steps outside the events) and the clocks seen meanwhile."""
+    steps outside the events), the clocks seen meanwhile and this library's
+    kernels launched by `plans` inside the timed region."""
     import torch
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             step()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(dev.index)
+    launches0 = sum(p.info()["kernel_launches"] for p in plans)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
@@ -469,7 +473,8 @@ def _timed(step, stream, dev, steps, warmup, flush):
             ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    return float(np.sum([a.elapsed_time(b) for a, b in ev])) / steps, clocks
+    launches = sum(p.info()["kernel_launches"] for p in plans) - launches0
+    return float(np.sum([a.elapsed_time(b) for a, b in ev])) / steps, clocks, launches
 
 
 def run_extra(args, wl, rank, world):
@@ -487,7 +492,7 @@ def run_extra(args, wl, rank, world):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     N, M = wl["N"], wl["M"]
-    extra, points_per_step, launches = {}, 0, 0
+    extra, points_per_step = {}, 0
     prec = args.precision
     if args.workload == "1d":
         prec = "fp64"
@@ -502,7 +507,7 @@ def run_extra(args, wl, rank, world):
             plan.set_points(x)
             plan.adjoint(f, out=oa)
             plan.forward(fh, out=of)
-        points_per_step, launches = 2 * M, 10
+        points_per_step = 2 * M
         plans = [plan]
     elif args.workload == "fluorite":
         r, q, L = inputs.fluorite(32)
@@ -514,7 +519,7 @@ def run_extra(args, wl, rank, world):
         def step():
             plan.set_points(xq)
             out["e"] = plan.ewald_reciprocal(qd, L, 0.6)
-        points_per_step, launches = len(q), 9
+        points_per_step = len(q)
         plans = [plan]
     else:   # picker
         from paper_2001_01583_gb300 import picker
@@ -535,13 +540,13 @@ def run_extra(args, wl, rank, world):
                 p.adjoint(f, out=oa)
                 p.forward(fh, out=of)
             return st
-        ms_rule, _ = _timed(make(plans[1]), stream, dev, max(2, args.steps // 2), args.warmup, flush)
+        ms_rule, _, _ = _timed(make(plans[1]), stream, dev, max(2, args.steps // 2), args.warmup, flush)
         step = make(plans[0])
-        points_per_step, launches = 2 * M, 12
+        points_per_step = 2 * M
         extra = {"picked": {"sigma": s_, "m": m_, "window": "gaussian" if w_ == 0 else "kaiser_bessel",
                             "fallback": fb}, "rule_of_thumb": {"sigma": rs, "m": rm, "window": "kaiser_bessel"},
                  "rule_ms_per_step": ms_rule, "eps": eps}
-    ms, clocks = _timed(step, stream, dev, args.steps, args.warmup, flush)
+    ms, clocks, launches = _timed(step, stream, dev, args.steps, args.warmup, flush, plans=plans[:1])
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -555,7 +560,7 @@ def run_extra(args, wl, rank, world):
     line = {"metric": METRIC, "value": points_per_step * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
-            "data": "synthetic", "config": cfg, "gpu_launches": launches * args.steps, "clocks": clocks}
+            "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for p in plans:

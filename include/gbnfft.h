@@ -101,9 +101,16 @@ typedef enum {
                                    NFFT_METHOD_GRID_WARP kernel, the rest on the
                                    tiled one (0 = automatic: one point per
                                    W^d / 2 tile cells, -1 = never) */
-  NFFT_OPT_SPARSE_POINTS_INTERP = 11 /* the same for interpolation (0 = automatic:
+  NFFT_OPT_SPARSE_POINTS_INTERP = 11, /* the same for interpolation (0 = automatic:
                                    one point per W^d / 5 tile cells; gathers
                                    need no atomics, so the split sits higher) */
+  NFFT_OPT_OWNER_SPREAD = 12    /* d = 3: 1 spreads the sparse bins by their
+                                   cells' owners (a warp per bin, no atomics,
+                                   every cell written once) where the grid
+                                   allows (n_t >= bin_t + W - 1); 0 (default)
+                                   uses the grid-warp atomics, which measure
+                                   faster (an owner pass repeats each point's
+                                   weights for every owner it touches) */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -139,6 +146,9 @@ typedef struct {
   int interp_threads;        /* NFFT_OPT_INTERP_THREADS (0 = chosen per launch) */
   int sparse_points;         /* spreading subproblems below this many points use the grid-warp kernel */
   int sparse_points_interp;  /* the same for interpolation */
+  int owner_spread;          /* 1: sparse bins are spread by the owner kernel */
+  int64_t kernel_launches;   /* this library's kernels launched by the plan so far
+                                (cuFFT's own kernels and memsets not included) */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling
@@ -305,6 +315,9 @@ int nfft_batch_autotune(nfft_batch* batch, int reps, double* best_ms);
 /* Stage times with NFFT_OPT_PROFILE on: a whole adjoint graph is booked as
  * NFFT_STAGE_SPREAD, a whole forward graph as NFFT_STAGE_INTERP. */
 int nfft_batch_stage_times(nfft_batch* batch, double* ms, int64_t* launches, int reset);
+/* This library's kernels launched by the batch so far, graph replays
+ * included (cuFFT's own kernels and memsets not included). */
+int nfft_batch_kernel_launches(const nfft_batch* batch, int64_t* count);
 
 /* ---- learned parameter picker ---------------------------------------------
  * A small MLP, n_in -> n_hidden -> n_hidden -> n_out with ReLU, trained and

@@ -32,7 +32,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
 
 METHOD_AUTO, METHOD_TILED, METHOD_GLOBAL, METHOD_WARP, METHOD_GRID_WARP = 0, 1, 2, 3, 4
 (OPT_METHOD, OPT_BIN_0, OPT_BIN_1, OPT_BIN_2, OPT_MAX_SUBPROBLEM, OPT_RHS_CAPACITY, OPT_PROFILE, OPT_THREADS,
- OPT_SPREAD_THREADS, OPT_INTERP_THREADS, OPT_SPARSE_POINTS, OPT_SPARSE_POINTS_INTERP) = range(12)
+ OPT_SPREAD_THREADS, OPT_INTERP_THREADS, OPT_SPARSE_POINTS, OPT_SPARSE_POINTS_INTERP, OPT_OWNER_SPREAD) = range(13)
 STAGES = ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp")
 
 
@@ -58,6 +58,8 @@ class PlanInfo(ctypes.Structure):
         ("interp_threads", ctypes.c_int),
         ("sparse_points", ctypes.c_int),
         ("sparse_points_interp", ctypes.c_int),
+        ("owner_spread", ctypes.c_int),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 
@@ -138,6 +140,7 @@ def _declare(lib):
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "nfft_deconv_amplification": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "nfft_batch_kernel_launches": (ctypes.c_int, [vp, i64p]),
         "nfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nfft_version": (ctypes.c_int, []),
     }

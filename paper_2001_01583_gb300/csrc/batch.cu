@@ -89,4 +89,10 @@ int nfft_batch_stage_times(nfft_batch* p, double* ms, int64_t* launches, int res
   return p->eng.stage_times(ms, launches, reset);
 }
 
+int nfft_batch_kernel_launches(const nfft_batch* p, int64_t* count) {
+  if (!p || !count) return NFFT_ERR_INVALID_ARG;
+  *count = p->eng.launched();
+  return NFFT_OK;
+}
+
 }  // extern "C"

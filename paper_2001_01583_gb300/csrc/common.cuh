@@ -129,6 +129,8 @@ struct SortedPoints {
   const SubProblem* subs;
   const int* sub_start;      // exclusive scan of subproblems per global bin
   const int* num_subs;       // device scalar: all subproblems
+  const int* bin_count;      // points per global bin
+  const int* bin_start;      // first sorted position per global bin
 };
 
 // Pack / unpack of in-bin offsets: 32 bits split evenly over d dimensions.

@@ -335,6 +335,7 @@ int Engine::build_layout() {
 
   struct Choice {
     int bin[3], tile[3], pitch, method, taps, sparse, sparse_interp;
+    bool owner;
   };
   std::vector<Choice> ch(nitems);
   for (int i = 0; i < nitems; ++i) {
@@ -426,6 +427,22 @@ int Engine::build_layout() {
       c.sparse = pick(sparse_opt, 2.0);
       c.sparse_interp = pick(sparse_interp_opt, 5.0);
     }
+    // 3-D sparse bins spread by their cells' owners (no atomics): needs one
+    // periodic image per footprint (n_t >= bin_t + W - 1) and the warps'
+    // tiles in shared memory
+    c.owner = false;
+    if (s.d == 3 && c.sparse > 0 && owner_enabled) {
+      const bool built = (precision == NFFT_FP64 ? owner_kernel_f64(c.taps) : owner_kernel_f32(c.taps)) != nullptr;
+      bool fits = built;
+      for (int t = 0; t < 3; ++t) {
+        fits = fits && n[t] >= (int64_t)c.bin[t] + c.taps - 1;
+        // bins within the reach (bin + W - 1 cells, possibly split in two by the wrap)
+        fits = fits && (c.bin[t] + c.taps - 2) / c.bin[t] + 3 <= kOwnerReachHost;
+      }
+      const size_t osmem = (size_t)kOwnerWarpsHost *
+                           ((size_t)c.bin[0] * c.bin[1] * c.bin[2] * csize + (size_t)3 * c.taps * (csize / 2));
+      c.owner = fits && osmem <= smem_optin;
+    }
   }
   // group items into kernel classes (stable by first appearance)
   // (items with different right-hand-side counts get their own launch: the
@@ -434,7 +451,7 @@ int Engine::build_layout() {
     return specs[a].d == specs[b].d && ch[a].taps == ch[b].taps && specs[a].window == specs[b].window &&
            (single || specs[a].nrhs == specs[b].nrhs) &&
            ch[a].method == ch[b].method && ch[a].sparse == ch[b].sparse &&
-           ch[a].sparse_interp == ch[b].sparse_interp && ch[a].bin[0] == ch[b].bin[0] &&
+           ch[a].sparse_interp == ch[b].sparse_interp && ch[a].owner == ch[b].owner && ch[a].bin[0] == ch[b].bin[0] &&
            ch[a].bin[1] == ch[b].bin[1] &&
            ch[a].bin[2] == ch[b].bin[2];
   };
@@ -535,6 +552,7 @@ int Engine::build_layout() {
       kc.pitch = c.pitch;
       kc.sparse_points = c.sparse;
       kc.sparse_points_interp = c.sparse_interp;
+      kc.owner = c.owner;
       kc.item_begin = k;
       kc.bin_begin = bin_off[k];
       kc.max_nrhs = 0;
@@ -548,6 +566,12 @@ int Engine::build_layout() {
     kc.max_subs += nb_total + s.M / max_sub + 1;
   }
   total_points = pts_off[nitems];
+  // an FFT class needs no clearing before spreading when the owner kernel
+  // writes every grid in it
+  for (auto& fc : fclasses) fc.owner_written = true;
+  for (const auto& kc : kclasses)
+    for (int k = kc.item_begin; k < kc.item_end; ++k)
+      if (!kc.owner) fclasses[item_fclass[order[k]]].owner_written = false;
   total_bins = bin_off[nitems];
   // device buffers
   int64_t before = device_bytes;
@@ -719,7 +743,11 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.pts.subs = subs;
   a.pts.sub_start = sub_start;
   a.pts.num_subs = num_subs;
+  a.pts.bin_count = bin_count;
+  a.pts.bin_start = bin_start;
   a.items = d_items;
+  a.item_begin = kc.item_begin;
+  a.item_end = kc.item_end;
   a.bin_begin = kc.bin_begin;
   a.bin_end = kc.bin_end;
   a.total_bins = total_bins;
@@ -731,9 +759,16 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.sub_max_count = INT_MAX;
   if (kc.method == NFFT_METHOD_GRID_WARP) return run_gm<Real>(kc, a, spread);
   if (kc.method == NFFT_METHOD_GLOBAL) return run_global<Real>(kc, a, spread);
-  // tiled kernels take the subproblems of at least `split` points, the
-  // grid-warp kernels the rest
+  // tiled kernels take the bins of at least `split` points, the owner
+  // kernel (3-D spreading, first: it writes every cell) or the grid-warp
+  // kernels the rest
   const int split = spread ? kc.sparse_points : kc.sparse_points_interp;
+  if (spread && kc.owner) {
+    TRY(run_owner<Real>(kc, a));
+    a.sub_min_count = split;
+    return kc.method == NFFT_METHOD_WARP ? run_planes<Real>(kc, a, spread, max_nrhs)
+                                         : run_tiled<Real>(kc, a, spread, max_nrhs);
+  }
   a.sub_min_count = split;
   const int st = kc.method == NFFT_METHOD_WARP
                      ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
@@ -742,6 +777,27 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.sub_min_count = 0;
   a.sub_max_count = split;
   return run_gm<Real>(kc, a, spread);
+}
+
+// A warp per owner bin; the launch covers every bin of the class.
+template <typename Real>
+int Engine::run_owner(const KClass& kc, PointKernelArgs<Real>& a) {
+  const void* fn = precision == NFFT_FP64 ? owner_kernel_f64(kc.taps) : owner_kernel_f32(kc.taps);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  const int threads = 32 * kOwnerWarpsHost;
+  const size_t smem = (size_t)kOwnerWarpsHost *
+                      ((size_t)kc.bin[0] * kc.bin[1] * kc.bin[2] * csize + (size_t)3 * kc.taps * (csize / 2));
+  const int per_sm = std::max(1, blocks_per_sm(fn, threads, smem));
+  int64_t blocks = (int64_t)per_sm * num_sms;
+  const int64_t need = ((int64_t)(kc.bin_end - kc.bin_begin) + kOwnerWarpsHost - 1) / kOwnerWarpsHost;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) return NFFT_OK;
+  const int sparse_below = kc.sparse_points;
+  void* args[] = {&a, (void*)&sparse_below};
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, stream));
+  ++kernel_launches;
+  return NFFT_OK;
 }
 
 // One warp per point straight on the grid; kGmSplitHost warps share a subproblem.
@@ -758,6 +814,7 @@ int Engine::run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread) {
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, 0, stream));
+  ++kernel_launches;
   return NFFT_OK;
 }
 
@@ -805,6 +862,7 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
   void* args[] = {&a, &lay};
   CK(cudaFuncSetAttribute(best_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
   CK(cudaLaunchKernel(best_fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
+  ++kernel_launches;
   return NFFT_OK;
 }
 
@@ -848,6 +906,7 @@ int Engine::run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int
   void* args[] = {&a, &lay};
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
+  ++kernel_launches;
   return NFFT_OK;
 }
 
@@ -878,6 +937,7 @@ int Engine::run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, i
   void* args[] = {&a};
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, stream));
+  ++kernel_launches;
   return NFFT_OK;
 }
 
@@ -891,6 +951,7 @@ int Engine::run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread) 
   void* args[] = {&a};
   const int threads = threads_opt > 0 ? threads_opt : 256;
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, 0, stream));
+  ++kernel_launches;
   return NFFT_OK;
 }
 
@@ -912,6 +973,7 @@ int Engine::set_points_impl(const double* x_override) {
   TRY(stage_begin(NFFT_STAGE_SORT, &ev));
   CK(cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)std::max(total_bins, 1), stream));
   CK(launch_bin_count<Real>(s, bin_count, bin_rank, stream));
+  kernel_launches += s.total_points > 0 ? 6 : 4;   // bin count, 2 scans, scatter, subproblem count and fill
   CK(launch_scan(bin_count, bin_start, total_bins, nullptr, stream));
   Real* d[3] = {static_cast<Real*>(delta[0]), static_cast<Real*>(delta[1]), static_cast<Real*>(delta[2])};
   CK(launch_scatter<Real>(s, bin_start, bin_rank, perm, local, d, stream));
@@ -960,7 +1022,7 @@ int Engine::adjoint_single(const void* f, void* fhat, int R) {
     const int nr = (R - r0) < rhs_cap ? (R - r0) : rhs_cap;
     EventPair ev{};
     TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
-    CK(cudaMemsetAsync(it.grid, 0, (size_t)nr * fc.cells * csize, stream));
+    if (!kclasses[0].owner || it.M == 0) CK(cudaMemsetAsync(it.grid, 0, (size_t)nr * fc.cells * csize, stream));
     if (it.M > 0) {
       const void* fin = static_cast<const char*>(f) + (int64_t)r0 * it.M * (int64_t)csize;
       TRY(precision == NFFT_FP64 ? run_points<double>(kclasses[0], true, fin, nullptr, nr)
@@ -975,6 +1037,7 @@ int Engine::adjoint_single(const void* f, void* fhat, int R) {
     const int64_t cblocks = scale_blocks(it.NN / it.N[it.geom.d - 1] * nr, it.N[it.geom.d - 1], false);
     CK(precision == NFFT_FP64 ? launch_deconv_crop<double>(d_items, nullptr, nullptr, cblocks, out, nr, stream)
                               : launch_deconv_crop<float>(d_items, nullptr, nullptr, cblocks, out, nr, stream));
+    kernel_launches += cblocks > 0 ? 1 : 0;
     TRY(stage_end(&ev));
   }
   return NFFT_OK;
@@ -991,6 +1054,7 @@ int Engine::forward_single(const void* fhat, void* f, int R) {
     const int64_t pblocks = scale_blocks(fc.cells / fc.n[fc.d - 1] * nr, fc.n[fc.d - 1], false);
     CK(precision == NFFT_FP64 ? launch_pad_deconv<double>(d_items, nullptr, nullptr, pblocks, hin, nr, stream)
                               : launch_pad_deconv<float>(d_items, nullptr, nullptr, pblocks, hin, nr, stream));
+    kernel_launches += pblocks > 0 ? 1 : 0;
     TRY(stage_end(&ev));
     TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
     TRY(run_fft(fc, nr, item_grid_offset[0], CUFFT_INVERSE));
@@ -1014,7 +1078,8 @@ template <typename Real>
 int Engine::adjoint_table(bool in_graph) {
   EventPair ev{};
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
-  for (auto& fc : fclasses) CK(cudaMemsetAsync(fc.buf, 0, (size_t)fc.grids * fc.cells * csize, stream));
+  for (auto& fc : fclasses)
+    if (!fc.owner_written) CK(cudaMemsetAsync(fc.buf, 0, (size_t)fc.grids * fc.cells * csize, stream));
   for (const auto& kc : kclasses) TRY(run_points<Real>(kc, true, nullptr, nullptr, 0));
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_FFT, &ev));
@@ -1023,6 +1088,7 @@ int Engine::adjoint_table(bool in_graph) {
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_DECONV, &ev));
   CK(launch_deconv_crop<Real>(d_items, d_crop_blocks, d_crop_blocks + items.size() + 1, crop_blocks, nullptr, 0,
                               stream));
+  kernel_launches += crop_blocks > 0 ? 1 : 0;
   if (!in_graph) TRY(stage_end(&ev));
   return NFFT_OK;
 }
@@ -1033,6 +1099,7 @@ int Engine::forward_table(bool in_graph) {
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_PAD, &ev));
   CK(launch_pad_deconv<Real>(d_items, d_pad_blocks, d_pad_blocks + items.size() + 1, pad_blocks, nullptr, 0,
                              stream));
+  kernel_launches += pad_blocks > 0 ? 1 : 0;
   if (!in_graph) TRY(stage_end(&ev));
   if (!in_graph) TRY(stage_begin(NFFT_STAGE_IFFT, &ev));
   for (auto& fc : fclasses) TRY(run_fft(fc, fc.grids, 0, CUFFT_INVERSE));
@@ -1071,12 +1138,15 @@ int Engine::capture_graphs() {
       cudaError_t e = cudaMemcpyAsync(d_items, h_table[k], sizeof(ItemDev) * items.size(), cudaMemcpyHostToDevice,
                                       stream);
       if (e != cudaSuccess) s = NFFT_ERR_CUDA;
+      const int64_t before = kernel_launches;
       if (s == NFFT_OK) {
         if (dir == 0)
           s = precision == NFFT_FP64 ? adjoint_table<double>(true) : adjoint_table<float>(true);
         else
           s = precision == NFFT_FP64 ? forward_table<double>(true) : forward_table<float>(true);
       }
+      graph_launches[dir] = kernel_launches - before;   // kernels per replay
+      kernel_launches = before;
       const cudaError_t ee = cudaStreamEndCapture(stream, &g);
       if (s != NFFT_OK || ee != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -1108,6 +1178,7 @@ int Engine::adjoint_batch(const void* const* f, void* const* fhat) {
   EventPair ev{};
   TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));   // whole-graph time is booked as the spread stage
   CK(cudaGraphLaunch(graph_adj[k], stream));
+  kernel_launches += graph_launches[0];
   TRY(stage_end(&ev));
   CK(cudaEventRecord(slot_done[k], stream));
   return NFFT_OK;
@@ -1125,6 +1196,7 @@ int Engine::forward_batch(const void* const* fhat, void* const* f) {
   EventPair ev{};
   TRY(stage_begin(NFFT_STAGE_INTERP, &ev));
   CK(cudaGraphLaunch(graph_fwd[k], stream));
+  kernel_launches += graph_launches[1];
   TRY(stage_end(&ev));
   CK(cudaEventRecord(slot_done[k], stream));
   return NFFT_OK;
@@ -1140,7 +1212,7 @@ int Engine::ewald_impl(const void* q, double L, double alpha) {
   const ItemDev& it = items[0];
   EventPair ev{};
   TRY(stage_begin(NFFT_STAGE_SPREAD, &ev));
-  CK(cudaMemsetAsync(it.grid, 0, (size_t)fc.cells * csize, stream));
+  if (!kclasses[0].owner || it.M == 0) CK(cudaMemsetAsync(it.grid, 0, (size_t)fc.cells * csize, stream));
   if (it.M > 0) TRY(run_points<Real>(kclasses[0], true, q, nullptr, 1));
   TRY(stage_end(&ev));
   TRY(stage_begin(NFFT_STAGE_FFT, &ev));
@@ -1159,8 +1231,10 @@ int Engine::ewald_impl(const void* q, double L, double alpha) {
   g.coef = M_PI * M_PI / (al * al);
   CK(launch_ewald_sum<Real>(static_cast<const C*>(it.grid), true, g, ewald_partials, 1.0 / (2.0 * M_PI * L), 0.0,
                             ewald_out, stream));
+  kernel_launches += 2;
   CK(launch_sumsq<Real>(static_cast<const C*>(q), it.M, ewald_partials, -alpha / std::sqrt(M_PI), 0.0,
                         ewald_out + 1, stream));
+  kernel_launches += 2;
   TRY(stage_end(&ev));
   return NFFT_OK;
 }
@@ -1195,6 +1269,7 @@ int Engine::ewald_sum(const void* S, double L, double alpha, double* sum_dev) {
   else
     CK(launch_ewald_sum<float>(static_cast<const float2*>(S), false, g, ewald_partials, scale, 0.0, sum_dev,
                                stream));
+  kernel_launches += 2;
   return NFFT_OK;
 }
 
@@ -1224,6 +1299,10 @@ int Engine::set_option(int option, int64_t value) {
     case NFFT_OPT_METHOD:
       if (value < NFFT_METHOD_AUTO || value > NFFT_METHOD_GRID_WARP) return NFFT_ERR_INVALID_ARG;
       method_opt = (int)value;
+      break;
+    case NFFT_OPT_OWNER_SPREAD:
+      if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
+      owner_enabled = value != 0;
       break;
     case NFFT_OPT_SPARSE_POINTS:
     case NFFT_OPT_SPARSE_POINTS_INTERP:
@@ -1306,6 +1385,8 @@ int Engine::info(nfft_plan_info* out) const {
   out->spread_threads = spread_threads_opt;
   out->sparse_points = kclasses.empty() ? 0 : kclasses[0].sparse_points;
   out->sparse_points_interp = kclasses.empty() ? 0 : kclasses[0].sparse_points_interp;
+  out->owner_spread = kclasses.empty() ? 0 : (kclasses[0].owner ? 1 : 0);
+  out->kernel_launches = kernel_launches;
   out->interp_threads = interp_threads_opt;
   return NFFT_OK;
 }

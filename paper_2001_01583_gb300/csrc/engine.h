@@ -41,6 +41,7 @@ struct KClass {
   int64_t max_subs;           // bound on the class's subproblems
   int sparse_points;          // spreading subproblems below this many points: grid-warp kernel (0: none)
   int sparse_points_interp;   // the same for interpolation
+  bool owner;                 // spreading of sparse bins by the owner kernel (3-D)
 };
 
 struct FClass {
@@ -50,6 +51,7 @@ struct FClass {
   int grids;                  // grids in the buffer
   void* buf = nullptr;
   std::map<int, cufftHandle> plans;
+  bool owner_written = false;   // every grid of the class is written whole by the owner kernel
 };
 
 struct EventPair {
@@ -85,6 +87,7 @@ class Engine {
   int ewald(const void* q, double L, double alpha, double* out3);
   int ewald_sum(const void* S, double L, double alpha, double* sum_dev);
   int info(nfft_plan_info* out) const;
+  int64_t launched() const { return kernel_launches; }
   // Time candidate layouts on the points already set and keep the fastest
   // (see nfft_autotune).  best_ms: adjoint + forward time of the winner.
   int autotune(int reps, double* best_ms);
@@ -105,6 +108,7 @@ class Engine {
   template <typename Real> int run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
   template <typename Real> int run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int max_nrhs);
   template <typename Real> int run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
+  template <typename Real> int run_owner(const KClass& kc, PointKernelArgs<Real>& a);
   template <typename Real> int run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
   template <typename Real> int adjoint_table(bool in_graph);
   template <typename Real> int forward_table(bool in_graph);
@@ -130,6 +134,9 @@ class Engine {
   int bin_opt[3] = {0, 0, 0};
   int max_sub_opt = 0;
   int sparse_opt = 0;          // NFFT_OPT_SPARSE_POINTS
+  bool owner_enabled = false;  // NFFT_OPT_OWNER_SPREAD
+  int64_t kernel_launches = 0;   // this library's kernels launched so far (graph replays included)
+  int64_t graph_launches[2] = {0, 0};
   int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP
   int max_sub = 1024;
   int threads_opt = 0;

@@ -50,9 +50,17 @@ struct PointKernelArgs {
   const void* in;
   void* out;
   int nrhs;
-  // subproblems with sub_min_count <= count < sub_max_count are this launch's
+  // subproblems whose bin holds sub_min_count <= points < sub_max_count are this launch's
   int sub_min_count, sub_max_count;
+  int item_begin, item_end;   // the launch's items (internal order)
 };
+
+// Points of the subproblem's whole bin (the sparse / dense split is per bin).
+template <typename Real>
+__device__ __forceinline__ bool sub_selected(const PointKernelArgs<Real>& a, const SubProblem& s) {
+  const int total = a.pts.bin_count[a.items[s.item].bin_offset + s.bin];
+  return total >= a.sub_min_count && total < a.sub_max_count;
+}
 
 // The launch's subproblems: [lo, hi).
 template <typename Real>
@@ -91,6 +99,14 @@ constexpr int kGmWarpsHost = 8;
 constexpr int kGmSplitHost = 4;   // warps sharing one subproblem
 const void* gm_kernel_f32(int d, int taps, bool spread);
 const void* gm_kernel_f64(int d, int taps, bool spread);
+
+// 3-D owner spreading of sparse bins (points_owner.cuh): a warp per bin's
+// cells, plain stores, no atomics; blocks of kOwnerWarpsHost warps, dynamic
+// shared memory kOwnerWarpsHost * (bin cells * complex + 3 taps * real).
+constexpr int kOwnerWarpsHost = 4;
+constexpr int kOwnerReachHost = 16;   // bins per dimension within a window's reach of a bin, at most
+const void* owner_kernel_f32(int taps);
+const void* owner_kernel_f64(int taps);
 
 // Warp-per-point (d = 2) and shared-tile (d = 3) kernels, taps <= 16.
 struct WppLayout {

@@ -31,8 +31,6 @@ struct GmShape {
 constexpr int kGmWarps = kGmWarpsHost;   // warps per block
 constexpr int kGmSplit = kGmSplitHost;   // warps sharing one subproblem's points
 
-__device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
 // Per-lane footprint of one point: offsets inside a plane and the product of
 // the in-plane weights; the point's first plane index (3-D).
 template <int D, int W, typename Real>
@@ -77,7 +75,7 @@ __device__ __forceinline__ void gm_point(const SortedPoints<Real>& pts, const It
   }
 }
 
-// a.sub_min_count <= count < a.sub_max_count selects the subproblems of this launch.
+// sub_selected (points of the subproblem's bin) selects the subproblems of this launch.
 template <int D, int W, typename Real>
 __global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Real> a) {
   using C = typename Cplx<Real>::type;
@@ -92,7 +90,7 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Rea
   for (int64_t wi = (int64_t)blockIdx.x * kGmWarps + warp; wi < work; wi += stride) {
     const int sp = lo + (int)(wi / kGmSplit), part = (int)(wi % kGmSplit);
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count || part >= sub.count) continue;
+    if (part >= sub.count || !sub_selected(a, sub)) continue;
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -146,7 +144,7 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_interp_gm(PointKernelArgs<Rea
   for (int64_t wi = (int64_t)blockIdx.x * kGmWarps + warp; wi < work; wi += stride) {
     const int sp = lo + (int)(wi / kGmSplit), part = (int)(wi % kGmSplit);
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count || part >= sub.count) continue;
+    if (part >= sub.count || !sub_selected(a, sub)) continue;
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, sub)) continue;   // block-uniform
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem sub = a.pts.subs[sp];
-    if (sub.count < a.sub_min_count || sub.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, sub)) continue;   // block-uniform
     const ItemDev& it = a.items[sub.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);

@@ -30,6 +30,9 @@ __device__ __forceinline__ void grid_add(double2* p, double2 v) {
   atomicAdd(&p->y, v.y);
 }
 
+// v mod n for v in [-n, 2n).
+__device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 // Bin coordinates of a bin id (C order over the d used dimensions).
 __device__ __forceinline__ void bin_coords(int bin, const GridGeom& g, int* bc) {
   for (int t = g.d - 1; t >= 0; --t) {
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(256) k_spread_tiled(PointKernelArgs<Real> a) {
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
-    if (s.count < a.sub_min_count || s.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, s)) continue;   // block-uniform
     const ItemDev& it = a.items[s.item];
     const GridGeom& g = it.geom;
     const WindowDev& win = it.win;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(256) k_interp_tiled(PointKernelArgs<Real> a) {
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
-    if (s.count < a.sub_min_count || s.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, s)) continue;   // block-uniform
     const ItemDev& it = a.items[s.item];
     const GridGeom& g = it.geom;
     const WindowDev& win = it.win;

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_spread_wpp(PointKernelArgs<Real> a, Wpp
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
-    if (s.count < a.sub_min_count || s.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, s)) continue;   // block-uniform
     const ItemDev& it = a.items[s.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_interp_wpp(PointKernelArgs<Real> a, Wpp
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
     const SubProblem s = a.pts.subs[sp];
-    if (s.count < a.sub_min_count || s.count >= a.sub_max_count) continue;   // block-uniform
+    if (!sub_selected(a, s)) continue;   // block-uniform
     const ItemDev& it = a.items[s.item];
     const GridGeom& g = it.geom;
     const ItemCall call = item_call(a, it);

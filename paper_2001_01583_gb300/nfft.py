@@ -145,6 +145,7 @@ class Plan:
                     device_bytes=inf.device_bytes, sigma=tuple(inf.sigma[:inf.d]),
                     max_subproblem=inf.max_subproblem, spread_threads=inf.spread_threads,
                     sparse_points=inf.sparse_points, sparse_points_interp=inf.sparse_points_interp,
+                    owner_spread=inf.owner_spread, kernel_launches=inf.kernel_launches,
                     interp_threads=inf.interp_threads)
 
     def autotune(self, reps=3):
@@ -249,6 +250,12 @@ class Batch:
 
     def set_option(self, option, value):
         _lib.check(self._lib.nfft_batch_set_option(self._h, int(option), int(value)), "nfft_batch_set_option")
+
+    def kernel_launches(self):
+        """This library's kernels launched by the batch so far."""
+        c = ctypes.c_int64()
+        _lib.check(self._lib.nfft_batch_kernel_launches(self._h, ctypes.byref(c)), "nfft_batch_kernel_launches")
+        return c.value
 
     def stage_times(self, reset=False):
         ms = (ctypes.c_double * len(_lib.STAGES))()

@@ -237,6 +237,58 @@ def test_wide_windows_fp64_without_plane_kernels(N, M, window, m):
     _elementwise(b, S.forward(x, fh, N, 2.0, m, WIN[window]), 1e-12)
 
 
+# ---- 3-D owner spreading of sparse bins (no atomics) -------------------------
+@pytest.mark.parametrize("N,M,window,m,precision,R", [
+    ((40, 36, 32), 2000, "kaiser_bessel", 4, "fp64", 1),
+    ((40, 36, 32), 2000, "kaiser_bessel", 4, "fp32", 1),
+    ((30, 26, 22), 1500, "gaussian", 3, "fp64", 3),      # ragged last bins, 3 right-hand sides
+    ((36, 34, 40), 1200, "kaiser_bessel", 9, "fp32", 1),  # 18 taps
+    ((32, 30, 34), 800, "gaussian", 12, "fp32", 1),       # 26 taps, small bins
+])
+@pytest.mark.parametrize("owner", [1, 0])
+def test_owner_spread_of_sparse_bins(N, M, window, m, precision, R, owner):
+    x = inputs.clustered_points(M, 3, 5, 0.08, seed=101)
+    f = inputs.complex_normal((R, M), seed=102)
+    fh = inputs.complex_normal(N, seed=103)
+    from paper_2001_01583_gb300 import Plan, _lib
+    with Plan(N, M, 2.0, m, window, precision) as p:
+        p.set_option(_lib.OPT_SPARSE_POINTS, 1 << 20)   # every bin sparse
+        p.set_option(_lib.OPT_OWNER_SPREAD, owner)
+        p.set_points(torch.from_numpy(x).cuda())
+        a = p.adjoint(torch.from_numpy(f).to(_cdt(precision)).cuda()).cpu().numpy().astype(np.complex128)
+        info = p.info()
+    assert info["owner_spread"] == owner
+    for r in range(R):
+        sa = S.adjoint(x, f[r], N, 2.0, m, WIN[window])
+        if precision == "fp64":
+            _elementwise(a[r], sa, 1e-12)
+        else:
+            amp, _ = _amplification(N, info["n"], m, window)
+            assert np.max(np.abs(a[r] - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2)) <= FP32_ELEM
+
+
+def test_owner_spread_in_a_batch_with_ineligible_items():
+    """Items whose grid is too small for the owner kernel (n_t < bin_t + W - 1)
+    keep the grid-warp path; both kinds share FFT classes and one graph."""
+    from paper_2001_01583_gb300 import Batch
+    items = [dict(N=(40, 36, 32), M=900, m=4), dict(N=(8, 8, 8), M=300, m=4), dict(N=(40, 36, 32), M=0, m=4),
+             dict(N=(24, 20, 28), M=2500, m=3, nrhs=2)]
+    xs = [inputs.uniform_points(it["M"], 3, seed=110 + i) for i, it in enumerate(items)]
+    fs = [inputs.complex_normal((it.get("nrhs", 1), it["M"]), seed=120 + i) for i, it in enumerate(items)]
+    with Batch(items, "fp64") as bt:
+        bt.set_points([torch.from_numpy(v).cuda() for v in xs])
+        for _ in range(2):   # replay the graph: no stale grid contents
+            A = bt.adjoint([torch.from_numpy(v).cuda() for v in fs])
+        bt.sync()
+    for i, it in enumerate(items):
+        for r in range(it.get("nrhs", 1)):
+            got = A[i][r].cpu().numpy()
+            if it["M"] == 0:
+                assert np.count_nonzero(got) == 0
+                continue
+            _elementwise(got, S.adjoint(xs[i], fs[i][r], it["N"], 2.0, it["m"], S.KAISER_BESSEL), 1e-12)
+
+
 # ---- rows longer than one scaling segment (4096 elements) --------------------
 @pytest.mark.parametrize("N,M", [((20000,), 3000), ((8, 5000), 2000)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
