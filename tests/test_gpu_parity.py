@@ -275,7 +275,9 @@ def test_owner_spread_in_a_batch_with_ineligible_items():
              dict(N=(24, 20, 28), M=2500, m=3, nrhs=2)]
     xs = [inputs.uniform_points(it["M"], 3, seed=110 + i) for i, it in enumerate(items)]
     fs = [inputs.complex_normal((it.get("nrhs", 1), it["M"]), seed=120 + i) for i, it in enumerate(items)]
+    from paper_2001_01583_gb300 import _lib
     with Batch(items, "fp64") as bt:
+        bt.set_option(_lib.OPT_OWNER_SPREAD, 1)
         bt.set_points([torch.from_numpy(v).cuda() for v in xs])
         for _ in range(2):   # replay the graph: no stale grid contents
             A = bt.adjoint([torch.from_numpy(v).cuda() for v in fs])
