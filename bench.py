@@ -106,6 +106,34 @@ def _step_hbm_bytes(wl):
     return per_set * len(wl["sets"])
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# a stage's kernel, from an ncu capture of this workload, valid while the
+# kernel's sources hash to `sources`; otherwise the traffic is reported null.
+TRAFFIC = {
+    # uniform set's spread launch, N = 64^3, M = 1e6 (profiles/spread_interp_planes_config_3d_n64_m1e6.md)
+    "spread": {"bytes": 44892928 + 29184, "sources": "c964ced460a917fd876757e6ad65858d9b4613259226ec35939a6704759bbfba"},
+    "interp": {"bytes": 36901376 + 5632, "sources": "c964ced460a917fd876757e6ad65858d9b4613259226ec35939a6704759bbfba"},
+}
+TRAFFIC_SOURCES = {"spread": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu"),
+                   "interp": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu")}
+
+
+def _sources_hash(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES.get(stage, ()):
+        with open(os.path.join(ROOT, "paper_2001_01583_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic(stage):
+    rec = TRAFFIC.get(stage)
+    if not rec or rec["sources"] != _sources_hash(stage):
+        return None
+    return rec["bytes"]
+
+
 def _roofline(stages, wl, peaks, kind, sms):
     total = {k: v[0] for k, v in stages.items() if v[1] > 0}
     per_launch = {k: v[0] / v[1] for k, v in stages.items() if v[1] > 0}
@@ -124,7 +152,8 @@ def _roofline(stages, wl, peaks, kind, sms):
         achieved = _stage_hbm_bytes(dom, wl) / t / 1e9
         r = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
              "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind}
-    r.update({"kernel": dom, "traffic": None, "launch_ms": per_launch[dom],
+    r.update({"kernel": dom, "traffic": _traffic(dom) if wl is WORKLOADS["config"] else None,
+              "launch_ms": per_launch[dom],
               "stage_share": {k: round(v / sum(total.values()), 4) for k, v in total.items()}})
     return r
 
