@@ -9,7 +9,7 @@ interpolate).  Units: a transform of M points counts M nonuniform points, so a
 step processes 2 sets x 2 transforms x M points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config|small|batch|1d|fluorite|picker]
+                  [--workload config|small|sparse|batch|1d|fluorite|picker]
                   [--precision fp32|fp64] [--autotune] [--no-cpu-baseline]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
@@ -52,6 +52,9 @@ WORKLOADS = {
     "picker": dict(N=(256, 256, 256), M=30_000_000, sets=("clustered64",), extra=True,
                    name="3-D adjoint+forward NFFT, N=256^3, M=3e7 points in 64 Gaussian clusters (std 0.01), eps=1e-5, "
                         "window parameters from the learned picker, mixed FP32"),
+    "sparse": dict(N=(64, 64, 64), M=20000, sets=("uniform",),
+                   name="3-D adjoint+forward NFFT, N=64^3, M=2e4 uniform (about 10 points per bin: the sparse "
+                        "grid-warp kernels), Kaiser-Bessel m=4, sigma=2, mixed FP32"),
     "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",),
                   name="3-D adjoint+forward NFFT, N=64^3, M=5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
                        "(profiling case: the same grid and bins, half the points, one set)"),
@@ -386,6 +389,9 @@ def run_ours(args, wl, rank, world):
     hbm_step = _step_hbm_bytes(wl)
     roofline["step_hbm_bytes"] = hbm_step
     roofline["step_hbm_frac"] = hbm_step / (ms_max * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    # every stage's algorithmic HBM bytes per launch over its mean launch time
+    roofline["stage_hbm_frac"] = {k: round(_stage_hbm_bytes(k, wl) / (v[0] / v[1] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
+                                  for k, v in stages.items() if v[1] > 0 and v[0] > 0}
     roofline["stage_ms_per_set"] = per_set
 
     cpu = None
