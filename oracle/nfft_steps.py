@@ -20,6 +20,11 @@ windows, written per dimension in the cell variable u = n x:
                  phihat(k) = (1/n) exp(-b (pi k / n)^2)
   Kaiser-Bessel  phi(x) = (1/pi) sinh(b sqrt(m^2 - u^2)) / sqrt(m^2 - u^2)  for |u| < m, else 0,
                  b = pi (2 - 1/sigma);   phihat(k) = (1/n) I0(m sqrt(b^2 - (2 pi k / n)^2))
+  B-spline       phi(x) = M_2m(u), the centred cardinal B-spline of order 2m
+                 (the 2m-fold convolution of the indicator of [-1/2, 1/2));
+                 phihat(k) = (1/n) sinc(pi k / n)^(2m),  sinc(t) = sin(t) / t
+  sinc-power     phi(x) = a sinc(pi a x)^(2m),  a = N (2 sigma - 1) / (2m),
+                 truncated to |u| < m;  phihat(k) = M_2m(k / a)
 
 with sigma = n_t / N_t of that dimension.  The scaling weight of a
 d-dimensional product window is c_k = prod_t n_t phihat_t(k_t): the Poisson
@@ -40,7 +45,31 @@ import scipy.special
 
 GAUSSIAN = 0
 KAISER_BESSEL = 1
-WINDOWS = {"gaussian": GAUSSIAN, "kaiser_bessel": KAISER_BESSEL}
+B_SPLINE = 2
+SINC_POWER = 3
+WINDOWS = {"gaussian": GAUSSIAN, "kaiser_bessel": KAISER_BESSEL, "b_spline": B_SPLINE, "sinc_power": SINC_POWER}
+
+
+def cardinal_bspline(order: int, u):
+    """Centred cardinal B-spline M_order(u) (support [-order/2, order/2],
+    integral 1) through the uniform B-spline N_k(s) = M_k(s - k/2), s in
+    [0, k], and its recurrence N_k(s) = (s N_(k-1)(s) + (k - s) N_(k-1)(s - 1))
+    / (k - 1) from N_1 = indicator of [0, 1): every step adds nonnegative
+    terms, so it loses no digits."""
+    s = np.asarray(u, dtype=np.float64) + order / 2.0
+    # vals[i] = N_j(s - i), i = 0 .. order - j
+    vals = [((s - i >= 0.0) & (s - i < 1.0)).astype(np.float64) for i in range(order)]
+    for j in range(2, order + 1):
+        vals = [((s - i) * vals[i] + (j - (s - i)) * vals[i + 1]) / (j - 1) for i in range(order - j + 1)]
+    return vals[0]
+
+
+def _sinc(t):
+    t = np.asarray(t, dtype=np.float64)
+    out = np.ones_like(t)
+    nz = t != 0
+    out[nz] = np.sin(t[nz]) / t[nz]
+    return out
 
 
 def oversampled_size(N: int, sigma: float, m: int) -> int:
@@ -69,16 +98,26 @@ def shape_param(window: int, m: int, n: int, N: int) -> float:
         return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * math.pi)
     if window == KAISER_BESSEL:
         return math.pi * (2.0 - 1.0 / sigma)
+    if window == B_SPLINE:
+        return 0.0
+    if window == SINC_POWER:
+        return N * (2.0 * sigma - 1.0) / (2.0 * m)   # a
     raise ValueError("unknown window %r" % window)
 
 
 def phi(window: int, u, m: int, n: int, N: int):
     """Window phi at x = u / n (u in cells), untruncated except for the
-    Kaiser-Bessel support |u| < m."""
+    Kaiser-Bessel and sinc-power support |u| < m (the B-spline's own support
+    is |u| < m)."""
     u = np.asarray(u, dtype=np.float64)
     b = shape_param(window, m, n, N)
     if window == GAUSSIAN:
         return np.exp(-(u * u) / b) / math.sqrt(math.pi * b)
+    if window == B_SPLINE:
+        return cardinal_bspline(2 * m, u)
+    if window == SINC_POWER:
+        # a sinc(pi a x)^(2m) at x = u / n, truncated to |u| < m
+        return np.where(np.abs(u) < m, b * _sinc(math.pi * b * u / n) ** (2 * m), 0.0)
     out = np.zeros_like(u)
     inside = np.abs(u) < m
     r = np.sqrt(m * m - u[inside] ** 2)
@@ -95,6 +134,10 @@ def phi_hat(window: int, k, m: int, n: int, N: int):
     b = shape_param(window, m, n, N)
     if window == GAUSSIAN:
         return np.exp(-b * (math.pi * k / n) ** 2) / n
+    if window == B_SPLINE:
+        return _sinc(math.pi * k / n) ** (2 * m) / n
+    if window == SINC_POWER:
+        return cardinal_bspline(2 * m, k / b)
     arg = b * b - (2.0 * math.pi * k / n) ** 2
     if np.any(arg < 0):
         raise ValueError("Kaiser-Bessel phihat needs |k| <= n b / (2 pi)")

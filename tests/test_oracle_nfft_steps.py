@@ -8,7 +8,11 @@
   windows and shrinks with m;
 - the NFFT and its inverse procedure are exact transposes (adjoint identity
   to rounding, independent of the window error);
-- the oversampled size rule.
+- the oversampled size rule;
+- the B-spline and sinc-power windows (Section 4, Fig. 12): textbook values,
+  integral and partition of unity of the cardinal B-spline, both transforms
+  against quadrature (the sinc-power one within its truncation tail), the
+  error decay against the direct NDFT, exact transposition.
 """
 import math
 
@@ -108,3 +112,68 @@ def test_points_on_cell_boundaries_and_wrap():
     assert np.max(np.abs(a - b)) < 1e-14
     exact = ndft.adjoint(np.array([[-0.5]]), f, N)
     assert ndft.rel_l2(a, exact) < 1e-6
+
+
+# ---- B-spline and sinc-power windows (Section 4, Fig. 12) ----------------------
+def test_cardinal_bspline_textbook_values():
+    # the hat function and the cubic B-spline, and the general properties
+    assert np.allclose(S.cardinal_bspline(2, np.array([0.0, 0.5, -0.5, 1.0])), [1.0, 0.5, 0.5, 0.0])
+    assert np.allclose(S.cardinal_bspline(4, np.array([0.0, 1.0, -1.0, 0.5, 2.0])), [2 / 3, 1 / 6, 1 / 6, 23 / 48, 0.0])
+    for order in (2, 5, 8, 13, 24):
+        u = np.linspace(-order / 2 - 1, order / 2 + 1, 20001)
+        assert abs(np.trapezoid(S.cardinal_bspline(order, u), u) - 1.0) < 1e-6
+        shift = 0.3137
+        assert abs(S.cardinal_bspline(order, shift + np.arange(-order, order + 1)).sum() - 1.0) < 1e-12
+        assert np.allclose(S.cardinal_bspline(order, u), S.cardinal_bspline(order, -u), atol=1e-14)
+
+
+@pytest.mark.parametrize("m,N,n", [(2, 16, 32), (4, 32, 64), (6, 20, 40), (3, 16, 24)])
+def test_bspline_phi_hat_matches_quadrature(m, N, n):
+    # compact support |u| < m: the transform is exact, no truncation term
+    knots = [(j - m) / n for j in range(2 * m + 1)]
+    for k in (0, 1, N // 4, N // 2 - 1, -N // 2):
+        val, _ = scipy.integrate.quad(lambda x: float(S.phi(S.B_SPLINE, np.array([n * x]), m, n, N)[0])
+                                      * math.cos(2 * math.pi * k * x), -m / n, m / n, points=knots, limit=400,
+                                      epsabs=1e-15, epsrel=1e-12)
+        assert abs(val - float(S.phi_hat(S.B_SPLINE, k, m, n, N))) <= 1e-10 * float(S.phi_hat(S.B_SPLINE, 0, m, n, N))
+
+
+@pytest.mark.parametrize("m,N,n", [(3, 16, 32), (5, 32, 64), (4, 20, 40)])
+def test_sinc_power_phi_hat_matches_quadrature(m, N, n):
+    # phi_hat = M_2m(k / a) is the transform of the untruncated a sinc(pi a x)^(2m);
+    # cutting at |u| = m changes it by at most the tail mass
+    # 2 a int_{m/n}^inf (pi a x)^(-2m) dx = 2 a (pi a)^(-2m) (m/n)^(1-2m) / (2m - 1)
+    a = S.shape_param(S.SINC_POWER, m, n, N)
+    tail = 2 * a * (math.pi * a) ** (-2 * m) * (m / n) ** (1 - 2 * m) / (2 * m - 1)
+    for k in (0, 1, N // 4, N // 2 - 1, -N // 2):
+        val, _ = scipy.integrate.quad(lambda x: float(S.phi(S.SINC_POWER, np.array([n * x]), m, n, N)[0])
+                                      * math.cos(2 * math.pi * k * x), -m / n, m / n, limit=400,
+                                      epsabs=1e-15, epsrel=1e-12)
+        assert abs(val - float(S.phi_hat(S.SINC_POWER, k, m, n, N))) <= tail + 1e-12
+
+
+@pytest.mark.parametrize("window", [S.B_SPLINE, S.SINC_POWER])
+def test_bspline_sinc_power_error_decay(window):
+    # the B-spline bound of Steidl: E <= 4 (2 sigma - 1)^(-2m); both windows'
+    # errors fall by at least a factor 5 per unit of m at sigma = 2
+    N = (64,)
+    M = 400
+    x = inputs.uniform_points(M, 1, seed=21)
+    f = inputs.complex_normal(M, seed=22)
+    exact = ndft.adjoint(x, f, N)
+    errs = [ndft.rel_l2(S.adjoint(x, f, N, 2.0, m, window), exact) for m in (2, 3, 4, 5, 6)]
+    for m, e in zip((2, 3, 4, 5, 6), errs):
+        assert e < 4.0 * 3.0 ** (-2 * m), (m, e)
+    assert all(b < a / 5 for a, b in zip(errs, errs[1:])), errs
+
+
+@pytest.mark.parametrize("window", [S.B_SPLINE, S.SINC_POWER])
+def test_bspline_sinc_power_pair_is_exact_transpose(window):
+    N = (12, 16)
+    M = 120
+    x = inputs.uniform_points(M, 2, seed=31)
+    f = inputs.complex_normal(M, seed=32)
+    g = inputs.complex_normal(N, seed=33)
+    lhs = np.vdot(S.forward(x, g, N, 2.0, 3, window), f)
+    rhs = np.vdot(g, S.adjoint(x, f, N, 2.0, 3, window))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
