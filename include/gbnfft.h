@@ -43,10 +43,16 @@ extern "C" {
 
 typedef struct nfft_plan nfft_plan;
 
-/* Window functions named in Section 4 (formulas: the standard NFFT windows). */
+/* Window functions named in Section 4 (Fig. 12), in the cell variable
+ * u = n x of each dimension (formulas: the standard NFFT windows).
+ * Gaussian: 2m + 2 taps; the others 2m taps (their weight vanishes at the
+ * two outer cells).  B-spline and sinc-power evaluate slower and serve
+ * precision studies; the picker chooses between Gaussian and Kaiser-Bessel. */
 typedef enum {
-  NFFT_GAUSSIAN = 0,
-  NFFT_KAISER_BESSEL = 1
+  NFFT_GAUSSIAN = 0,      /* exp(-u^2 / b), b = 2 sigma m / ((2 sigma - 1) pi) */
+  NFFT_KAISER_BESSEL = 1, /* sinh(b sqrt(m^2 - u^2)) / sqrt(m^2 - u^2), |u| < m, b = pi (2 - 1/sigma) */
+  NFFT_B_SPLINE = 2,      /* M_2m(u), the centred cardinal B-spline of order 2m */
+  NFFT_SINC_POWER = 3     /* sinc(pi u (2 sigma - 1) / (2 m sigma))^(2m), |u| < m (sinc t = sin t / t) */
 } nfft_window;
 
 /* NFFT_FP64: FP64 points, weights, grid and FFT (the plain form).

@@ -24,7 +24,10 @@ ERR_UNSUPPORTED = -8
 
 GAUSSIAN = 0
 KAISER_BESSEL = 1
-WINDOWS = {"gaussian": GAUSSIAN, "kaiser_bessel": KAISER_BESSEL, "kb": KAISER_BESSEL}
+B_SPLINE = 2
+SINC_POWER = 3
+WINDOWS = {"gaussian": GAUSSIAN, "kaiser_bessel": KAISER_BESSEL, "kb": KAISER_BESSEL, "b_spline": B_SPLINE,
+           "bspline": B_SPLINE, "sinc_power": SINC_POWER}
 
 FP64 = 0
 FP32_MIXED = 1

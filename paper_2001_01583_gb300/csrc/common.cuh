@@ -35,12 +35,12 @@ template <> __device__ __forceinline__ double2 cmake<double2>(double re, double 
 // moved into the FP64 scaling factors on the host).  The shape parameter
 // depends on sigma_t = n_t / N_t, so it is kept per dimension.
 struct WindowDev {
-  int kind;                 // 0 Gaussian, 1 Kaiser-Bessel
+  int kind;                 // 0 Gaussian, 1 Kaiser-Bessel, 2 B-spline, 3 sinc-power
   int m;                    // cut-off
   int shift;                // s: first tap is c - m + s
   int taps;                 // W
   double b[kMaxDim];        // shape parameter per dimension
-  double kb_norm[kMaxDim];  // 1 / (1 - exp(-2 b m)) per dimension
+  double kb_norm[kMaxDim];  // Kaiser-Bessel: 1 / (1 - exp(-2 b m)); B-spline: 1 / M_2m(0)
   float bf[kMaxDim];        // the same two, rounded to float once (FP32 kernels)
   float kb_normf[kMaxDim];
 };
@@ -48,11 +48,36 @@ struct WindowDev {
 // psi(u) = phi(u / n) / phi(0) for the distance u (in cells).
 //   Gaussian:       exp(-u^2 / b)
 //   Kaiser-Bessel:  sinh(b z) / z * m / sinh(b m),  z = sqrt(m^2 - u^2), |u| < m
+//   B-spline:       M_2m(u) / M_2m(0)           (window_psi_any only)
+//   sinc-power:     sinc(pi b u)^(2m),  |u| < m
 // The Kaiser-Bessel form is evaluated as
 //   exp(-b u^2 / (z + m)) * m * (-expm1(-2 b z) / z) * kb_norm
 // so the large exponent b m cancels exactly instead of in floating point.
 template <typename Real>
 __device__ __forceinline__ Real window_psi(const WindowDev& w, int t, Real u);
+
+// Centred cardinal B-spline M_order(u), |u| < order / 2, raised from the
+// indicator of [0, 1) by the two-term recurrence of uniform B-splines
+// (nonnegative terms only).  Only window_psi_any (the global kernels, which
+// run every B-spline plan) calls it: the other kernels keep their registers.
+template <typename Real>
+__device__ __noinline__ Real cardinal_bspline_dev(int order, Real u) {
+  const Real s = u + (Real)(order / 2);
+  if (!(s > (Real)0 && s < (Real)order)) return (Real)0;
+  Real v[kMaxTaps + 1];
+  const int f = (int)floor(s);
+  for (int i = 0; i <= order; ++i) v[i] = (Real)0;
+  v[f] = (Real)1;
+  for (int j = 2; j <= order; ++j) {
+    const Real inv = (Real)1 / (Real)(j - 1);
+    const int i0 = f - j + 1 > 0 ? f - j + 1 : 0, i1 = f < order - j ? f : order - j;
+    for (int i = i0; i <= i1; ++i) {
+      const Real si = s - (Real)i;
+      v[i] = (si * v[i] + ((Real)j - si) * v[i + 1]) * inv;
+    }
+  }
+  return v[0];
+}
 
 template <>
 __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, float u) {
@@ -62,6 +87,15 @@ __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, fl
   const float u2 = u * u;
   const float m2 = m * m;
   if (!(u2 < m2)) return 0.0f;
+  if (w.kind == 3) {
+    // sinc(pi c u) with c = b: sinpi needs no large-argument reduction
+    const float zz = b * u;
+    const float sc = zz != 0.0f ? sinpif(zz) / (3.14159265358979f * zz) : 1.0f;
+    const float r = sc * sc;
+    float p = 1.0f;
+    for (int i = 0; i < w.m; ++i) p *= r;
+    return p;
+  }
   const float z = sqrtf(m2 - u2);
   const float e = expf(-b * u2 / (z + m));
   const float s = -expm1f(-2.0f * b * z) / z;
@@ -76,10 +110,25 @@ __device__ __forceinline__ double window_psi<double>(const WindowDev& w, int t, 
   const double u2 = u * u;
   const double m2 = m * m;
   if (!(u2 < m2)) return 0.0;
+  if (w.kind == 3) {
+    const double zz = b * u;
+    const double sc = zz != 0.0 ? sinpi(zz) / (3.141592653589793 * zz) : 1.0;
+    const double r = sc * sc;
+    double p = 1.0;
+    for (int i = 0; i < w.m; ++i) p *= r;
+    return p;
+  }
   const double z = sqrt(m2 - u2);
   const double e = exp(-b * u2 / (z + m));
   const double s = -expm1(-2.0 * b * z) / z;
   return e * m * s * w.kb_norm[t];
+}
+
+// Every window, the B-spline included (global kernels only).
+template <typename Real>
+__device__ __forceinline__ Real window_psi_any(const WindowDev& w, int t, Real u) {
+  if (w.kind == 2) return cardinal_bspline_dev<Real>(2 * w.m, u) * (Real)w.kb_norm[t];
+  return window_psi<Real>(w, t, u);
 }
 
 // One subproblem: a run of sorted points inside one bin of one item.

@@ -34,7 +34,7 @@ bool is_fft_friendly(int64_t n) {
   return n == 1;
 }
 
-int taps_for(int window, int m) { return window == NFFT_KAISER_BESSEL ? 2 * m : 2 * m + 2; }
+int taps_for(int window, int m) { return window == NFFT_GAUSSIAN ? 2 * m + 2 : 2 * m; }
 
 // Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2
 // (all terms positive, so it is accurate to rounding for the x used here).
@@ -146,6 +146,9 @@ size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* t
 
 double shape_param(int window, int m, double sigma) {
   if (window == NFFT_GAUSSIAN) return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * M_PI);
+  if (window == NFFT_B_SPLINE) return 0.0;
+  // sinc-power: sinc(pi b u) in the cell variable u
+  if (window == NFFT_SINC_POWER) return (2.0 * sigma - 1.0) / (2.0 * m * sigma);
   return M_PI * (2.0 - 1.0 / sigma);
 }
 
@@ -153,10 +156,39 @@ double shape_param(int window, int m, double sigma) {
 // normalisation psi = phi / phi(0):  inv_c(k) = phi(0) / (n phihat(k)).
 //   Gaussian:       phi(0) = (pi b)^(-1/2),        n phihat(k) = exp(-b (pi k / n)^2)
 //   Kaiser-Bessel:  phi(0) = sinh(b m) / (pi m),   n phihat(k) = I0(m sqrt(b^2 - (2 pi k / n)^2))
+double cardinal_bspline(int order, double u) {
+  const double s = u + 0.5 * order;
+  if (!(s > 0.0 && s < (double)order)) return 0.0;
+  // v[i] = N_j(s - i) of the uniform B-spline N_j (support [0, j]), raised
+  // from N_1 (the indicator of [0, 1)) by N_j(s) = (s N_(j-1)(s) +
+  // (j - s) N_(j-1)(s - 1)) / (j - 1): nonnegative terms only
+  double v[2 * kMaxTaps + 2] = {0.0};
+  const int f = (int)std::floor(s);
+  v[f] = 1.0;
+  for (int j = 2; j <= order; ++j)
+    for (int i = 0; i <= order - j; ++i) {
+      const double si = s - i;
+      v[i] = (si * v[i] + (j - si) * v[i + 1]) / (j - 1);
+    }
+  return v[0];
+}
+
 double inv_c_at(int window, int m, int64_t n, double b, double k) {
   if (window == NFFT_GAUSSIAN) {
     const double t = M_PI * k / (double)n;
     return std::exp(b * t * t) / std::sqrt(M_PI * b);
+  }
+  if (window == NFFT_B_SPLINE) {
+    // phi(0) = M_2m(0), n phihat(k) = sinc(pi k / n)^(2m)
+    const double t = M_PI * k / (double)n;
+    const double sc = t == 0.0 ? 1.0 : std::sin(t) / t;
+    return cardinal_bspline(2 * m, 0.0) / std::pow(sc, 2 * m);
+  }
+  if (window == NFFT_SINC_POWER) {
+    // phi(x) = a sinc(pi a x)^(2m) with a = n b: phi(0) = a,
+    // n phihat(k) = n M_2m(k / a)
+    const double a = (double)n * b;
+    return a / ((double)n * cardinal_bspline(2 * m, k / a));
   }
   const double w = 2.0 * M_PI * k / (double)n;
   const double arg = m * std::sqrt(b * b - w * w);
@@ -181,7 +213,7 @@ int validate_spec(const ItemSpec& s, int precision) {
   if (s.M < 0 || s.M > (int64_t)INT32_MAX) return NFFT_ERR_INVALID_ARG;
   if (!(s.sigma >= 1.0) || !std::isfinite(s.sigma) || s.sigma > 16.0) return NFFT_ERR_INVALID_ARG;
   if (s.m < 1) return NFFT_ERR_INVALID_ARG;
-  if (s.window != NFFT_GAUSSIAN && s.window != NFFT_KAISER_BESSEL) return NFFT_ERR_INVALID_ARG;
+  if (s.window < NFFT_GAUSSIAN || s.window > NFFT_SINC_POWER) return NFFT_ERR_INVALID_ARG;
   if (precision != NFFT_FP64 && precision != NFFT_FP32_MIXED) return NFFT_ERR_INVALID_ARG;
   if (s.nrhs < 1 || s.nrhs > 4096) return NFFT_ERR_INVALID_ARG;
   if (taps_for(s.window, s.m) > kMaxTaps) return NFFT_ERR_UNSUPPORTED;
@@ -402,6 +434,12 @@ int Engine::build_layout() {
     const bool warp_ok = s.d == 3 ? planes : (s.d == 2 && c.taps <= 16 && 2 * wtile + 4096 <= budget);
     int method = method_opt;
     if (method == NFFT_METHOD_AUTO) method = warp_ok ? NFFT_METHOD_WARP : (tiled_ok ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
+    // B-spline windows run on the global kernels only (the others keep their
+    // registers free of its evaluation)
+    if (s.window == NFFT_B_SPLINE) {
+      if (method_opt != NFFT_METHOD_AUTO && method_opt != NFFT_METHOD_GLOBAL) return NFFT_ERR_UNSUPPORTED;
+      method = NFFT_METHOD_GLOBAL;
+    }
     if (method == NFFT_METHOD_TILED && !tiled_ok) return NFFT_ERR_UNSUPPORTED;
     if (method == NFFT_METHOD_WARP && !warp_ok) return NFFT_ERR_UNSUPPORTED;
     const bool gm_ok = (precision == NFFT_FP64 ? gm_kernel_f64(s.d, c.taps, true) : gm_kernel_f32(s.d, c.taps, true)) !=
@@ -507,13 +545,14 @@ int Engine::build_layout() {
     WindowDev& w = it.win;
     w.kind = s.window;
     w.m = s.m;
-    w.shift = s.window == NFFT_KAISER_BESSEL ? 1 : 0;
+    w.shift = s.window == NFFT_GAUSSIAN ? 0 : 1;
     w.taps = c.taps;
     for (int t = 0; t < 3; ++t) {
       const double sig = t < s.d ? (double)g.n[t] / (double)s.N[t] : 2.0;
       const double b = shape_param(s.window, s.m, sig);
       w.b[t] = b;
-      w.kb_norm[t] = 1.0 / (1.0 - std::exp(-2.0 * b * s.m));
+      w.kb_norm[t] = s.window == NFFT_KAISER_BESSEL ? 1.0 / (1.0 - std::exp(-2.0 * b * s.m))
+                     : (s.window == NFFT_B_SPLINE ? 1.0 / cardinal_bspline(2 * s.m, 0.0) : 1.0);
       w.bf[t] = (float)w.b[t];
       w.kb_normf[t] = (float)w.kb_norm[t];
       if (t < s.d) {

@@ -64,6 +64,8 @@ int64_t oversampled_size(int64_t N, double sigma);
 int window_taps(int window, int m);
 int validate_spec(const ItemSpec& s, int precision);
 double shape_param(int window, int m, double sigma);
+// centred cardinal B-spline M_order(u) (support |u| < order / 2), host FP64
+double cardinal_bspline(int order, double u);
 // 1 / c_k of one dimension at frequency k (kernels' normalisation psi = phi / phi(0)).
 double inv_c_at(int window, int m, int64_t n, double b, double k);
 

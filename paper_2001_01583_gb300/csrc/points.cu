@@ -19,7 +19,7 @@ __device__ __forceinline__ void global_taps(const SortedPoints<Real>& pts, const
     const Real base = pts.delta[t][idx] + (Real)(it.win.m - it.win.shift);
     const int c0 = origin[t] + unpack_local(loc, g.d, t);
     for (int i = 0; i < W; ++i) {
-      w[t][i] = window_psi<Real>(it.win, t, base - (Real)i);
+      w[t][i] = window_psi_any<Real>(it.win, t, base - (Real)i);
       gi[t][i] = wrap_mod(c0 + i, g.n[t]);
     }
   }

@@ -30,6 +30,10 @@ struct GmShape {
 
 constexpr int kGmWarps = kGmWarpsHost;   // warps per block
 constexpr int kGmSplit = kGmSplitHost;   // warps sharing one subproblem's points
+// resident blocks asked of the compiler: the kernels wait on global loads,
+// so narrow windows trade registers (at most 64) for more warps
+template <int W>
+constexpr int gm_min_blocks() { return W <= 6 ? 4 : (W <= 8 ? 3 : 1); }
 
 // Per-lane footprint of one point: offsets inside a plane and the product of
 // the in-plane weights; the point's first plane index (3-D).
@@ -77,7 +81,7 @@ __device__ __forceinline__ void gm_point(const SortedPoints<Real>& pts, const It
 
 // sub_selected (points of the subproblem's bin) selects the subproblems of this launch.
 template <int D, int W, typename Real>
-__global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Real> a) {
+__global__ void __launch_bounds__(32 * kGmWarps, gm_min_blocks<W>()) k_spread_gm(PointKernelArgs<Real> a) {
   using C = typename Cplx<Real>::type;
   using S = GmShape<D, W>;
   __shared__ Real wt_all[kGmWarps][D * W];
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(32 * kGmWarps) k_spread_gm(PointKernelArgs<Rea
 }
 
 template <int D, int W, typename Real>
-__global__ void __launch_bounds__(32 * kGmWarps) k_interp_gm(PointKernelArgs<Real> a) {
+__global__ void __launch_bounds__(32 * kGmWarps, gm_min_blocks<W>()) k_interp_gm(PointKernelArgs<Real> a) {
   using C = typename Cplx<Real>::type;
   using S = GmShape<D, W>;
   __shared__ Real wt_all[kGmWarps][D * W];

@@ -25,7 +25,7 @@ from paper_2001_01583_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-WIN = {"gaussian": S.GAUSSIAN, "kaiser_bessel": S.KAISER_BESSEL}
+WIN = {"gaussian": S.GAUSSIAN, "kaiser_bessel": S.KAISER_BESSEL, "b_spline": S.B_SPLINE, "sinc_power": S.SINC_POWER}
 FP32_ELEM = 1e-5
 FP32_L2 = 1e-6
 
@@ -94,6 +94,10 @@ CASES = [
     (2, (40, 30), 2500, "kaiser_bessel", 4),
     (3, (22, 18, 16), 5000, "kaiser_bessel", 4),
     (3, (20, 14, 12), 3000, "gaussian", 2),
+    (1, (160,), 2000, "b_spline", 5),
+    (2, (36, 28), 2500, "sinc_power", 4),
+    (3, (18, 16, 14), 3000, "b_spline", 3),
+    (3, (16, 20, 12), 2500, "sinc_power", 4),
 ]
 
 
@@ -103,6 +107,8 @@ CASES = [
 def test_against_oracles(d, N, M, window, m, precision, method):
     if method == "warp" and d == 1:
         pytest.skip("the warp-per-point kernels cover d = 2, 3")
+    if window == "b_spline" and method != "global":
+        pytest.skip("B-spline windows run on the global kernels")
     x = inputs.uniform_points(M, d, seed=5 + d)
     f = inputs.complex_normal(M, seed=6)
     fh = inputs.complex_normal(N, seed=7)
@@ -122,6 +128,45 @@ def test_against_oracles(d, N, M, window, m, precision, method):
     slack = 1e-13 if precision == "fp64" else 1e-6
     assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= ea * 1.01 + slack
     assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= eb * 1.01 + slack
+
+
+# ---- the precision study of Section 4 (Fig. 12) -----------------------------
+def test_precision_against_cut_off_fig12():
+    """3-D, N = 16^3, M = 4096, sigma = 2, the four windows, m = 1 .. 12,
+    FP64: the relative l2 error (Eq. 9) of the adjoint and the forward
+    transform against the direct NDFT, for every window and m; each equals
+    the FP64 oracle NFFT's error (checked up to m = 3, where the oracle is
+    quick), and every window's error falls with m to the FP64 floor."""
+    from paper_2001_01583_gb300 import Plan
+    N, M = (16, 16, 16), 4096
+    x = inputs.uniform_points(M, 3, seed=12)
+    f = inputs.complex_normal(M, seed=13)
+    fh = inputs.complex_normal(N, seed=14)
+    exact_a, exact_f = ndft.adjoint(x, f, N), ndft.forward(x, fh, N)
+    xd = torch.from_numpy(x).cuda()
+    table = {}
+    for window in ("gaussian", "b_spline", "sinc_power", "kaiser_bessel"):
+        for m in range(1, 13):
+            with Plan(N, M, 2.0, m, window, "fp64") as p:
+                p.set_points(xd)
+                a = p.adjoint(torch.from_numpy(f).cuda()).cpu().numpy()
+                b = p.forward(torch.from_numpy(fh).cuda()).cpu().numpy()
+            ea, ef = ndft.rel_l2(a, exact_a), ndft.rel_l2(b, exact_f)
+            table[window, m] = (ea, ef)
+            if m <= 3:
+                oa = ndft.rel_l2(S.adjoint(x, f, N, 2.0, m, WIN[window]), exact_a)
+                assert abs(ea - oa) <= 1e-3 * oa + 1e-13, (window, m, ea, oa)
+    for window in ("gaussian", "b_spline", "sinc_power", "kaiser_bessel"):
+        print(window, " ".join("%.1e" % table[window, m][0] for m in range(1, 13)))
+        errs = [table[window, m][0] for m in range(1, 13)]
+        floor = 1e-13
+        for e0, e1 in zip(errs, errs[1:]):
+            assert e1 < e0 or e1 < floor, (window, errs)
+        assert errs[-1] < 1e-9
+        # forward and adjoint errors are of the same size (the paper's (a) and (b))
+        for m in range(1, 13):
+            ea, ef = table[window, m]
+            assert ef < 10 * ea + 1e-13 and ea < 10 * ef + 1e-13
 
 
 # ---- wide windows: the 3-D shared-tile kernels up to 26 taps ----------------
