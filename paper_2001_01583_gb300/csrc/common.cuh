@@ -43,6 +43,7 @@ struct WindowDev {
   double kb_norm[kMaxDim];  // Kaiser-Bessel: 1 / (1 - exp(-2 b m)); B-spline: 1 / M_2m(0)
   float bf[kMaxDim];        // the same two, rounded to float once (FP32 kernels)
   float kb_normf[kMaxDim];
+  float binvf[kMaxDim];     // 1 / b in float (FP32 Gaussian)
 };
 
 // psi(u) = phi(u / n) / phi(0) for the distance u (in cells).
@@ -51,7 +52,7 @@ struct WindowDev {
 //   B-spline:       M_2m(u) / M_2m(0)           (window_psi_any only)
 //   sinc-power:     sinc(pi b u)^(2m),  |u| < m
 // The Kaiser-Bessel form is evaluated as
-//   exp(-b u^2 / (z + m)) * m * (-expm1(-2 b z) / z) * kb_norm
+//   exp(-b u^2 / (z + m)) * m * ((1 - exp(-2 b z)) / z) * kb_norm
 // so the large exponent b m cancels exactly instead of in floating point.
 template <typename Real>
 __device__ __forceinline__ Real window_psi(const WindowDev& w, int t, Real u);
@@ -79,10 +80,17 @@ __device__ __noinline__ Real cardinal_bspline_dev(int order, Real u) {
   return v[0];
 }
 
+// FP32: the hardware reciprocal square root, reciprocal and exponential
+// (a few ulp each) in place of correctly rounded division, sqrt and expm1.
+// At the window's peak the result is exp(0) = 1 times 1/z, within 2 ulp;
+// the exponentials' argument-proportional error and the cancellation in
+// 1 - exp(-2 b z) for small z act only where the weight is far below one
+// (at |u| = m it is about 2 b m exp(-b m)), so every weight stays within a
+// few 1e-8 of psi(u) in absolute terms, the size of its FP32 rounding.
 template <>
 __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, float u) {
+  if (w.kind == 0) return expf(-(u * u) * w.binvf[t]);
   const float b = w.bf[t];
-  if (w.kind == 0) return expf(-(u * u) / b);
   const float m = (float)w.m;
   const float u2 = u * u;
   const float m2 = m * m;
@@ -90,15 +98,17 @@ __device__ __forceinline__ float window_psi<float>(const WindowDev& w, int t, fl
   if (w.kind == 3) {
     // sinc(pi c u) with c = b: sinpi needs no large-argument reduction
     const float zz = b * u;
-    const float sc = zz != 0.0f ? sinpif(zz) / (3.14159265358979f * zz) : 1.0f;
+    const float sc = zz != 0.0f ? __fdividef(sinpif(zz), 3.14159265358979f * zz) : 1.0f;
     const float r = sc * sc;
     float p = 1.0f;
     for (int i = 0; i < w.m; ++i) p *= r;
     return p;
   }
-  const float z = sqrtf(m2 - u2);
-  const float e = expf(-b * u2 / (z + m));
-  const float s = -expm1f(-2.0f * b * z) / z;
+  const float z2 = m2 - u2;
+  const float rz = rsqrtf(z2);   // 1 / z
+  const float z = z2 * rz;
+  const float e = __expf(__fdividef(-b * u2, z + m));
+  const float s = (1.0f - __expf(-2.0f * b * z)) * rz;
   return e * m * s * w.kb_normf[t];
 }
 

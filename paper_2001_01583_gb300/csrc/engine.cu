@@ -555,6 +555,7 @@ int Engine::build_layout() {
                      : (s.window == NFFT_B_SPLINE ? 1.0 / cardinal_bspline(2 * s.m, 0.0) : 1.0);
       w.bf[t] = (float)w.b[t];
       w.kb_normf[t] = (float)w.kb_norm[t];
+      w.binvf[t] = w.b[t] != 0.0 ? (float)(1.0 / w.b[t]) : 0.0f;
       if (t < s.d) {
         const auto key = std::make_tuple(s.window, s.N[t], (int64_t)g.n[t], s.m, 0);
         auto f = table_cache.find(key);

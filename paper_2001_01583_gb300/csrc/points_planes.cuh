@@ -36,22 +36,64 @@ struct PlaneShape {
   static constexpr bool POW2 = (W & (W - 1)) == 0;
 };
 
+// Per-point record of a staged batch: the value of the first right-hand
+// side, the tile offset of the point's first tap and its first-tap plane.
+// One 16-byte shared load in FP32.
+template <typename Real>
+struct PlaneRec;
+template <>
+struct __align__(16) PlaneRec<float> {
+  float vx, vy;
+  int off, z;
+};
+template <>
+struct __align__(8) PlaneRec<double> {
+  double vx, vy;
+  int off, z;
+};
+
+// Window weights of a staged point, one row of 3W per point.
+//   interpolation: wz[W] | wy[W] | wx[W]
+//   spreading (NW warps): wz | wy | wx, where wz is rotated when NW divides
+//     W, so that warp w finds the weight of the u-th plane it owns at slot
+//     u * NW + w without knowing the point's plane, and wy is permuted when
+//     the lane rows cover the W rows exactly (Q * PASSES == W), so that lane
+//     row q finds its PASSES weights (rows q, q + Q, ...) side by side.
+template <int W, int NW>
+struct SpreadRow {
+  using S = PlaneShape<W>;
+  static constexpr int TAPS = (W + NW - 1) / NW;
+  static constexpr bool ROT = W % NW == 0;
+  static constexpr bool PERM = S::Q * S::PASSES == W;
+  static constexpr int WZ = 0;
+  static constexpr int WY = W;
+  static constexpr int WX = 2 * W;
+  static constexpr int STRIDE = 3 * W;   // W is even: 8-byte aligned rows
+};
+
+// Weight-row stride of both kernels.
+template <int W>
+__host__ __device__ inline int plane_wt_stride(int) {
+  return 3 * W;
+}
+
 // Shared layout after the tiles (bp points per batch, np right-hand sides):
-//   wt[bp][3W] Real | vt[np][bp] complex | pt[bp] int2 (tile offset, plane) |
-//   jt[bp] int | gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
+//   (16-byte aligned) rec[bp] PlaneRec | wt[bp][stride] Real |
+//   vt[np - 1][bp] complex (right-hand sides after the first) | jt[bp] int |
+//   gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
 template <int W, typename Real>
 __host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile) {
-  return (size_t)bp * (3 * W) * sizeof(Real) + (size_t)np * bp * 2 * sizeof(Real) + (size_t)bp * sizeof(int2) +
-         (size_t)bp * sizeof(int) + (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) +
-         (size_t)nw * 64 * sizeof(Real);
+  return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W>(nw) * sizeof(Real) +
+         (size_t)(np - 1) * bp * 2 * sizeof(Real) + (size_t)(bp + 1) * sizeof(int) +
+         (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) + (size_t)nw * 64 * sizeof(Real);
 }
 
 template <int W, typename Real>
 struct PlaneSmem {
   typename Cplx<Real>::type* tile;   // [np][rows][pitch]
+  PlaneRec<Real>* rec;
   Real* wt;
   typename Cplx<Real>::type* vt;
-  int2* pt;
   int* jt;
   int64_t* gz;
   int64_t* gy;
@@ -61,14 +103,15 @@ struct PlaneSmem {
 
 template <int W, typename Real>
 __device__ __forceinline__ PlaneSmem<W, Real> plane_smem(unsigned char* raw, int np_max, int tile_elems, int bp,
-                                                         const GridGeom& g) {
+                                                         int nw, const GridGeom& g) {
   using C = typename Cplx<Real>::type;
   PlaneSmem<W, Real> s;
   s.tile = reinterpret_cast<C*>(raw);
-  s.wt = reinterpret_cast<Real*>(s.tile + (size_t)np_max * tile_elems);
-  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * 3 * W);
-  s.pt = reinterpret_cast<int2*>(s.vt + (size_t)np_max * bp);
-  s.jt = reinterpret_cast<int*>(s.pt + bp);
+  const size_t rec_at = ((size_t)np_max * tile_elems * sizeof(C) + 15) & ~(size_t)15;
+  s.rec = reinterpret_cast<PlaneRec<Real>*>(raw + rec_at);
+  s.wt = reinterpret_cast<Real*>(s.rec + bp);
+  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * plane_wt_stride<W>(nw));
+  s.jt = reinterpret_cast<int*>(s.vt + (size_t)(np_max - 1) * bp);
   s.gz = reinterpret_cast<int64_t*>(s.jt + bp + (bp & 1));   // keep 8-byte alignment
   s.gy = s.gz + g.tile[0];
   s.gx = s.gy + g.tile[1];
@@ -93,29 +136,209 @@ __device__ __forceinline__ void plane_index_tables(const PlaneSmem<W, Real>& s, 
   }
 }
 
-// Stage a batch: thread t handles point first + t.
-template <int W, typename Real>
+// Stage a batch: thread t handles point first + t.  NW > 0: the spreading
+// layout for NW warps (values of every right-hand side of the pass);
+// NW == 0: the interpolation layout (no values, the point's index instead).
+template <int W, int NW, typename Real>
 __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a, const PlaneSmem<W, Real>& s,
                                                   const WindowDev& win, const typename Cplx<Real>::type* f_in,
                                                   int64_t M, int first, int nb, int r0, int np, int bp, int T1,
-                                                  int pitch, bool want_values) {
+                                                  int pitch, int stride) {
+  using S = PlaneShape<W>;
   const int t = threadIdx.x;
-  if (t < nb) {
-    const int idx = first + t;
-    const int j = a.pts.perm[idx];
-    const uint32_t loc = a.pts.local[idx];
-    const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
-    s.pt[t] = make_int2((l0 * T1 + l1) * pitch + l2, l0);
+  if (t >= nb) return;
+  const int idx = first + t;
+  const int j = a.pts.perm[idx];
+  const uint32_t loc = a.pts.local[idx];
+  const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
+  PlaneRec<Real> rec;
+  rec.off = (l0 * T1 + l1) * pitch + l2;
+  rec.z = l0;
+  rec.vx = 0;
+  rec.vy = 0;
+  Real* w = s.wt + (size_t)t * stride;
+  Real base[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) base[d] = a.pts.delta[d][idx] + (Real)(win.m - win.shift);
+  if (NW == 0) {
     s.jt[t] = j;
-    Real* w = s.wt + t * (3 * W);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const Real base = a.pts.delta[d][idx] + (Real)(win.m - win.shift);
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(win, d, base - (Real)i);
+      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(win, d, base[d] - (Real)i);
+  } else {
+    using R = SpreadRow<W, (NW > 0 ? NW : 1)>;
+    constexpr int NWs = NW > 0 ? NW : 1;
+#pragma unroll
+    for (int u = 0; u < R::TAPS; ++u)
+#pragma unroll
+      for (int ww = 0; ww < NWs; ++ww) {
+        const int slot = u * NWs + ww;
+        const int i = R::ROT ? ((ww - l0) & (NWs - 1)) + u * NWs : slot;
+        if (slot < W) w[R::WZ + slot] = window_psi<Real>(win, 0, base[0] - (Real)i);
+      }
+#pragma unroll
+    for (int q = 0; q < S::Q; ++q)
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) {
+        const int slot = R::PERM ? q * S::PASSES + k : k * S::Q + q;
+        const int i = k * S::Q + q;
+        if (i < W) w[R::WY + slot] = window_psi<Real>(win, 1, base[1] - (Real)i);
+      }
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[R::WX + i] = window_psi<Real>(win, 2, base[2] - (Real)i);
+    if (np > 0) {
+      const auto v0 = f_in[(int64_t)r0 * M + j];
+      rec.vx = v0.x;
+      rec.vy = v0.y;
     }
-    if (want_values)
-      for (int r = 0; r < np; ++r) s.vt[r * bp + t] = f_in[(int64_t)(r0 + r) * M + j];
+    for (int r = 1; r < np; ++r) s.vt[(r - 1) * bp + t] = f_in[(int64_t)(r0 + r) * M + j];
+  }
+  s.rec[t] = rec;
+}
+
+// PASSES consecutive weights of a spreading row (8-byte aligned pairs).
+template <int N, typename Real>
+__device__ __forceinline__ void load_row(const Real* p, Real* out) {
+  if (sizeof(Real) == 4 && N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p + k);
+      out[k] = v.x;
+      out[k + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = p[k];
+  }
+}
+
+// 32-bit shared-memory accesses (the spreading loop's addresses are byte
+// offsets in the block's shared window).
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float lds_f1(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// The weights a spreading lane needs for one point: those of the planes its
+// warp owns (u-th: tap (warp - z) mod NW + u NW), of its rows (q + k Q) and
+// of its column ix.  Zero where a tap is past the window.
+template <int W, int NW, typename Real>
+__device__ __forceinline__ void spread_point_weights(const Real* w, int z, int warp, int q, int ix, bool active,
+                                                     Real* wz, Real* wy, Real& wx) {
+  using S = PlaneShape<W>;
+  using R = SpreadRow<W, NW>;
+  const int i0 = (warp - z) & (NW - 1);
+#pragma unroll
+  for (int u = 0; u < R::TAPS; ++u) {
+    if (R::ROT) {
+      wz[u] = w[R::WZ + u * NW + warp];
+    } else {
+      const int i = i0 + u * NW;
+      wz[u] = i < W ? w[R::WZ + i] : (Real)0;
+    }
+  }
+  if (R::PERM) {
+    if (active) {
+      load_row<S::PASSES>(w + R::WY + q * S::PASSES, wy);
+    } else {
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) wy[k] = 0;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < S::PASSES; ++k) {
+      const int i = k * S::Q + q;
+      wy[k] = (active && i < W) ? w[R::WY + i] : (Real)0;
+    }
+  }
+  wx = w[R::WX + ix];
+}
+
+// The plane-owner loop over a staged batch for one right-hand side in FP32
+// (see k_spread_planes): each point's record and weights are loaded one
+// point ahead; the warp adds the point into the cells of its planes.
+template <int W, int NW, typename Real>
+__device__ __forceinline__ void spread_points_fast(const PlaneSmem<W, Real>& s, int nb, int warp, int lane_off,
+                                                   int q, int ix, int pstride, int qstride) {
+  using S = PlaneShape<W>;
+  using R = SpreadRow<W, NW>;
+  constexpr uint32_t ROW = 4u * R::STRIDE;   // bytes per weight row
+  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile) + 8u * (uint32_t)lane_off;
+  const uint32_t rec_a = (uint32_t)__cvta_generic_to_shared(s.rec);
+  const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
+  const uint32_t wz_a = wt_a + 4u * (uint32_t)(R::WZ + warp);
+  const uint32_t wy_a = wt_a + 4u * (uint32_t)(R::WY + q * S::PASSES);
+  const uint32_t wx_a = wt_a + 4u * (uint32_t)(R::WX + ix);
+  const uint32_t pb = 8u * (uint32_t)pstride;
+  uint32_t qoff[S::PASSES], uoff[R::TAPS];
+#pragma unroll
+  for (int k = 0; k < S::PASSES; ++k) qoff[k] = 8u * (uint32_t)(k * qstride);
+#pragma unroll
+  for (int u = 0; u < R::TAPS; ++u) uoff[u] = (uint32_t)(u * NW) * pb;
+  float4 nrec = lds_f4(rec_a);
+  float nwz[R::TAPS], nwy[S::PASSES], nwx;
+#pragma unroll
+  for (int u = 0; u < R::TAPS; ++u) nwz[u] = lds_f1(wz_a + 4u * (uint32_t)(u * NW));
+#pragma unroll
+  for (int k = 0; k < S::PASSES; k += 2) {
+    const float2 t = lds_f2(wy_a + 4u * k);
+    nwy[k] = t.x;
+    nwy[k + 1] = t.y;
+  }
+  nwx = lds_f1(wx_a);
+#pragma unroll 2
+  for (int pp = 0; pp < nb; ++pp) {
+    const float4 rc = nrec;
+    float wz[R::TAPS], wy[S::PASSES];
+    const float wx = nwx;
+#pragma unroll
+    for (int u = 0; u < R::TAPS; ++u) wz[u] = nwz[u];
+#pragma unroll
+    for (int k = 0; k < S::PASSES; ++k) wy[k] = nwy[k];
+    const uint32_t pn = (uint32_t)min(pp + 1, nb - 1);
+    nrec = lds_f4(rec_a + 16u * pn);
+#pragma unroll
+    for (int u = 0; u < R::TAPS; ++u) nwz[u] = lds_f1(wz_a + ROW * pn + 4u * (uint32_t)(u * NW));
+#pragma unroll
+    for (int k = 0; k < S::PASSES; k += 2) {
+      const float2 t = lds_f2(wy_a + ROW * pn + 4u * k);
+      nwy[k] = t.x;
+      nwy[k + 1] = t.y;
+    }
+    nwx = lds_f1(wx_a + ROW * pn);
+    const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);   // first tap whose plane this warp owns
+    const uint32_t a0 = tile_a + 8u * (uint32_t)__float_as_int(rc.z) + (uint32_t)i0 * pb;
+#pragma unroll
+    for (int u = 0; u < R::TAPS; ++u) {
+      const float wzx = wz[u] * wx;
+      const float vr = rc.x * wzx, vi = rc.y * wzx;
+      const uint32_t au = a0 + uoff[u];
+      float2 c[S::PASSES];
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) c[k] = lds_f2(au + qoff[k]);
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) {
+        c[k].x = fmaf(vr, wy[k], c[k].x);
+        c[k].y = fmaf(vi, wy[k], c[k].y);
+        sts_f2(au + qoff[k], c[k]);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -124,8 +347,11 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   using C = typename Cplx<Real>::type;
   using S = PlaneShape<W>;
   static_assert((NW & (NW - 1)) == 0 && NW <= 8, "warps per block must be a power of two, at most 8");
-  constexpr int TAPS = (W + NW - 1) / NW;   // at most this many planes of a point per warp
-  constexpr bool EVEN = W % NW == 0;        // every warp takes exactly TAPS planes
+  using R = SpreadRow<W, NW>;                // R::TAPS: at most this many planes of a point per warp
+  constexpr bool EVEN = W % NW == 0;        // every warp takes exactly R::TAPS planes
+  // FP32, every lane busy on every pass, rotated and permuted weight rows:
+  // the single-right-hand-side loop runs on 32-bit shared addresses
+  constexpr bool FAST = sizeof(Real) == 4 && EVEN && S::FULL && R::ROT && R::PERM && S::PASSES % 2 == 0;
   constexpr int BP = 32 * NW;    // points per batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -146,51 +372,73 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
     C* grid = static_cast<C*>(it.grid);
     const int T1 = g.tile[1], T2 = g.tile[2];
     const int rows = g.tile[0] * T1;
-    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, g);
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, NW, g);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
     for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
     plane_index_tables<W, Real>(s, g, origin);
+    const int lane_off = ix + q * pitch;   // this lane's first cell in a plane of the footprint
+    const int pstride = T1 * pitch;        // tile plane
+    const int qstride = S::Q * pitch;      // rows between a lane's passes
     for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
       const int np = min(a.rhs_per_pass, call.nrhs - r0);
       for (int e = threadIdx.x; e < np * tile_elems; e += BP) s.tile[e] = cmake<C>(0.0, 0.0);
       for (int pb = 0; pb < sub.count; pb += BP) {
         const int nb = min(BP, sub.count - pb);
         __syncthreads();   // tile zeroed / previous batch no longer read
-        plane_stage_batch<W, Real>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, np, BP, T1, pitch, true);
+        plane_stage_batch<W, NW, Real>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, np, BP, T1, pitch,
+                                       R::STRIDE);
         __syncthreads();
+        if (FAST && np == 1) {
+          spread_points_fast<W, NW>(s, nb, warp, lane_off, q, ix, pstride, qstride);
+          continue;
+        }
+        // a point's parameters, loaded one point ahead (the tables are
+        // read-only here): the record, the weights of this warp's planes,
+        // of this lane's rows and of its column
+        PlaneRec<Real> nrec = s.rec[0];
+        Real nwz[R::TAPS], nwy[S::PASSES], nwx;
+        spread_point_weights<W, NW, Real>(s.wt, nrec.z, warp, q, ix, active, nwz, nwy, nwx);
+#pragma unroll 2
         for (int pp = 0; pp < nb; ++pp) {
-          const int2 rec = s.pt[pp];                // (tile offset of the point's first tap, its plane)
-          const Real* w = s.wt + pp * (3 * W);
-          const Real wx = w[2 * W + ix];
-          Real wy[S::PASSES];
+          const PlaneRec<Real> rec = nrec;
+          Real wz[R::TAPS], wy[S::PASSES];
+          const Real wx = nwx;
 #pragma unroll
-          for (int k = 0; k < S::PASSES; ++k) {
-            const int iy = k * S::Q + q;
-            wy[k] = (active && iy < W) ? w[W + iy] : (Real)0;
+          for (int u = 0; u < R::TAPS; ++u) wz[u] = nwz[u];
+#pragma unroll
+          for (int k = 0; k < S::PASSES; ++k) wy[k] = nwy[k];
+          {
+            const int pn = min(pp + 1, nb - 1);
+            nrec = s.rec[pn];
+            spread_point_weights<W, NW, Real>(s.wt + pn * R::STRIDE, nrec.z, warp, q, ix, active, nwz, nwy, nwx);
           }
-          const int i0 = (warp - rec.y) & (NW - 1);   // first tap whose plane this warp owns
-          const int lanebase = rec.x + ix + q * pitch;
+          const int i0 = (warp - rec.z) & (NW - 1);   // first tap whose plane this warp owns
+          const int cell0 = rec.off + lane_off + i0 * pstride;
           for (int r = 0; r < np; ++r) {
-            const C v = s.vt[r * BP + pp];
-            C* tr = s.tile + r * tile_elems + lanebase;
+            Real vx = rec.vx, vy = rec.vy;
+            if (r > 0) {
+              const C v = s.vt[(r - 1) * BP + pp];
+              vx = v.x;
+              vy = v.y;
+            }
+            C* tr = s.tile + r * tile_elems + cell0;
 #pragma unroll
-            for (int u = 0; u < TAPS; ++u) {
-              const int i = i0 + u * NW;
-              if (!EVEN && i >= W) break;
-              const Real wzx = w[i] * wx;
-              const Real vr = v.x * wzx, vi = v.y * wzx;
-              C* plane = tr + i * T1 * pitch;
+            for (int u = 0; u < R::TAPS; ++u) {
+              if (!EVEN && i0 + u * NW >= W) break;
+              const Real wzx = wz[u] * wx;
+              const Real vr = vx * wzx, vi = vy * wzx;
+              C* plane = tr + u * NW * pstride;
               C cell[S::PASSES];
 #pragma unroll
               for (int k = 0; k < S::PASSES; ++k)
-                if (active && k * S::Q + q < W) cell[k] = plane[k * S::Q * pitch];
+                if (active && k * S::Q + q < W) cell[k] = plane[k * qstride];
 #pragma unroll
               for (int k = 0; k < S::PASSES; ++k) {
                 if (active && k * S::Q + q < W) {
                   cell[k].x += vr * wy[k];
                   cell[k].y += vi * wy[k];
-                  plane[k * S::Q * pitch] = cell[k];
+                  plane[k * qstride] = cell[k];
                 }
               }
             }
@@ -242,7 +490,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
     const int T1 = g.tile[1], T2 = g.tile[2];
     const int rows = g.tile[0] * T1;
     const int plane_stride = T1 * pitch;
-    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, g);
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, nw, g);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
     for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
@@ -280,7 +528,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
       for (int pb = 0; pb < sub.count; pb += bp) {
         const int nb = min(bp, sub.count - pb);
         __syncthreads();
-        plane_stage_batch<W, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, np, bp, T1, pitch, false);
+        plane_stage_batch<W, 0, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, 0, bp, T1, pitch, 3 * W);
         __syncthreads();
         for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
           const int pp = p0 + grp;
@@ -296,7 +544,7 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
               wy[i] = w[W + i];
             }
             wx = w[2 * W + ix];
-            base = s.pt[pp].x + ix;
+            base = s.rec[pp].off + ix;
           }
           for (int r = 0; r < np; ++r) {
             Real ar = 0, ai = 0;
