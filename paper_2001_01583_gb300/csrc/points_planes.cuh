@@ -138,7 +138,8 @@ __device__ __forceinline__ void plane_index_tables(const PlaneSmem<W, Real>& s, 
 
 // Stage a batch: thread t handles point first + t.  NW > 0: the spreading
 // layout for NW warps (values of every right-hand side of the pass);
-// NW == 0: the interpolation layout (no values, the point's index instead).
+// NW == 0: the interpolation layout (no values, the point's index instead);
+// NW < 0: the interpolation layout with wy permuted as for spreading.
 template <int W, int NW, typename Real>
 __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a, const PlaneSmem<W, Real>& s,
                                                   const WindowDev& win, const typename Cplx<Real>::type* f_in,
@@ -187,12 +188,16 @@ __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a
       }
 #pragma unroll
     for (int i = 0; i < W; ++i) w[R::WX + i] = window_psi<Real>(win, 2, base[2] - (Real)i);
-    if (np > 0) {
-      const auto v0 = f_in[(int64_t)r0 * M + j];
-      rec.vx = v0.x;
-      rec.vy = v0.y;
+    if (NW < 0) {
+      s.jt[t] = j;
+    } else {
+      if (np > 0) {
+        const auto v0 = f_in[(int64_t)r0 * M + j];
+        rec.vx = v0.x;
+        rec.vy = v0.y;
+      }
+      for (int r = 1; r < np; ++r) s.vt[(r - 1) * bp + t] = f_in[(int64_t)(r0 + r) * M + j];
     }
-    for (int r = 1; r < np; ++r) s.vt[(r - 1) * bp + t] = f_in[(int64_t)(r0 + r) * M + j];
   }
   s.rec[t] = rec;
 }
@@ -228,6 +233,11 @@ __device__ __forceinline__ float2 lds_f2(uint32_t a) {
 __device__ __forceinline__ float lds_f1(uint32_t a) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int lds_i1(uint32_t a) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
 __device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
@@ -389,9 +399,11 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
         plane_stage_batch<W, NW, Real>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, np, BP, T1, pitch,
                                        R::STRIDE);
         __syncthreads();
-        if (FAST && np == 1) {
-          spread_points_fast<W, NW>(s, nb, warp, lane_off, q, ix, pstride, qstride);
-          continue;
+        if constexpr (FAST) {
+          if (np == 1) {
+            spread_points_fast<W, NW>(s, nb, warp, lane_off, q, ix, pstride, qstride);
+            continue;
+          }
         }
         // a point's parameters, loaded one point ahead (the tables are
         // read-only here): the record, the weights of this warp's planes,
@@ -464,8 +476,112 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   }
 }
 
+// Interpolation of a staged batch for one right-hand side in FP32.  A warp
+// takes 4 points at a time, one after another: lane (ix, q) reads cell ix
+// of rows q, q + Q, ... of every plane of the point's footprint, with the
+// spreading layout's conflict-free rows, and sums them with the plane and
+// row weights; times the column weight, that is the lane's share of the
+// point's value.  A transposed butterfly then reduces the 4 points' 8 real
+// values over the warp at once (10 shuffles): after the exchanges over
+// lane bits 4, 3 and 2 each lane keeps one value, and bits 1 and 0 finish
+// its sum.
 template <int W, typename Real>
-__global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
+__device__ __forceinline__ void interp_points_fast(const PlaneSmem<W, Real>& s, int nb, int warp, int nw, int lane,
+                                                   int pitch, int pstride, typename Cplx<Real>::type* out) {
+  using S = PlaneShape<W>;
+  constexpr int PG = 4;                      // points per warp pass
+  constexpr uint32_t ROW = 4u * 3 * W;       // bytes per weight row (16-byte multiple)
+  const int ix = lane % W, q = lane / W;
+  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile) + 8u * (uint32_t)(ix + q * pitch);
+  const uint32_t off_a = (uint32_t)__cvta_generic_to_shared(s.rec) + 8u;   // PlaneRec<float>::off
+  const uint32_t jt_a = (uint32_t)__cvta_generic_to_shared(s.jt);
+  const uint32_t wz_a = (uint32_t)__cvta_generic_to_shared(s.wt);
+  const uint32_t wy_a = wz_a + 4u * (uint32_t)(W + q * S::PASSES);
+  const uint32_t wx_a = wz_a + 4u * (uint32_t)(2 * W + ix);
+  const uint32_t pb = 8u * (uint32_t)pstride;
+  uint32_t qoff[S::PASSES];
+#pragma unroll
+  for (int k = 0; k < S::PASSES; ++k) qoff[k] = 8u * (uint32_t)(k * S::Q * pitch);
+  const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+  for (int p0 = warp * PG; p0 < nb; p0 += nw * PG) {
+    float v[2 * PG];
+#pragma unroll
+    for (int g = 0; g < PG; ++g) {
+      const uint32_t pp = (uint32_t)min(p0 + g, nb - 1);   // past the batch: recomputed, not written
+      const int off = lds_i1(off_a + 16u * pp);
+      float wz[W], wy[S::PASSES];
+#pragma unroll
+      for (int i = 0; i < W; i += 4) {
+        const float4 t = lds_f4(wz_a + ROW * pp + 4u * i);
+        wz[i] = t.x;
+        wz[i + 1] = t.y;
+        wz[i + 2] = t.z;
+        wz[i + 3] = t.w;
+      }
+#pragma unroll
+      for (int k = 0; k < S::PASSES; k += 2) {
+        const float2 t = lds_f2(wy_a + ROW * pp + 4u * k);
+        wy[k] = t.x;
+        wy[k + 1] = t.y;
+      }
+      const float wx = lds_f1(wx_a + ROW * pp);
+      float ur[S::PASSES], ui[S::PASSES];
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) ur[k] = ui[k] = 0.0f;
+      uint32_t ad = tile_a + 8u * (uint32_t)off;
+#pragma unroll
+      for (int iz = 0; iz < W; ++iz) {
+#pragma unroll
+        for (int k = 0; k < S::PASSES; ++k) {
+          const float2 c = lds_f2(ad + qoff[k]);
+          ur[k] = fmaf(wz[iz], c.x, ur[k]);
+          ui[k] = fmaf(wz[iz], c.y, ui[k]);
+        }
+        ad += pb;
+      }
+      float sr = 0.0f, si = 0.0f;
+#pragma unroll
+      for (int k = 0; k < S::PASSES; ++k) {
+        sr = fmaf(wy[k], ur[k], sr);
+        si = fmaf(wy[k], ui[k], si);
+      }
+      v[2 * g] = sr * wx;
+      v[2 * g + 1] = si * wx;
+    }
+    float a4[4], a2[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float send = b4 ? v[j] : v[4 + j];
+      const float keep = b4 ? v[4 + j] : v[j];
+      a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float send = b3 ? a4[j] : a4[2 + j];
+      const float keep = b3 ? a4[2 + j] : a4[j];
+      a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float a1;
+    {
+      const float send = b2 ? a2[0] : a2[1];
+      const float keep = b2 ? a2[1] : a2[0];
+      a1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    // lane l now holds value l >> 2: point l >> 3, real part when bit 2 is 0
+    const float im = __shfl_down_sync(0xffffffffu, a1, 4);
+    const int g = lane >> 3;
+    if ((lane & 7) == 0 && p0 + g < nb) {
+      const int j = lds_i1(jt_a + 4u * (uint32_t)(p0 + g));
+      out[j] = make_float2(a1, im);
+    }
+  }
+}
+
+// FP32 narrow windows: three blocks of 256 threads per SM (at most 85 registers)
+template <int W, typename Real>
+__global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
   using C = typename Cplx<Real>::type;
   using S = PlaneShape<W>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -477,6 +593,10 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
   const int tile_elems = lay.warp_cells;
   const int grp = lane / W, ix = lane % W;
   const bool active = grp < S::PPW;
+  // FP32 with every lane busy (8 taps or fewer: the registers of wider
+  // windows would halve the resident blocks): one point at a time per warp
+  // in the spreading lane layout (conflict-free rows at the chosen pitch)
+  constexpr bool FAST = sizeof(Real) == 4 && S::FULL && S::PASSES % 2 == 0 && W <= 8;
   int lo, hi;
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
@@ -528,6 +648,16 @@ __global__ void __launch_bounds__(256) k_interp_groups(PointKernelArgs<Real> a, 
       for (int pb = 0; pb < sub.count; pb += bp) {
         const int nb = min(bp, sub.count - pb);
         __syncthreads();
+        if constexpr (FAST) {
+          if (np == 1) {
+            plane_stage_batch<W, -1, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, 0, bp, T1,
+                                           pitch, 3 * W);
+            __syncthreads();
+            interp_points_fast<W, Real>(s, nb, warp, nw, lane, pitch, plane_stride,
+                                        f_out + (int64_t)r0 * it.M);
+            continue;
+          }
+        }
         plane_stage_batch<W, 0, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, 0, bp, T1, pitch, 3 * W);
         __syncthreads();
         for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
