@@ -24,17 +24,57 @@ __device__ __forceinline__ int find_item(const T* offs, int n, T v) {
   return lo;
 }
 
-// Reduce one coordinate: x -> x - floor(x) in [0, 1] (exact for Eq. 5, which
-// is 1-periodic), u = n x, cell c = floor(u) in [0, n), offset u - c in FP64,
-// then rounded once to Real.  An offset that rounds up to 1 moves to the next
-// cell with offset 0 (the same position).
+// Reduce one coordinate: x -> x - floor(x) in [0, 1) (exact for Eq. 5, which
+// is 1-periodic), u = n x, cell c = floor(u) in [0, n), offset u - c, rounded
+// once to Real.  An offset that rounds up to 1 moves to the next cell with
+// offset 0 (the same position).
+//
+// FP32 offsets: integer arithmetic throughout (FP64 is a slow pipe here).
+// The fraction of |x| is taken from its mantissa bits as a 64-bit binary
+// fraction F (exact for |x| >= 2^-12; below that the bits under 2^-64 are
+// dropped), the fraction of x is F or 1 - F, and the 96-bit product n F
+// splits into the cell (its bits 64 and up) and the offset (the 64 below),
+// whose top 32 bits are rounded to float.
+// FP64 offsets: x - floor(x) and n (x - floor(x)) in FP64, so the offset
+// carries the rounding of that product (about n 2^-53 cells) like any FP64
+// evaluation of the same formula.
+__device__ __forceinline__ unsigned long long frac64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = 1075 - e;   // |x| = mant * 2^-sh
+  unsigned long long f;
+  if (e == 0 || sh <= 0) f = 0;           // zero, subnormal (taken as 0) or an integer
+  else if (sh <= 64) f = mant << (64 - sh);
+  else if (sh < 64 + 53) f = mant >> (sh - 64);
+  else f = 0;
+  if ((b >> 63) && f) f = 0ull - f;       // frac(-y) = 1 - frac(y)
+  return f;
+}
+
 template <typename Real>
-__device__ __forceinline__ void reduce_coord(double x, int n, int& c, Real& delta) {
+__device__ __forceinline__ void reduce_cell(double x, int n, int& c, Real& delta);
+template <>
+__device__ __forceinline__ void reduce_cell<float>(double x, int n, int& c, float& delta) {
+  const unsigned long long f = frac64(x);
+  const unsigned long long nn = (unsigned long long)n;
+  c = (int)__umul64hi(f, nn);
+  delta = __uint2float_rn((unsigned)((f * nn) >> 32)) * 2.3283064365386963e-10f;   // 2^-32
+}
+template <>
+__device__ __forceinline__ void reduce_cell<double>(double x, int n, int& c, double& delta) {
   const double xw = x - floor(x);
   const double u = (double)n * xw;
   const double cf = floor(u);
-  int ci = (int)cf;
-  Real dr = (Real)(u - cf);
+  c = (int)cf;
+  delta = u - cf;
+}
+
+template <typename Real>
+__device__ __forceinline__ void reduce_coord(double x, int n, int& c, Real& delta) {
+  int ci;
+  Real dr;
+  reduce_cell<Real>(x, n, ci, dr);
   if (dr >= (Real)1) {
     dr = (Real)0;
     ci += 1;
