@@ -114,8 +114,8 @@ def _step_hbm_bytes(wl):
 # kernel's sources hash to `sources`; otherwise the traffic is reported null.
 TRAFFIC = {
     # uniform set's spread launch, N = 64^3, M = 1e6 (profiles/spread_interp_planes_config_3d_n64_m1e6.md)
-    "spread": {"bytes": 44922624 + 28160, "sources": "c45f46017e07bde44b6bb931ca583151a8145891e8597cf59a6533fa5bdb8976"},
-    "interp": {"bytes": 36925952 + 5632, "sources": "c45f46017e07bde44b6bb931ca583151a8145891e8597cf59a6533fa5bdb8976"},
+    "spread": {"bytes": 44899072 + 29696, "sources": "c30c07064ac2acf38481645668cbd50bb0eba60b9ed5a08c9bec11e5e0be9e15"},
+    "interp": {"bytes": 36900096 + 9728, "sources": "c30c07064ac2acf38481645668cbd50bb0eba60b9ed5a08c9bec11e5e0be9e15"},
 }
 TRAFFIC_SOURCES = {"spread": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu"),
                    "interp": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu")}
