@@ -104,6 +104,43 @@ def _stage_hbm_bytes(stage, wl):
     }[stage]
 
 
+def _transform_bytes(N, M, sigma=SIGMA, nrhs=1, real=4, sort=True, adjoint=True, forward=True, ewald=False):
+    """Algorithmic HBM bytes of one transform's stages, with the terms of
+    _stage_hbm_bytes: point records (index, packed cell, d offsets), values,
+    the oversampled grid once per pass, I_N once per scaling pass.  An Ewald
+    adjoint reads its weighted modes once instead of writing fhat."""
+    d = len(N)
+    NN = int(np.prod(N))
+    cells = int(np.prod([int(round(sigma * n)) for n in N]))
+    cz = 2 * real
+    rec = 8 + d * real
+    b = 0
+    if sort:
+        b += M * (2 * 8 * d + 16 + rec)
+    if adjoint:
+        b += M * (rec + cz * nrhs) + cells * cz * nrhs + 2 * cells * cz * nrhs
+        b += NN * cz if ewald else NN * cz * 2 * nrhs
+    if forward:
+        b += (cells + NN) * cz * nrhs + 2 * cells * cz * nrhs + M * (rec + cz * nrhs) + cells * cz * nrhs
+    return b
+
+
+def _step_roofline(bytes_per_step, ms, note):
+    """Whole-step HBM roofline (workloads without per-stage events)."""
+    peaks, kind = _peaks()
+    achieved = bytes_per_step / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "whole step", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "traffic": None, "step_hbm_bytes": bytes_per_step,
+            "note": note}
+
+
+def _cpu_baseline(args, wl, rank, world):
+    if rank != 0 or world != 1 or args.no_cpu_baseline:
+        return None
+    v, threads, desc = _oracle_sample(wl)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+
 def _step_hbm_bytes(wl):
     per_set = sum(_stage_hbm_bytes(s, wl) for s in ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp"))
     return per_set * len(wl["sets"])
@@ -497,6 +534,11 @@ def run_batch(args, wl, rank, world):
                        "precision": args.precision, "autotuned": bool(args.autotune),
                        "l2": "flushed between timed steps (512 MB write outside the step events)"},
             "gpu_launches": launches_timed, "clocks": clocks}
+    real = 4 if args.precision == "fp32" else 8
+    hbm = sum(_transform_bytes(it["N"], it["M"], SIGMA, it["nrhs"], real, sort=False) for it in items)
+    line["roofline"] = _step_roofline(hbm, ms, "one adjoint and one forward per item (points sorted outside the "
+                                               "step); per-kernel roofline in the 3-D workloads")
+    line["cpu_baseline"] = _cpu_baseline(args, wl, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
@@ -612,6 +654,16 @@ def run_extra(args, wl, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clocks}
+    real = 4 if prec == "fp32" else 8
+    if args.workload == "fluorite":
+        hbm = _transform_bytes(N, points_per_step, SIGMA, 1, real, forward=False, ewald=True)
+    elif args.workload == "picker":
+        hbm = _transform_bytes(N, M, s_, 1, real)
+    else:
+        hbm = _transform_bytes(N, M, SIGMA, 1, real)
+    line["roofline"] = _step_roofline(hbm, ms, "set_points and the transforms of one step; per-kernel roofline "
+                                               "in the 3-D workloads")
+    line["cpu_baseline"] = _cpu_baseline(args, wl, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     for p in plans:
