@@ -9,11 +9,13 @@ interpolate).  Units: a transform of M points counts M nonuniform points, so a
 step processes 2 sets x 2 transforms x M points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config|small|sparse|batch|1d|fluorite|picker]
+                  [--workload config|small|sparse|batch|1d|fluorite|picker|fig13|fig16]
                   [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
-with ncu's multi-pass sections.  Prints one JSON line (rank 0).  Under torchrun
+with ncu's multi-pass sections.  "--workload fig13" and "fig16" sweep the
+sizes of the paper's runtime figures (58^3 ... 120^3 points; fluorite with
+12 x {32 ... 64}^3 ions) and list every size in config.sweep.  Prints one JSON line (rank 0).  Under torchrun
 every rank runs its own independent copy of the workload (weak scaling, no
 collective on the data path); the value is all ranks' points over the slowest
 rank's time.
@@ -52,6 +54,12 @@ WORKLOADS = {
     "picker": dict(N=(256, 256, 256), M=30_000_000, sets=("clustered64",), extra=True,
                    name="3-D adjoint+forward NFFT, N=256^3, M=3e7 points in 64 Gaussian clusters (std 0.01), eps=1e-5, "
                         "window parameters from the learned picker, mixed FP32"),
+    "fig13": dict(N=(128, 128, 128), M=120 ** 3, sets=("uniform",), sweep=True,
+                  name="sweep shaped like Fig. 13: 3-D adjoint+forward NFFT of 58^3, 80^3, 100^3 and 120^3 uniform "
+                       "points at N=64^3 and 128^3, Kaiser-Bessel m=4, sigma=2, mixed FP32; value at 120^3, N=128^3"),
+    "fig16": dict(N=(128, 128, 128), M=12 * 64 ** 3, sets=("fluorite",), sweep=True, lc=64,
+                  name="sweep shaped like Fig. 16: Ewald reciprocal energy of fluorite with 12 x {32, 45, 56, 64}^3 "
+                       "ions, N=128^3, Kaiser-Bessel m=6, sigma=2, alpha=0.6; value at 12 x 64^3 ions"),
     "sparse": dict(N=(64, 64, 64), M=20000, sets=("uniform",),
                    name="3-D adjoint+forward NFFT, N=64^3, M=2e4 uniform (about 10 points per bin: the sparse "
                         "grid-warp kernels), Kaiser-Bessel m=4, sigma=2, mixed FP32"),
@@ -265,7 +273,7 @@ def _oracle_sample(wl, seconds_target=15.0):
     # the batch samples its largest item (N = 64^3, M = 1e5)
     N, M = wl["N"] or (64, 64, 64), wl["M"] or 100000
     if "fluorite" in wl["sets"]:
-        r, _, L = inputs.fluorite(32)
+        r, _, L = inputs.fluorite(wl.get("lc", 32))
         x = inputs.box_points(r, L)
     else:
         x = inputs.uniform_points(M, len(N), seed=0)
@@ -671,6 +679,107 @@ def run_extra(args, wl, rank, world):
     return 0
 
 
+def run_sweep(args, wl, rank, world):
+    """The single-GPU counterparts of the paper's runtime sweeps (Fig. 13:
+    NFFT of 58^3 ... 120^3 points; Fig. 16: fluorite energies of
+    12 x {32 ... 64}^3 ions): every size timed like the other workloads,
+    one line whose value is the largest size's throughput."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_01583_gb300 import Plan, _lib, inputs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.load()
+    stream = torch.cuda.Stream(dev)
+    prec = args.precision
+    ctype = np.complex64 if prec == "fp32" else np.complex128
+    real = 4 if prec == "fp32" else 8
+    with torch.cuda.stream(stream):
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    steps = max(3, args.steps // 4)
+    rows, clocks_all, launches_all = [], [], 0
+    if args.workload == "fig13":
+        cases = [((n,) * 3, side ** 3) for n in (64, 128) for side in (58, 80, 100, 120)]
+    else:
+        cases = [((128,) * 3, lc) for lc in (32, 45, 56, 64)]
+    for N, size in cases:
+        if args.workload == "fig13":
+            M = size
+            x = torch.from_numpy(inputs.uniform_points(M, 3, seed=100 * rank + size % 97)).to(dev)
+            f = torch.from_numpy(inputs.complex_normal(M, seed=100 * rank + 1, dtype=ctype)).to(dev)
+            fh = torch.from_numpy(inputs.complex_normal(N, seed=100 * rank + 2, dtype=ctype)).to(dev)
+            plan = Plan(N, M, SIGMA, MCUT, WINDOW, prec, stream=stream)
+            oa = torch.empty(N, dtype=f.dtype, device=dev)
+            of = torch.empty(M, dtype=f.dtype, device=dev)
+            if args.autotune:
+                with torch.cuda.stream(stream):
+                    plan.set_points(x)
+                    plan.autotune(reps=3)
+
+            def step():
+                plan.set_points(x)
+                plan.adjoint(f, out=oa)
+                plan.forward(fh, out=of)
+            units = 2 * M
+            hbm = _transform_bytes(N, M, SIGMA, 1, real)
+            row = {"N": N[0], "M": M, "points": "%d^3" % round(M ** (1 / 3))}
+        else:
+            r, q, L = inputs.fluorite(size)
+            M = len(q)
+            x = torch.from_numpy(inputs.box_points(r, L)).to(dev)
+            qd = torch.from_numpy(q.astype(ctype)).to(dev)
+            plan = Plan(N, M, SIGMA, 6, WINDOW, prec, stream=stream)
+            out = {}
+
+            def step():
+                plan.set_points(x)
+                out["e"] = plan.ewald_reciprocal(qd, L, 0.6)
+            units = M
+            hbm = _transform_bytes(N, M, SIGMA, 1, real, forward=False, ewald=True)
+            row = {"N": N[0], "cells": size, "ions": M}
+        ms, clocks, launches = _timed(step, stream, dev, steps, args.warmup, flush, plans=[plan])
+        if args.workload == "fig16":
+            row["reciprocal_energy"] = out["e"][0]
+        row.update(ms_per_step=ms, units_per_s=units / (ms * 1e-3),
+                   step_hbm_frac=hbm / (ms * 1e-3) / 1e9 / _peaks()[0]["hbm_gbs"])
+        rows.append(row)
+        clocks_all.append(clocks)
+        launches_all += launches
+        plan.close()
+        del x
+        torch.cuda.empty_cache()
+    t = torch.tensor([rows[-1]["ms_per_step"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = t.item()
+    units = 2 * cases[-1][1] if args.workload == "fig13" else rows[-1]["ions"]
+    sm = [c["sm_mhz"] for c in clocks_all if c.get("sm_mhz")]
+    clocks = {"sm_mhz": float(np.median(sm)) if sm else None,
+              "sm_max_mhz": max((c.get("sm_max_mhz") or 0) for c in clocks_all) or None,
+              "reasons": sorted({r_ for c in clocks_all for r_ in c.get("reasons", [])}),
+              "samples": sum(c.get("samples", 0) for c in clocks_all)}
+    last = cases[-1]
+    hbm = _transform_bytes(last[0], last[1], SIGMA, 1, real) if args.workload == "fig13" else \
+        _transform_bytes(last[0], rows[-1]["ions"], SIGMA, 1, real, forward=False, ewald=True)
+    line = {"metric": METRIC, "value": units * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "precision": prec, "autotuned": bool(args.autotune),
+                       "l2": "flushed between timed steps (512 MB write outside the step events)",
+                       "parallelism": "independent replicas x%d" % world, "sweep": rows},
+            "gpu_launches": launches_all, "clocks": clocks,
+            "roofline": _step_roofline(hbm, ms, "largest size of the sweep, whole step; per-kernel roofline in "
+                                                "the 3-D workloads"),
+            "cpu_baseline": _cpu_baseline(args, wl, rank, world)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -695,6 +804,8 @@ def main():
     try:
         if args.workload == "batch":
             return run_batch(args, wl, rank, world)
+        if wl.get("sweep"):
+            return run_sweep(args, wl, rank, world)
         if wl.get("extra"):
             return run_extra(args, wl, rank, world)
         return run_ours(args, wl, rank, world)
