@@ -616,6 +616,10 @@ def run_extra(args, wl, rank, world):
         qd = torch.from_numpy(q.astype(np.complex128 if prec == "fp64" else np.complex64)).to(dev)
         plan = Plan(N, len(q), 2.0, 6, "kaiser_bessel", prec, stream=stream)
         out = {}
+        if args.autotune:
+            with torch.cuda.stream(stream):
+                plan.set_points(xq)
+                plan.autotune(reps=3)
 
         def step():
             plan.set_points(xq)
@@ -634,6 +638,11 @@ def run_extra(args, wl, rank, world):
         oa = torch.empty((1,) + N, dtype=torch.complex64, device=dev)
         of = torch.empty((1, M), dtype=torch.complex64, device=dev)
         plans = [Plan(N, M, s_, m_, w_, "fp32", stream=stream), Plan(N, M, rs, rm, rw, "fp32", stream=stream)]
+        if args.autotune:
+            with torch.cuda.stream(stream):
+                for p in plans:
+                    p.set_points(x)
+                    p.autotune(reps=3)
 
         def make(p):
             def st():
@@ -655,6 +664,7 @@ def run_extra(args, wl, rank, world):
     if args.workload == "fluorite":
         extra = {"reciprocal_energy": out["e"], "alpha": 0.6, "L": float(L)}
     cfg = {"workload": wl["name"], "points_per_step_per_gpu": points_per_step, "precision": prec,
+           "autotuned": bool(args.autotune) and args.workload in ("fluorite", "picker"),
            "l2": "flushed between timed steps (512 MB write outside the step events)",
            "parallelism": "independent replicas x%d" % world}
     cfg.update(extra)
@@ -733,6 +743,10 @@ def run_sweep(args, wl, rank, world):
             qd = torch.from_numpy(q.astype(ctype)).to(dev)
             plan = Plan(N, M, SIGMA, 6, WINDOW, prec, stream=stream)
             out = {}
+            if args.autotune:
+                with torch.cuda.stream(stream):
+                    plan.set_points(x)
+                    plan.autotune(reps=3)
 
             def step():
                 plan.set_points(x)

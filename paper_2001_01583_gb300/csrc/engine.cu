@@ -1591,6 +1591,37 @@ int Engine::autotune(int reps, double* best_ms) {
     }
     drop_graphs();
   }
+  // the sparse/dense split, for spreading and for interpolation: points of a
+  // bin below which the grid-warp kernels take it (the automatic threshold
+  // is a rule of thumb; the crossover moves with the window and the point
+  // density)
+  if (st == NFFT_OK && method_opt == NFFT_METHOD_AUTO) {
+    for (int pass = 0; pass < 2 && st == NFFT_OK; ++pass) {
+      int& opt = pass == 0 ? sparse_opt : sparse_interp_opt;
+      const int base = opt;
+      int keep = base;
+      for (int th : {-1, 32, 128, 512, 1 << 20}) {
+        if (th == base) continue;
+        opt = th;
+        CK(cudaStreamSynchronize(stream));
+        double ms = 0;
+        if (build_layout() != NFFT_OK || reset_points() != NFFT_OK ||
+            time_transforms(reps, fin, fout, hin, hout, &ms) != NFFT_OK) {
+          cudaGetLastError();
+          continue;
+        }
+        if (ms < best) {
+          best = ms;
+          keep = th;
+        }
+      }
+      opt = keep;
+      CK(cudaStreamSynchronize(stream));
+      st = build_layout();
+      if (st == NFFT_OK) st = reset_points();
+    }
+    drop_graphs();
+  }
   (void)save_bin;
   (void)save_P;
   CK(cudaStreamSynchronize(stream));
