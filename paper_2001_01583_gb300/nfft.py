@@ -11,6 +11,7 @@ forward = Eq. 6 (f(x_j) = sum_k fhat(k) exp(+2 pi i k.x_j)).
 """
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -64,10 +65,23 @@ class Plan:
         self.close()
 
     # -- helpers -----------------------------------------------------------------
+    def _copy_stream(self):
+        """Host copies run on their own stream, ordered against the plan's
+        stream by events, so that they overlap kernels of earlier calls."""
+        if getattr(self, "_cs", None) is None:
+            self._cs = torch.cuda.Stream(self.device)
+        return self._cs
+
     def _to_device(self, t, dtype):
         if t.device.type != "cuda":
-            with torch.cuda.stream(self.stream):
-                return t.to(device=self.device, dtype=dtype, non_blocking=True).contiguous(), True
+            cs = self._copy_stream()
+            with torch.cuda.stream(cs):
+                d = t.to(device=self.device, dtype=dtype, non_blocking=True).contiguous()
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            self.stream.wait_event(ev)
+            d.record_stream(self.stream)
+            return d, True
         if t.dtype != dtype:
             raise TypeError("expected %s, got %s" % (dtype, t.dtype))
         return t.contiguous(), False
@@ -81,34 +95,63 @@ class Plan:
         self._x = xd  # keep alive until the sort kernels have read it
         _lib.check(self._lib.nfft_set_points(self._h, ctypes.c_void_p(xd.data_ptr())), "nfft_set_points")
 
+    def _result_buffer(self, shape, out):
+        """Device buffer for a result: `out` itself when it is a CUDA tensor,
+        else a new one, kept alive for the plan's stream."""
+        if out is not None and out.device.type == "cuda":
+            if out.dtype != self.cdtype or out.numel() != int(np.prod(shape)):
+                raise ValueError("out must hold %s %s values" % (shape, self.cdtype))
+            return out
+        dev = torch.empty(shape, dtype=self.cdtype, device=self.device)
+        dev.record_stream(self.stream)
+        return dev
+
+    def _finish(self, dev, out, host, single):
+        """A CPU `out` (pinned, for an asynchronous copy) receives the result
+        on the copy stream once the plan's stream has produced it: valid after
+        sync().  Otherwise a host input gets its result back as a new CPU
+        tensor (a blocking copy)."""
+        if out is not None and out.device.type == "cpu":
+            if out.dtype != self.cdtype or out.numel() != dev.numel() or not out.is_contiguous():
+                raise ValueError("out must be a contiguous tensor of %d %s values" % (dev.numel(), self.cdtype))
+            res = out.view(dev.shape)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            cs = self._copy_stream()
+            cs.wait_event(ev)
+            with torch.cuda.stream(cs):
+                res.copy_(dev, non_blocking=True)
+            dev.record_stream(cs)
+        elif host:
+            with torch.cuda.stream(self.stream):
+                res = dev.to("cpu")
+        else:
+            res = dev.view(dev.shape)
+        return res[0] if single else res
+
     def adjoint(self, f, out=None):
-        """Eq. 5.  f: (M,) or (R, M) complex; returns N or (R,) + N complex."""
+        """Eq. 5.  f: (M,) or (R, M) complex; returns N or (R,) + N complex.
+        out: a CUDA tensor, or a pinned CPU tensor that receives the result
+        asynchronously (read it after sync())."""
         single = f.dim() == 1
         rows = (1 if single else f.shape[0]) if self.M == 0 else -1
         fd, host = self._to_device(f.reshape(rows, self.M), self.cdtype)
         R = fd.shape[0]
-        if out is None:
-            out = torch.empty((R,) + self.N, dtype=self.cdtype, device=self.device)
-        _lib.check(self._lib.nfft_adjoint(self._h, ctypes.c_void_p(fd.data_ptr()), ctypes.c_void_p(out.data_ptr()), R),
+        dev = self._result_buffer((R,) + self.N, out)
+        _lib.check(self._lib.nfft_adjoint(self._h, ctypes.c_void_p(fd.data_ptr()), ctypes.c_void_p(dev.data_ptr()), R),
                    "nfft_adjoint")
-        if host:
-            with torch.cuda.stream(self.stream):
-                out = out.to("cpu")
-        return out[0] if single else out
+        return self._finish(dev.view((R,) + self.N), out, host, single)
 
     def forward(self, fhat, out=None):
-        """Eq. 6.  fhat: N or (R,) + N complex; returns (M,) or (R, M) complex."""
+        """Eq. 6.  fhat: N or (R,) + N complex; returns (M,) or (R, M) complex.
+        out: as for adjoint()."""
         single = fhat.dim() == self.d
         hd, host = self._to_device(fhat.reshape((-1,) + self.N), self.cdtype)
         R = hd.shape[0]
-        if out is None:
-            out = torch.empty((R, self.M), dtype=self.cdtype, device=self.device)
-        _lib.check(self._lib.nfft_forward(self._h, ctypes.c_void_p(hd.data_ptr()), ctypes.c_void_p(out.data_ptr()), R),
+        dev = self._result_buffer((R, self.M), out)
+        _lib.check(self._lib.nfft_forward(self._h, ctypes.c_void_p(hd.data_ptr()), ctypes.c_void_p(dev.data_ptr()), R),
                    "nfft_forward")
-        if host:
-            with torch.cuda.stream(self.stream):
-                out = out.to("cpu")
-        return out[0] if single else out
+        return self._finish(dev.view((R, self.M)), out, host, single)
 
     def ewald_reciprocal(self, q, L, alpha):
         """Eq. 12 for charges q (M values) at the points set (x = r / L).
@@ -130,7 +173,10 @@ class Plan:
         return out
 
     def sync(self):
-        """Wait for the plan's stream; raises NFFTError for a device-side error."""
+        """Wait for the plan's stream and its host copies; raises NFFTError for
+        a device-side error."""
+        if getattr(self, "_cs", None) is not None:
+            self._cs.synchronize()
         _lib.check(self._lib.nfft_sync(self._h), "nfft_sync")
 
     def set_option(self, option, value):

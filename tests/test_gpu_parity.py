@@ -499,6 +499,29 @@ def test_host_buffers_end_to_end():
     _elementwise(a.numpy(), S.adjoint(x, f, N, 2.0, 4, S.KAISER_BESSEL), 1e-12)
 
 
+def test_pinned_host_results_asynchronous():
+    """Host inputs with pinned CPU `out` tensors: the results arrive on the
+    plan's stream and equal the device path's (the forward bit for bit; the
+    adjoint up to the order of its tile flushes' atomic additions)."""
+    N, M = (16, 16, 16), 3000
+    x = inputs.uniform_points(M, 3, seed=91)
+    f = inputs.complex_normal(M, seed=92, dtype=np.complex64)
+    fh = inputs.complex_normal(N, seed=93, dtype=np.complex64)
+    with _plan(N, M, 2.0, 4, "kaiser_bessel", "fp32") as p:
+        p.set_points(torch.from_numpy(x).cuda())
+        a_dev = p.adjoint(torch.from_numpy(f).cuda()).cpu()
+        b_dev = p.forward(torch.from_numpy(fh).cuda()).cpu()
+        oa = torch.empty(N, dtype=torch.complex64).pin_memory()
+        ob = torch.empty(M, dtype=torch.complex64).pin_memory()
+        p.set_points(torch.from_numpy(x).pin_memory())
+        ra = p.adjoint(torch.from_numpy(f).pin_memory(), out=oa)
+        rb = p.forward(torch.from_numpy(fh).pin_memory(), out=ob)
+        p.sync()
+    assert ra.data_ptr() == oa.data_ptr() and rb.data_ptr() == ob.data_ptr()
+    _elementwise(oa.numpy(), a_dev.numpy(), 1e-6)
+    assert torch.equal(ob, b_dev)
+
+
 # ---- full size of the 3-D configuration, sampled oracle ----------------------
 @pytest.mark.parametrize("kind", ["uniform", "clustered"])
 def test_full_size_3d_sampled(kind):
