@@ -249,10 +249,13 @@ int nfft_stage_times(nfft_plan* plan, double* ms, int64_t* launches, int reset);
 
 /* Autotuner: with the points set, time adjoint + forward for candidate
  * layouts -- bin edges, points per subproblem, then the threads per block of
- * spreading and of interpolation -- on synthetic values (median of `reps`
- * runs each, CUDA events) and keep the fastest.  Sets the points again for
- * the winner; allocates temporary buffers during the call.  *best_ms (may be
- * NULL) gets the winner's adjoint + forward milliseconds. */
+ * spreading and of interpolation, then (with NFFT_METHOD_AUTO) the sparse /
+ * dense split of each (NFFT_OPT_SPARSE_POINTS and _INTERP: never, automatic,
+ * or 32, 128, 512 or all points per bin) -- on synthetic values (median of
+ * `reps` runs each, CUDA events) and keep the fastest.  The chosen values
+ * replace the corresponding options.  Sets the points again for the winner;
+ * allocates temporary buffers during the call.  *best_ms (may be NULL) gets
+ * the winner's adjoint + forward milliseconds. */
 int nfft_autotune(nfft_plan* plan, int reps, double* best_ms);
 
 /* Host-only parameter rule (no device needed): the oversampled size n_t for
