@@ -25,7 +25,6 @@
 
 namespace gbnfft {
 
-constexpr int kLoadRows = 8;   // tile rows a warp loads at once (loads in flight)
 
 template <int W>
 struct PlaneShape {
@@ -235,6 +234,16 @@ __device__ __forceinline__ float lds_f1(uint32_t a) {
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
   return v;
 }
+// One grid cell copied from global to shared memory without passing through
+// registers (8 bytes in FP32, 16 in FP64); completed by cp_async_wait_all.
+__device__ __forceinline__ void cp_async_cell(uint32_t dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_cell(uint32_t dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ int lds_i1(uint32_t a) {
   int v;
   asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
@@ -619,32 +628,18 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
     for (int r0 = 0; r0 < call.nrhs; r0 += a.rhs_per_pass) {
       const int np = min(a.rhs_per_pass, call.nrhs - r0);
       __syncthreads();
-      // load the tile: a warp takes kLoadRows rows at a time, lanes along
-      // the rows, all loads issued before the shared-memory stores
-      for (int e0 = warp * kLoadRows; e0 < np * rows; e0 += nw * kLoadRows) {
-        for (int x = lane; x < T2; x += 32) {
-          const int64_t gx = s.gx[x];
-          C v[kLoadRows];
-#pragma unroll
-          for (int u = 0; u < kLoadRows; ++u) {
-            const int e = e0 + u;
-            if (e < np * rows) {
-              const int r = e / rows;
-              const int row = e - r * rows;
-              const int z = row / T1, y = row - z * T1;
-              v[u] = grid_in[(int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y] + gx];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kLoadRows; ++u) {
-            const int e = e0 + u;
-            if (e < np * rows) {
-              const int r = e / rows;
-              s.tile[r * tile_elems + (e - r * rows) * pitch + x] = v[u];
-            }
-          }
-        }
+      // load the tile with asynchronous global-to-shared copies: a warp per
+      // row, lanes along it; every copy of the tile is in flight before the
+      // block waits for them
+      for (int e = warp; e < np * rows; e += nw) {
+        const int r = e / rows;
+        const int row = e - r * rows;
+        const int z = row / T1, y = row - z * T1;
+        const C* src = grid_in + (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s.tile + r * tile_elems + row * pitch);
+        for (int x = lane; x < T2; x += 32) cp_async_cell(dst + (uint32_t)(x * sizeof(C)), src + s.gx[x]);
       }
+      cp_async_wait_all();
       for (int pb = 0; pb < sub.count; pb += bp) {
         const int nb = min(bp, sub.count - pb);
         __syncthreads();
