@@ -229,6 +229,23 @@ int nfft_ewald_reciprocal_sum(nfft_plan* plan, const void* S_dev, double L, doub
 int nfft_ewald_reciprocal_sum_noalloc(int d, const int64_t* N, int precision, const void* S_dev, double L,
                                       double alpha, double* sum_dev, void* cuda_stream);
 
+/* Real-space Ewald energy, Eq. 11 (Section 5): 1/2 sum over pairs (i, j)
+ * and periodic images n, omitting n = 0 for i = j, of q_i q_j erfc(alpha d)/d
+ * with d = |r_i - r_j + n L| < rcut.  r_dev: n x 3 positions (device, FP64,
+ * row-major, any finite values: reduced mod L per coordinate); q_dev: n
+ * charges (device, FP64).  Requires 0 < rcut < L.  When L / rcut >= 3 the
+ * ions are sorted into a cell list of edge >= rcut (only the minimum image
+ * of a pair is then within rcut) and the pair terms are FP32 from offsets to
+ * the cells' centres, with FP64 sums per ion; otherwise every pair and its
+ * 27 nearest images are summed in FP64 (n <= 65536, else
+ * NFFT_ERR_UNSUPPORTED).  The total is a fixed-order FP64 reduction.
+ * Allocates scratch, runs on cuda_stream (NULL = legacy default stream) and
+ * waits for it; *energy gets U^R (host double).  The paper computes this term
+ * on the CPU side of its method; the library adds it so that the whole
+ * Madelung check (Eq. 10) runs on the GPU. */
+int nfft_ewald_real_space(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha, double rcut,
+                          double* energy, void* cuda_stream);
+
 /* Wait for the plan's stream, then report (and clear) the device error flag. */
 int nfft_sync(nfft_plan* plan);
 

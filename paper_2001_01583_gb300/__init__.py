@@ -10,11 +10,11 @@ The CUDA library (libgbnfft.so) is loaded on first use; importing this
 package alone (for example for the input generators) needs no GPU.
 """
 
-__all__ = ["Plan", "Batch", "plan_params"]
+__all__ = ["Plan", "Batch", "plan_params", "ewald_real_space"]
 
 
 def __getattr__(name):
-    if name in ("Plan", "Batch", "plan_params"):
+    if name in ("Plan", "Batch", "plan_params", "ewald_real_space"):
         from . import nfft
         return getattr(nfft, name)
     raise AttributeError(name)

@@ -320,3 +320,23 @@ def plan_params(N, sigma=2.0, m=4, window="kaiser_bessel"):
     win = _lib.WINDOWS[window] if isinstance(window, str) else int(window)
     _lib.check(lib.nfft_plan_params(d, Narr, float(sigma), int(m), win, nout, ctypes.byref(taps)), "nfft_plan_params")
     return tuple(nout), taps.value
+
+
+def ewald_real_space(r, q, L, alpha, rcut, stream=None):
+    """Eq. 11: the real-space Ewald energy of charges q (n) at positions r
+    (n x 3, any finite values, periodic box of edge L), pairs and images
+    closer than rcut (0 < rcut < L).  CPU tensors are copied to the device
+    first.  Waits for the stream and returns the energy as a float."""
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(st):
+        rd = r.to(device=dev, dtype=torch.float64).contiguous()
+        qd = q.to(device=dev, dtype=torch.float64).contiguous()
+    if rd.dim() != 2 or rd.shape[1] != 3 or qd.numel() != rd.shape[0]:
+        raise ValueError("r must be (n, 3) and q must hold n charges")
+    out = ctypes.c_double()
+    _lib.check(lib.nfft_ewald_real_space(int(rd.shape[0]), ctypes.c_void_p(rd.data_ptr()),
+                                         ctypes.c_void_p(qd.data_ptr()), float(L), float(alpha), float(rcut),
+                                         ctypes.byref(out), _stream_handle(st)), "nfft_ewald_real_space")
+    return out.value

@@ -142,3 +142,76 @@ def test_madelung_fluorite_32_cells(precision, tol):
     mad = ewald.madelung(ur_per_ion * len(q) + uk, len(q), 3, 2, -1)
     assert abs(mad - direct) <= tol * abs(direct)
     assert abs(mad - _golden("madelung_fluorite.txt")) < 5e-5
+
+
+# ---- Eq. 11 on the GPU (nfft_ewald_real_space) -------------------------------
+def _real_space(r, q, L, alpha, rcut):
+    from paper_2001_01583_gb300 import ewald_real_space
+    return ewald_real_space(torch.from_numpy(np.asarray(r, dtype=np.float64)).cuda(),
+                            torch.from_numpy(np.asarray(q, dtype=np.float64)).cuda(), L, alpha, rcut)
+
+
+def test_real_space_all_pairs_form_against_oracle():
+    # L / rcut < 3: every pair and its 27 nearest images, FP64
+    r, q, L = inputs.fluorite(4)
+    alpha, rcut = 1.0, 0.99 * L
+    ref = ewald.real_space_energy(r, q, L, alpha, rcut)
+    got = _real_space(r, q, L, alpha, rcut)
+    assert abs(got - ref) <= 1e-12 * abs(ref)
+    assert _real_space(r, q, L, alpha, rcut) == got           # fixed-order reduction
+
+
+def test_real_space_cell_list_on_a_supercell():
+    # L / rcut >= 3: the cell list (FP32 pair terms).  A perfect crystal has
+    # the same real-space energy per ion in any supercell, so the 8-cell
+    # crystal's energy is 8 times the 4-cell one's (the cut-offs differ only
+    # where erfc(alpha d) / d < 1e-17)
+    r4, q4, L4 = inputs.fluorite(4)
+    ref = 8 * ewald.real_space_energy(r4, q4, L4, 1.0, 0.99 * L4)
+    r8, q8, L8 = inputs.fluorite(8)
+    assert L8 / 6.0 >= 3
+    got = _real_space(r8, q8, L8, 1.0, 6.0)
+    assert abs(got - ref) <= 2e-6 * abs(ref)
+
+
+def test_real_space_cell_list_random_ions_against_oracle():
+    # random ions, coordinates outside [0, L) (reduced mod L), cell list;
+    # the bar is relative to the sum of the terms' magnitudes (the oracle with
+    # all charges positive), since a random configuration's energy cancels
+    rng = np.random.default_rng(11)
+    n, L, alpha, rcut = 1500, 20.0, 0.9, 6.5
+    r = rng.uniform(0.0, L, size=(n, 3)) + L * rng.integers(-2, 3, size=(n, 3))
+    q = rng.choice([-1.0, 1.0, 2.0], size=n)
+    ref = ewald.real_space_energy(np.mod(r, L), q, L, alpha, rcut)
+    scale = ewald.real_space_energy(np.mod(r, L), np.abs(q), L, alpha, rcut)
+    got = _real_space(r, q, L, alpha, rcut)
+    assert abs(got - ref) <= 1e-6 * scale
+
+
+def test_madelung_fluorite_32_cells_all_on_gpu():
+    # the paper's system with both parts of the Ewald energy from the GPU:
+    # Eq. 11 by the cell list (alpha = 0.6, cut-off 10: erfc(6) ~ 2e-17),
+    # Eq. 12 by the adjoint NFFT (N = 128^3, m = 6, FP64), Eq. 10 from both
+    alpha = 0.6
+    r2, q2, L2 = inputs.fluorite(2)
+    direct = ewald.madelung(ewald.ewald_energy(r2, q2, L2, 1.5, min(7.0 / 1.5, 0.99 * L2),
+                                               int(math.ceil(2.2 * 1.5 * L2))), len(q2), 3, 2, -1)
+    r, q, L = inputs.fluorite(32)
+    ur = _real_space(r, q, L, alpha, 10.0)
+    with _plan((128, 128, 128), len(q), 6, "fp64") as p:
+        p.set_points(torch.from_numpy(inputs.box_points(r, L)).cuda())
+        uk, _, _ = p.ewald_reciprocal(torch.from_numpy(q.astype(np.complex128)).cuda(), L, alpha)
+        p.sync()
+    mad = ewald.madelung(ur + uk, len(q), 3, 2, -1)
+    assert abs(mad - direct) <= 2e-6 * abs(direct)
+    assert abs(mad - _golden("madelung_fluorite.txt")) < 5e-5
+
+
+def test_real_space_argument_errors():
+    from paper_2001_01583_gb300 import _lib
+    r, q, L = inputs.fluorite(1)
+    for alpha, rcut in ((0.0, 1.0), (1.0, 0.0), (1.0, L), (1.0, 2 * L)):
+        with pytest.raises(_lib.NFFTError) as e:
+            _real_space(r, q, L, alpha, rcut)
+        assert e.value.status == _lib.ERR_INVALID_ARG
+    assert _real_space(np.zeros((0, 3)), np.zeros(0), L, 1.0, 1.0) == 0.0
