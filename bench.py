@@ -159,8 +159,8 @@ def _step_hbm_bytes(wl):
 # kernel's sources hash to `sources`; otherwise the traffic is reported null.
 TRAFFIC = {
     # uniform set's spread launch, N = 64^3, M = 1e6 (profiles/spread_interp_planes_config_3d_n64_m1e6.md)
-    "spread": {"bytes": 44901376 + 21248, "sources": "78e396c9ba2d3ac8742f566cf5f2886962da1f521589b5b25539bdb2c5143a73"},
-    "interp": {"bytes": 36901888 + 8960, "sources": "78e396c9ba2d3ac8742f566cf5f2886962da1f521589b5b25539bdb2c5143a73"},
+    "spread": {"bytes": 44901376 + 21248, "sources": "92d338ca3e5f02a026b34161a242629d2b2592bf77bce6109da4401b664ee9a0"},
+    "interp": {"bytes": 36901888 + 8960, "sources": "92d338ca3e5f02a026b34161a242629d2b2592bf77bce6109da4401b664ee9a0"},
 }
 TRAFFIC_SOURCES = {"spread": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu"),
                    "interp": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu")}

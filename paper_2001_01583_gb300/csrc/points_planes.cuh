@@ -2,9 +2,9 @@
 //
 // A block takes a subproblem (a run of bin-sorted points of one bin) and
 // stages its points in batches of blockDim.x: thread t loads point t's
-// record and value, evaluates its 3*W window weights into a shared table and
-// stores the point's tile offset, so the per-point work of every warp is
-// table lookups.  The wrapped grid index of every tile row and column is
+// record (value, tile offset, first plane) and evaluates its 3*W window
+// weights into a shared table, so the per-point work of every warp is table
+// lookups.  The wrapped grid index of every tile row and column is
 // tabulated once per subproblem for the tile load / flush.
 //
 // spread ("plane owner"): warp w of NW (a power of two) owns the tile planes
@@ -15,10 +15,15 @@
 //   Inside a plane, lane (ix, q) = (lane % W, lane / W) takes cell ix of rows
 //   q, q + Q, ... (Q = 32 / W).  After the subproblem the tile is added to
 //   the grid once (vector atomics: halos of neighbouring bins overlap).
-// interp ("point groups"): a warp works on 32/W points at once, W lanes per
-//   point; lane ix of a group sums column ix of its point's W x W rows from
-//   the read-only tile with the weights held in registers, then the group
-//   adds its W partial sums.
+//   In FP32 with every lane busy and one right-hand side, the point loop
+//   runs on 32-bit shared addresses with the next point's parameters loaded
+//   ahead (spread_points_fast).
+// interp: the tile arrives by cp.async copies.  In FP32 with up to 8 taps a
+//   warp reads one point at a time in the spreading lane layout and reduces
+//   four points at once (interp_points_fast); otherwise ("point groups") a
+//   warp works on 32/W points at once, W lanes per point: lane ix of a group
+//   sums column ix of its point's W x W rows with the weights held in
+//   registers, then the group adds its W partial sums.
 #pragma once
 
 #include "points_tiled.cuh"
