@@ -1540,11 +1540,8 @@ int Engine::autotune(int reps, double* best_ms) {
     for (int b : {1024, 256, 4096})
       for (int P : Ps) cands.push_back(Cand{{b, 0, 0}, P});
   }
-  const int save_bin[3] = {bin_opt[0], bin_opt[1], bin_opt[2]};
-  const int save_P = max_sub_opt;
   double best = 1e30;
   Cand best_c = cands[0];
-  int best_sw = 0, best_iw = 0;
   for (const Cand& c : cands) {
     if (st != NFFT_OK) break;
     for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? c.bin[t] : 0;
@@ -1587,7 +1584,6 @@ int Engine::autotune(int reps, double* best_ms) {
         }
       }
       opt = keep;
-      (pass == 0 ? best_sw : best_iw) = keep;
     }
     drop_graphs();
   }
@@ -1622,8 +1618,6 @@ int Engine::autotune(int reps, double* best_ms) {
     }
     drop_graphs();
   }
-  (void)save_bin;
-  (void)save_P;
   CK(cudaStreamSynchronize(stream));
   for (void* p : owned) cudaFree(p);
   profile = was_profiling;
