@@ -1,24 +1,32 @@
 """Throughput benchmark of the GB300 NFFT library.
 
-Workload (one "step", default): the 3-D configuration N = 64^3, M = 10^6,
-Kaiser-Bessel window m = 4, sigma = 2, mixed FP32 form, on two point sets
-(uniform, and 32 Gaussian clusters of std 0.02).  For each set a step runs
-nfft_set_points (argument reduction + bin sort), the adjoint NFFT (Eq. 5:
-spread, FFT, scale) and the forward NFFT (Eq. 6: subdivide, inverse FFT,
-interpolate).  Units: a transform of M points counts M nonuniform points, so a
-step processes 2 sets x 2 transforms x M points.
+Workload (one "step", default "picker"): the largest configuration that fits
+one GPU, N = 256^3 and M = 3e7 points in 64 Gaussian clusters of std 0.01,
+complex64 values, eps = 1e-5, with the window parameters the learned picker
+chooses, mixed FP32.  A step runs nfft_set_points (argument reduction + bin
+sort), the adjoint NFFT (Eq. 5: spread, FFT, scale) and the forward NFFT
+(Eq. 6: subdivide, inverse FFT, interpolate).  Units: a transform of M points
+counts M nonuniform points, so a step processes 2 x M points per point set.
+The same line reports the relative l2 error (Eq. 9) of the timed outputs at
+sampled frequencies and points against the direct NDFT, the rule-of-thumb
+parameters and the plain FP64 form of the same workload on the same GPU, the
+end-to-end rate with host buffers, and the dominant stage's HBM roofline.
+
+"--workload config" is the 3-D configuration N = 64^3, M = 10^6, Kaiser-Bessel
+m = 4, sigma = 2, on two point sets (uniform, and 32 Gaussian clusters of std
+0.02).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config|small|sparse|batch|1d|fluorite|picker|fig13|fig16]
-                  [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline]
+                  [--workload picker|config|small|sparse|batch|1d|fluorite|fig13|fig16]
+                  [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline] [--no-fp64-form]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  "--workload fig13" and "fig16" sweep the
 sizes of the paper's runtime figures (58^3 ... 120^3 points; fluorite with
-12 x {32 ... 64}^3 ions) and list every size in config.sweep.  Prints one JSON line (rank 0).  Under torchrun
-every rank runs its own independent copy of the workload (weak scaling, no
-collective on the data path); the value is all ranks' points over the slowest
-rank's time.
+12 x {32 ... 64}^3 ions) and list every size in config.sweep.  Prints one JSON
+line (rank 0).  Under torchrun every rank runs its own independent copy of the
+workload (weak scaling, no collective on the data path); the value is all
+ranks' points over the slowest rank's time.
 """
 import argparse
 import json
@@ -37,8 +45,10 @@ METRIC = "NFFT nonuniform points/s at stated rel-l2 error; % of HBM roofline"
 UNIT = "points/s"
 SIGMA, MCUT, WINDOW = 2.0, 4, "kaiser_bessel"
 
+DEFAULT_WORKLOAD = "picker"   # the largest configuration that fits one GPU
+
 WORKLOADS = {
-    "config": dict(N=(64, 64, 64), M=10 ** 6, sets=("uniform", "clustered"),
+    "config": dict(N=(64, 64, 64), M=10 ** 6, sets=("uniform", "clustered"), seeds=dict(x=(0, 1), f=7, fh=8),
                    name="3-D adjoint+forward NFFT, N=64^3, M=10^6, uniform + clustered (32 clusters, std 0.02), "
                         "Kaiser-Bessel m=4, sigma=2, mixed FP32"),
     "batch": dict(N=None, M=None, sets=("batch",),
@@ -51,19 +61,21 @@ WORKLOADS = {
     "fluorite": dict(N=(128, 128, 128), M=12 * 32 ** 3, sets=("fluorite",), extra=True,
                      name="Ewald reciprocal energy of fluorite, 32^3 cells (393216 ions), N=128^3, Kaiser-Bessel m=6, "
                           "sigma=2: set_points + adjoint NFFT of the charges + weighted mode sum"),
-    "picker": dict(N=(256, 256, 256), M=30_000_000, sets=("clustered64",), extra=True,
-                   name="3-D adjoint+forward NFFT, N=256^3, M=3e7 points in 64 Gaussian clusters (std 0.01), eps=1e-5, "
-                        "window parameters from the learned picker, mixed FP32"),
+    "picker": dict(N=(256, 256, 256), M=30_000_000, sets=("clustered64",), picked=True, eps=1e-5,
+                   seeds=dict(x=(0,), f=1, fh=2),
+                   name="learned parameter picker applied to 3-D N=256^3, M=3x10^7 clustered points (64 Gaussian "
+                        "clusters, std 0.01), complex64, eps=1e-5, vs the rule-of-thumb parameters: one step = "
+                        "set_points + adjoint + forward NFFT with the picked window parameters, mixed FP32"),
     "fig13": dict(N=(128, 128, 128), M=120 ** 3, sets=("uniform",), sweep=True,
                   name="sweep shaped like Fig. 13: 3-D adjoint+forward NFFT of 58^3, 80^3, 100^3 and 120^3 uniform "
                        "points at N=64^3 and 128^3, Kaiser-Bessel m=4, sigma=2, mixed FP32; value at 120^3, N=128^3"),
     "fig16": dict(N=(128, 128, 128), M=12 * 64 ** 3, sets=("fluorite",), sweep=True, lc=64,
                   name="sweep shaped like Fig. 16: Ewald reciprocal energy of fluorite with 12 x {32, 45, 56, 64}^3 "
                        "ions, N=128^3, Kaiser-Bessel m=6, sigma=2, alpha=0.6; value at 12 x 64^3 ions"),
-    "sparse": dict(N=(64, 64, 64), M=20000, sets=("uniform",),
+    "sparse": dict(N=(64, 64, 64), M=20000, sets=("uniform",), seeds=dict(x=(0,), f=7, fh=8),
                    name="3-D adjoint+forward NFFT, N=64^3, M=2e4 uniform (about 10 points per bin: the sparse "
                         "grid-warp kernels), Kaiser-Bessel m=4, sigma=2, mixed FP32"),
-    "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",),
+    "small": dict(N=(64, 64, 64), M=500000, sets=("uniform",), seeds=dict(x=(0,), f=7, fh=8),
                   name="3-D adjoint+forward NFFT, N=64^3, M=5e5, uniform, Kaiser-Bessel m=4, sigma=2, mixed FP32 "
                        "(profiling case: the same grid and bins, half the points, one set)"),
 }
@@ -89,47 +101,62 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _taps():
-    return 2 * MCUT   # Kaiser-Bessel: 2m nonzero taps per dimension
+def _oversampled(N_t, sigma):
+    """n_t: the smallest even 2,3,5,7-smooth integer >= sigma N_t (the
+    library's rule, nfft_plan_params)."""
+    n = max(int(np.ceil(sigma * N_t - 1e-9)), 2)
+    while True:
+        r = n
+        for p in (2, 3, 5, 7):
+            while r % p == 0:
+                r //= p
+        if n % 2 == 0 and r == 1:
+            return n
+        n += 1
 
 
-def _stage_hbm_bytes(stage, wl):
-    """Algorithmic HBM bytes of one launch of a stage (complex64 data)."""
-    M = wl["M"]
-    NN = int(np.prod(wl["N"]))
-    cells = int(np.prod([2 * n for n in wl["N"]]))
+def _cells(N, sigma):
+    return int(np.prod([_oversampled(n, sigma) for n in N]))
+
+
+def _stage_hbm_bytes(stage, N, M, sigma=SIGMA, real=4, nrhs=1):
+    """Algorithmic HBM bytes of one launch of a stage: each point's d offsets
+    and value once per pass, the oversampled grid once per pass, two passes
+    per FFT, I_N once per scaling pass.  The sort reads x (8 B per
+    coordinate) once and writes the sorted record (d offsets, the cell and
+    the point's index).  Index and cell words that the kernels also read
+    (perm, packed cell: 8 B per point per pass) are implementation traffic,
+    visible in the measured DRAM bytes, not algorithmic."""
+    d = len(N)
+    NN = int(np.prod(N))
+    cells = _cells(N, sigma)
+    cz = 2 * real
+    rec = d * real
     return {
-        # point record (4 B index + 4 B packed cell + 3 x 4 B offsets) + one value (8 B) + grid once (8 B / cell)
-        "spread": M * (20 + 8) + cells * 8,
-        "interp": M * (20 + 8) + cells * 8,
-        # in-place C2C FFT: one read and one write of the grid
-        "fft": 2 * cells * 8,
-        "ifft": 2 * cells * 8,
-        "deconv": NN * 8 * 2,
-        "pad": cells * 8 + NN * 8,
-        # x read twice (24 B each), bin/rank record written + read (8 B), sorted record written (20 B)
-        "sort": M * (2 * 24 + 16 + 20),
+        "spread": M * (rec + cz * nrhs) + cells * cz * nrhs,
+        "interp": M * (rec + cz * nrhs) + cells * cz * nrhs,
+        "fft": 2 * cells * cz * nrhs,
+        "ifft": 2 * cells * cz * nrhs,
+        "deconv": 2 * NN * cz * nrhs,
+        "pad": (cells + NN) * cz * nrhs,
+        "sort": M * (8 * d + 8 + rec),
     }[stage]
 
 
 def _transform_bytes(N, M, sigma=SIGMA, nrhs=1, real=4, sort=True, adjoint=True, forward=True, ewald=False):
-    """Algorithmic HBM bytes of one transform's stages, with the terms of
-    _stage_hbm_bytes: point records (index, packed cell, d offsets), values,
-    the oversampled grid once per pass, I_N once per scaling pass.  An Ewald
-    adjoint reads its weighted modes once instead of writing fhat."""
-    d = len(N)
+    """Algorithmic HBM bytes of one transform's stages (the terms of
+    _stage_hbm_bytes).  An Ewald adjoint reads its weighted modes once
+    instead of writing fhat."""
     NN = int(np.prod(N))
-    cells = int(np.prod([int(round(sigma * n)) for n in N]))
     cz = 2 * real
-    rec = 8 + d * real
+    st = lambda k: _stage_hbm_bytes(k, N, M, sigma, real, nrhs)   # noqa: E731
     b = 0
     if sort:
-        b += M * (2 * 8 * d + 16 + rec)
+        b += st("sort")
     if adjoint:
-        b += M * (rec + cz * nrhs) + cells * cz * nrhs + 2 * cells * cz * nrhs
-        b += NN * cz if ewald else NN * cz * 2 * nrhs
+        b += st("spread") + st("fft") + (NN * cz if ewald else st("deconv"))
     if forward:
-        b += (cells + NN) * cz * nrhs + 2 * cells * cz * nrhs + M * (rec + cz * nrhs) + cells * cz * nrhs
+        b += st("pad") + st("ifft") + st("interp")
     return b
 
 
@@ -149,65 +176,72 @@ def _cpu_baseline(args, wl, rank, world):
     return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
 
-def _step_hbm_bytes(wl):
-    per_set = sum(_stage_hbm_bytes(s, wl) for s in ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp"))
-    return per_set * len(wl["sets"])
-
-
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# a stage's kernel, from an ncu capture of this workload, valid while the
-# kernel's sources hash to `sources`; otherwise the traffic is reported null.
-TRAFFIC = {
-    # uniform set's spread launch, N = 64^3, M = 1e6 (profiles/spread_interp_planes_config_3d_n64_m1e6.md)
-    "spread": {"bytes": 44901376 + 21248, "sources": "92d338ca3e5f02a026b34161a242629d2b2592bf77bce6109da4401b664ee9a0"},
-    "interp": {"bytes": 36901888 + 8960, "sources": "92d338ca3e5f02a026b34161a242629d2b2592bf77bce6109da4401b664ee9a0"},
-}
-TRAFFIC_SOURCES = {"spread": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu"),
-                   "interp": ("points_planes.cuh", "points_tiled.cuh", "kernels.h", "common.cuh", "planes_f32.cu")}
+# a stage's kernels, from an ncu capture, valid while the kernels' sources
+# hash to `sources`; otherwise the traffic is reported null.  Keyed by
+# (workload, stage); "scaled" says when a smaller case was captured and its
+# bytes scaled by the units processed.
+TRAFFIC = {}
+TRAFFIC_SOURCES = ("points_planes.cuh", "points_tiled.cuh", "points_gm.cuh", "kernels.h", "common.cuh")
 
 
-def _sources_hash(stage):
+def _sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for name in TRAFFIC_SOURCES.get(stage, ()):
+    for name in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_2001_01583_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def _traffic(stage):
-    rec = TRAFFIC.get(stage)
-    if not rec or rec["sources"] != _sources_hash(stage):
+def _traffic(workload, stage):
+    rec = TRAFFIC.get((workload, stage))
+    if not rec or rec["sources"] != _sources_hash():
         return None
     return rec["bytes"]
 
 
-def _roofline(stages, wl, peaks, kind, sms):
+STAGE_KERNELS = {"spread": "k_spread_planes (dense bins) + k_spread_gm (sparse bins), after a grid memset",
+                 "interp": "k_interp_groups (dense bins) + k_interp_gm (sparse bins)",
+                 "sort": "k_bin_count + k_scan + k_scatter + subproblem kernels",
+                 "fft": "cuFFT C2C", "ifft": "cuFFT C2C", "deconv": "k_deconv_crop", "pad": "k_pad_deconv"}
+
+
+def _roofline(stages, workload, geom, peaks, kind, sms):
+    """The dominant stage's algorithmic HBM bytes per launch over its mean
+    CUDA-event duration in the timed region, against the measured copy
+    bandwidth; the spreading and interpolation stages also against the
+    shared-memory pipe (a derived peak) and the FP32 pipe."""
+    N, M, sigma, taps, real = geom
     total = {k: v[0] for k, v in stages.items() if v[1] > 0}
     per_launch = {k: v[0] / v[1] for k, v in stages.items() if v[1] > 0}
     dom = max(total, key=total.get)
     t = per_launch[dom] * 1e-3
-    if dom in SMEM_BYTES_PER_CELL:
-        # on-chip bound: the shared-memory pipe, 128 B per clock per SM
-        visits = wl["M"] * _taps() ** 3
-        achieved = visits * SMEM_BYTES_PER_CELL[dom] / t / 1e9
-        peak = sms * SMEM_BYTES_PER_CLK_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
-        r = {"bound": "alu", "resource": "shared-memory load/store pipe (%d SMs x 128 B/clk x %.0f MHz)" %
-             (sms, peaks.get("sm_max_mhz", 2070.0)), "achieved": achieved, "peak": peak, "unit": "GB/s",
-             "frac": achieved / peak, "peak_kind": "derived from unit counts and max clock",
-             "cell_updates_per_s": visits / t}
-        # the FP32 arithmetic of the same updates: a complex value times a real
-        # weight added into a complex cell is two FMAs (4 flops) per update,
-        # against 128 FP32 lanes x 2 flops per clock per SM
-        fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-        r["alu_fp32_frac"] = visits * 4 / t / fp32_peak
-    else:
-        achieved = _stage_hbm_bytes(dom, wl) / t / 1e9
-        r = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-             "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind}
-    r.update({"kernel": dom, "traffic": _traffic(dom) if wl is WORKLOADS["config"] else None,
-              "launch_ms": per_launch[dom],
-              "stage_share": {k: round(v / sum(total.values()), 4) for k, v in total.items()}})
+    alg = _stage_hbm_bytes(dom, N, M, sigma, real)
+    achieved = alg / t / 1e9
+    r = {"bound": "hbm", "kernel": dom, "kernels": STAGE_KERNELS.get(dom), "achieved": achieved,
+         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+         "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % kind if kind == "measured" else kind,
+         "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch[dom],
+         "traffic": _traffic(workload, dom),
+         "stage_share": {k: round(v / sum(total.values()), 4) for k, v in total.items()},
+         "stage_hbm_frac": {k: round(_stage_hbm_bytes(k, N, M, sigma, real) / (per_launch[k] * 1e-3) / 1e9 /
+                                     peaks["hbm_gbs"], 4) for k in per_launch if per_launch[k] > 0},
+         "stage_launch_ms": {k: round(v, 5) for k, v in per_launch.items()}}
+    for st in ("spread", "interp"):
+        if st not in per_launch:
+            continue
+        ts = per_launch[st] * 1e-3
+        visits = M * taps ** len(N)
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+        ach = visits * SMEM_BYTES_PER_CELL[st] / ts / 1e9
+        # a complex value times a real weight added into a complex cell is two
+        # FMAs (4 flops) per update, against 128 FP32 lanes x 2 flops per clock per SM
+        r["smem_pipe_" + st] = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                "peak_kind": "derived: %d SMs x 128 B/clk x %.0f MHz" % (sms, mhz),
+                                "cell_updates_per_s": visits / ts,
+                                "alu_fp32_frac": visits * 4 / ts / (sms * 128 * 2 * mhz * 1e6)}
     return r
 
 
@@ -264,23 +298,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_sample(wl, seconds_target=15.0):
+def _workload_inputs(wl, rank):
+    """The seeded synthetic inputs of a plan workload: one point set per
+    entry of wl["sets"], the values f (M complex) and fhat (N complex)."""
+    from paper_2001_01583_gb300 import inputs
+    N, M = wl["N"], wl.get("M")
+    sd = wl.get("seeds", dict(x=tuple(range(len(wl["sets"]))), f=7, fh=8))
+    gens = {"uniform": lambda s: inputs.uniform_points(M, len(N), seed=s),
+            "clustered": lambda s: inputs.clustered_points(M, 3, 32, 0.02, seed=s),
+            "clustered64": lambda s: inputs.clustered_points(M, 3, 64, 0.01, seed=s)}
+    xs = [gens[name](100 * rank + sd["x"][i]) for i, name in enumerate(wl["sets"])]
+    return xs, sd
+
+
+def _oracle_sample(wl, seconds_target=15.0, xs=None, f=None, fh=None):
     """Time the FP64 direct NDFT (the oracle, as it stands) on the host cores
-    for a bounded sample of the workload's points: the adjoint over all of I_N
-    and the forward at the same points.  Returns (points/s, threads, text)."""
+    for a bounded sample of the workload: the adjoint over all of I_N and the
+    forward, both at the first points of the workload's first point set.
+    Returns (points/s, threads, text)."""
     from oracle import ndft
     from paper_2001_01583_gb300 import inputs
     # the batch samples its largest item (N = 64^3, M = 1e5)
     N, M = wl["N"] or (64, 64, 64), wl["M"] or 100000
-    if "fluorite" in wl["sets"]:
+    if xs is not None:
+        x = xs[0]
+    elif "fluorite" in wl["sets"]:
         r, _, L = inputs.fluorite(wl.get("lc", 32))
         x = inputs.box_points(r, L)
+    elif wl.get("seeds"):
+        x = _workload_inputs(wl, 0)[0][0]
     else:
         x = inputs.uniform_points(M, len(N), seed=0)
-    f = inputs.complex_normal(M, seed=1)
-    fh = inputs.complex_normal(N, seed=2)
+    M = x.shape[0]
+    f = inputs.complex_normal(M, seed=1) if f is None else np.asarray(f, dtype=np.complex128)
+    fh = inputs.complex_normal(N, seed=2) if fh is None else np.asarray(fh, dtype=np.complex128)
     threads = ndft.threads_used(0)
-    m0 = 256
+    m0 = 16
     t0 = time.perf_counter()
     ndft.adjoint(x[:m0], f[:m0], N)
     ndft.forward(x[:m0], fh, N)
@@ -294,13 +347,35 @@ def _oracle_sample(wl, seconds_target=15.0):
                                  "points, FP64, %d threads, %.1f s" % ("x".join(map(str, N)), ms, threads, dt)
 
 
+def _oracle_check(x, f, fh, N, samples):
+    """The relative l2 error (Eq. 9) of timed GPU outputs at sampled outputs
+    against the direct NDFT (the oracle): samples maps a label to
+    (ks, adjoint values at ks, js, forward values at js).  Part of the CPU
+    oracle leg, after the timed region."""
+    from oracle import ndft
+    out = {}
+    f64 = np.asarray(f, dtype=np.complex128)
+    fh64 = np.asarray(fh, dtype=np.complex128)
+    refs = {}
+    for label, (ks, ga, js, gb) in samples.items():
+        key = (ks.tobytes(), js.tobytes())
+        if key not in refs:
+            refs[key] = (ndft.adjoint(x, f64, N, ksel=ks), ndft.forward(x, fh64, N, jsel=js))
+        ra, rb = refs[key]
+        out[label] = {"adjoint": ndft.rel_l2(ga, ra), "forward": ndft.rel_l2(gb, rb)}
+    return out
+
+
 def run_reference(args, wl, rank, world):
     """The reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
         return 0
     vals, desc, threads = [], "", 0
+    xs = None
+    if wl.get("seeds"):
+        xs, _ = _workload_inputs(wl, 0)
     for i in range(args.warmup + args.steps):
-        v, threads, desc = _oracle_sample(wl, seconds_target=6.0 if i >= args.warmup else 1.0)
+        v, threads, desc = _oracle_sample(wl, seconds_target=6.0 if i >= args.warmup else 1.0, xs=xs)
         if i >= args.warmup:
             vals.append(v)
     value = float(np.median(vals))
@@ -315,7 +390,57 @@ def run_reference(args, wl, rank, world):
     return 0
 
 
+def _time_plans(step, plans, stream, dev, steps, warmup, flush, world, profile):
+    """W warm-up steps, then K steps bracketed by a barrier and a device
+    synchronize, each between CUDA events on the plans' stream (L2 flushed
+    between steps, outside the events).  With `profile` the plans record
+    per-stage events during the timed steps.  Returns (ms per step, clocks,
+    kernels launched, per-stage (ms, launches))."""
+    import torch
+    import torch.distributed as dist
+    from paper_2001_01583_gb300 import _lib
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    for p in plans:
+        p.sync()
+        p.set_option(_lib.OPT_PROFILE, 1 if profile else 0)
+        p.stage_times(reset=True)
+    sampler = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = sum(p.info()["kernel_launches"] for p in plans)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.nvtx.range_push("bench_timed")   # lets a profiler select the timed steps' kernels
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))          # evict L2 between timed steps, outside the step's events
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = sum(p.info()["kernel_launches"] for p in plans) - launches0
+    stages = {}
+    for p in plans:
+        p.sync()
+        for k, (ms, n) in p.stage_times(reset=True).items():
+            acc = stages.setdefault(k, [0.0, 0])
+            acc[0] += ms
+            acc[1] += n
+        p.set_option(_lib.OPT_PROFILE, 0)
+    return float(np.sum([a.elapsed_time(b) for a, b in ev])) / steps, clocks, launches, stages
+
+
 def run_ours(args, wl, rank, world):
+    """The plan workloads (3-D configuration, the largest configuration with
+    picked parameters, and the small and sparse profiling cases): every step
+    runs set_points, the adjoint and the forward NFFT on each point set."""
     import torch
     import torch.distributed as dist
 
@@ -329,13 +454,31 @@ def run_ours(args, wl, rank, world):
     stream = torch.cuda.Stream(dev)
 
     # inputs: every rank its own seeds (independent problems)
-    gens = {"uniform": lambda s: inputs.uniform_points(M, 3, seed=s),
-            "clustered": lambda s: inputs.clustered_points(M, 3, 32, 0.02, seed=s)}
-    xs_host = [gens[name](100 * rank + i) for i, name in enumerate(wl["sets"])]
+    xs_host, sd = _workload_inputs(wl, rank)
     ctype = np.complex64 if args.precision == "fp32" else np.complex128
     tctype = torch.complex64 if args.precision == "fp32" else torch.complex128
-    f_host = inputs.complex_normal(M, seed=100 * rank + 7, dtype=ctype)
-    fh_host = inputs.complex_normal(N, seed=100 * rank + 8, dtype=ctype)
+    f_host = inputs.complex_normal(M, seed=100 * rank + sd["f"], dtype=ctype)
+    fh_host = inputs.complex_normal(N, seed=100 * rank + sd["fh"], dtype=ctype)
+
+    # window parameters: the learned picker's for the largest configuration,
+    # the stated ones otherwise; the rule of thumb for the plain FP64 form
+    params = (SIGMA, MCUT, WINDOW)
+    extra = {}
+    if wl.get("picked"):
+        from paper_2001_01583_gb300 import picker
+        pk = picker.load_default(stream=stream)
+        s_, m_, w_, fb = pk.pick(N, M, 0.01, wl["eps"], precision=args.precision)
+        rs, rm, rw = picker.rule_of_thumb(wl["eps"])
+        wname = lambda w: "gaussian" if w == 0 else "kaiser_bessel"   # noqa: E731
+        params = (s_, m_, wname(w_))
+        rule = (rs, rm, wname(rw))
+        pk.mlp.close()
+        extra["picked"] = {"sigma": s_, "m": m_, "window": wname(w_), "fallback": fb}
+        extra["rule_of_thumb"] = {"sigma": rs, "m": rm, "window": wname(rw)}
+        extra["eps"] = wl["eps"]
+    else:
+        rule = params
+    sigma, mcut, window = params
 
     with torch.cuda.stream(stream):
         xs = [torch.from_numpy(x).to(dev) for x in xs_host]
@@ -344,13 +487,15 @@ def run_ours(args, wl, rank, world):
         outs_a = [torch.empty((1,) + N, dtype=tctype, device=dev) for _ in xs]
         outs_f = [torch.empty((1, M), dtype=tctype, device=dev) for _ in xs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
-    plans = [Plan(N, M, SIGMA, MCUT, WINDOW, args.precision, stream=stream) for _ in xs]
+    plans = [Plan(N, M, sigma, mcut, window, args.precision, stream=stream) for _ in xs]
     if args.autotune:
         # the library's autotuner, once per point set, outside the timed region
         with torch.cuda.stream(stream):
             for p, x in zip(plans, xs):
                 p.set_points(x)
                 p.autotune(reps=3)
+    info = plans[0].info()
+    taps = info["taps"]
 
     def step():
         for p, x, a, b in zip(plans, xs, outs_a, outs_f):
@@ -358,56 +503,20 @@ def run_ours(args, wl, rank, world):
             p.adjoint(f, out=a)
             p.forward(fh, out=b)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    for p in plans:
-        p.sync()
+    ms_per_step, clocks, launches_timed, stages = _time_plans(step, plans, stream, dev, args.steps, args.warmup,
+                                                              flush, world, profile=True)
 
-    sampler = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    launches0 = sum(p.info()["kernel_launches"] for p in plans)
-    sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.nvtx.range_push("bench_timed")   # lets a profiler select the timed steps' kernels
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.fill_(float(i))          # evict L2 between timed steps, outside the step's events
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize(dev)
-    launches_timed = sum(p.info()["kernel_launches"] for p in plans) - launches0
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms_per_step = float(np.sum([a.elapsed_time(b) for a, b in ev])) / args.steps
-    # stage breakdown from separate steps with per-stage events (the timed
-    # steps above run without them)
-    for p in plans:
-        p.set_option(_lib.OPT_PROFILE, 1)
-        p.stage_times(reset=True)
-    with torch.cuda.stream(stream):
-        for i in range(max(3, args.steps // 2)):
-            flush.fill_(float(i))
-            step()
-    for p in plans:
-        p.sync()
-    stages, per_set = {}, {}
-    for name, p in zip(wl["sets"], plans):
-        per_set[name] = {}
-        for k, (ms, n) in p.stage_times(reset=True).items():
-            acc = stages.setdefault(k, [0.0, 0])
-            acc[0] += ms
-            acc[1] += n
-            if n:
-                per_set[name][k] = round(ms / n, 5)
-    for p in plans:
-        p.sync()
-        p.set_option(_lib.OPT_PROFILE, 0)
+    # sampled outputs of the timed steps, for the relative l2 error against
+    # the direct NDFT (computed in the oracle leg below)
+    rng = np.random.default_rng(12345)
+    nk, nj = (128, 128) if M >= 10 ** 7 else (64, 64)
+    ks = np.stack([rng.integers(-n // 2, n // 2, size=nk) for n in N], axis=1)
+    js = rng.integers(0, M, size=nj)
+    kidx = tuple(torch.from_numpy(ks[:, t] + N[t] // 2).to(dev) for t in range(len(N)))
+    jidx = torch.from_numpy(js).to(dev)
+    samples = {}
+    for name, a, b in zip(wl["sets"], outs_a, outs_f):
+        samples[name] = (ks, a[0][kidx].cpu().numpy(), js, b[0][jidx].cpu().numpy())
 
     # end to end through the public API with host buffers (pinned): inputs
     # copied in and results copied out inside the timed region, every step
@@ -418,7 +527,8 @@ def run_ours(args, wl, rank, world):
     # (the synchronize after each step waits for them)
     oa_pin = [torch.empty((1,) + N, dtype=tctype).pin_memory() for _ in xs]
     of_pin = [torch.empty((1, M), dtype=tctype).pin_memory() for _ in xs]
-    h2d = sum(x.numel() * 8 for x in xs_pin) + f_pin.numel() * 8 + fh_pin.numel() * 8
+    h2d = sum(x.numel() * 8 for x in xs_pin) + f_pin.numel() * f_pin.element_size() + \
+        fh_pin.numel() * fh_pin.element_size()
     d2h = sum(t.numel() * t.element_size() for t in oa_pin + of_pin)
 
     def e2e_step():
@@ -429,6 +539,8 @@ def run_ours(args, wl, rank, world):
 
     with torch.cuda.stream(stream):
         e2e_step()
+    for p in plans:
+        p.sync()
     torch.cuda.synchronize(dev)
     e_ms = []
     for i in range(max(3, min(args.steps, 5))):
@@ -437,47 +549,119 @@ def run_ours(args, wl, rank, world):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             e2e_step()
+        for p in plans:
+            p.sync()
         torch.cuda.synchronize(dev)
         e_ms.append((time.perf_counter() - t0) * 1e3)
+    del xs_pin, oa_pin, of_pin
+    for p in plans:
+        p.close()
+    del outs_a, outs_f
+
+    # the other forms of the same workload on the same GPU, timed the same
+    # way: the rule-of-thumb parameters in the same precision (when the
+    # picker chose others) and the plain FP64 form (rule-of-thumb parameters)
+    forms = {}
+    form_list = []
+    if wl.get("picked") and rule != params:
+        form_list.append(("rule_of_thumb_" + args.precision, rule, args.precision))
+    if args.precision == "fp32" and not args.no_fp64_form:
+        form_list.append(("plain_fp64", rule, "fp64"))
+    for label, (fs_, fm_, fw_), prec in form_list:
+        cdt = torch.complex64 if prec == "fp32" else torch.complex128
+        with torch.cuda.stream(stream):
+            fo = f.to(cdt)
+            fho = fh.to(cdt)
+            oa = [torch.empty((1,) + N, dtype=cdt, device=dev) for _ in xs]
+            ob = [torch.empty((1, M), dtype=cdt, device=dev) for _ in xs]
+        fplans = [Plan(N, M, fs_, fm_, fw_, prec, stream=stream) for _ in xs]
+        if args.autotune:
+            with torch.cuda.stream(stream):
+                for p, x in zip(fplans, xs):
+                    p.set_points(x)
+                    p.autotune(reps=2 if prec == "fp64" else 3)
+
+        def fstep(fplans=fplans, fo=fo, fho=fho, oa=oa, ob=ob):
+            for p, x, a, b in zip(fplans, xs, oa, ob):
+                p.set_points(x)
+                p.adjoint(fo, out=a)
+                p.forward(fho, out=b)
+        fms, _, _, _ = _time_plans(fstep, fplans, stream, dev, max(3, args.steps // 4), 3, flush, world,
+                                   profile=False)
+        for name, a, b in zip(wl["sets"], oa, ob):
+            samples[label + ":" + name] = (ks, a[0][kidx].cpu().numpy(), js, b[0][jidx].cpu().numpy())
+        forms[label] = {"sigma": fs_, "m": fm_, "window": fw_, "precision": prec, "ms_per_step": fms,
+                        "value": len(xs) * 2 * M * world / (fms * 1e-3)}
+        for p in fplans:
+            p.close()
+        del fo, fho, oa, ob
+        torch.cuda.empty_cache()
 
     points_per_step = len(xs) * 2 * M
-    t = torch.tensor([ms_per_step, float(np.median(e_ms))], dtype=torch.float64, device=dev)
+    t = torch.tensor([ms_per_step, float(np.median(e_ms))] + [v["ms_per_step"] for v in forms.values()],
+                     dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = t.tolist()
+    tl = t.tolist()
+    ms_max, e2e_max = tl[0], tl[1]
+    for k, v in zip(forms, tl[2:]):
+        forms[k]["ms_per_step"] = v
+        forms[k]["value"] = points_per_step * world / (v * 1e-3)
     value = points_per_step * world / (ms_max * 1e-3)
     e2e_value = points_per_step * world / (e2e_max * 1e-3)
 
     peaks, kind = _peaks()
     props = torch.cuda.get_device_properties(dev)
-    roofline = _roofline(stages, wl, peaks, kind, props.multi_processor_count)
-    hbm_step = _step_hbm_bytes(wl)
+    real = 4 if args.precision == "fp32" else 8
+    roofline = _roofline(stages, args.workload, (N, M, sigma, taps, real), peaks, kind,
+                         props.multi_processor_count)
+    hbm_step = len(xs) * _transform_bytes(N, M, sigma, 1, real)
     roofline["step_hbm_bytes"] = hbm_step
     roofline["step_hbm_frac"] = hbm_step / (ms_max * 1e-3) / 1e9 / peaks["hbm_gbs"]
-    # every stage's algorithmic HBM bytes per launch over its mean launch time
-    roofline["stage_hbm_frac"] = {k: round(_stage_hbm_bytes(k, wl) / (v[0] / v[1] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
-                                  for k, v in stages.items() if v[1] > 0 and v[0] > 0}
-    roofline["stage_ms_per_set"] = per_set
 
-    cpu = None
+    # the CPU oracle leg (rank 0, one GPU): the timed baseline on a bounded
+    # sample, then the relative l2 error of the sampled timed outputs
+    cpu, rel = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, threads, desc = _oracle_sample(wl)
+        v, threads, desc = _oracle_sample(wl, xs=xs_host, f=f_host, fh=fh_host)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        errs = {}
+        for i, name in enumerate(wl["sets"]):
+            sub = {k: v_ for k, v_ in samples.items() if k == name or k.endswith(":" + name)}
+            errs.update(_oracle_check(xs_host[i], f_host, fh_host, N, sub))
+        rel = {"value": max(max(e.values()) for k, e in errs.items() if ":" not in k),
+               "target": wl.get("eps", 1e-6),
+               "per_output": {k: e for k, e in errs.items() if ":" not in k},
+               "sample": "direct NDFT (the oracle, FP64) at %d frequencies of I_N (adjoint) and %d points "
+                         "(forward), drawn uniformly with seed 12345, per point set, from the last timed step's "
+                         "outputs" % (nk, nj)}
+        for k, e in errs.items():
+            if ":" in k:
+                label, _ = k.split(":", 1)
+                forms[label].setdefault("rel_l2", {})[k.split(":", 1)[1]] = e
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "rel_l2": rel["value"] if rel else None,
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points_per_step,
-                       "precision": args.precision, "autotuned": bool(args.autotune),
-                       "l2": "flushed between timed steps (512 MB write outside the step events)",
+                       "precision": args.precision, "sigma": sigma, "m": mcut, "window": window, "taps": taps,
+                       "autotuned": bool(args.autotune),
+                       "autotuned_layout": {k: info[k] for k in ("bin", "max_subproblem", "spread_block_threads",
+                                                                 "interp_block_threads", "sparse_points",
+                                                                 "sparse_points_interp")},
+                       "l2": "flushed between timed steps (512 MB write outside the step events); inputs and "
+                             "grid larger than L2",
+                       "stage_events": "per-stage CUDA events on the plans' stream during the timed steps",
                        "parallelism": "independent replicas x%d" % world},
+            "rel_l2_detail": rel,
+            "other_forms": forms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_timed,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+    line["config"].update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for p in plans:
-        p.close()
     return 0
 
 
@@ -583,8 +767,7 @@ def _timed(step, stream, dev, steps, warmup, flush, plans=()):
 
 
 def run_extra(args, wl, rank, world):
-    """The other configurations: 1-D FP64, the fluorite Ewald energy, and
-    the large clustered problem with picked window parameters."""
+    """The other configurations: 1-D FP64 and the fluorite Ewald energy."""
     import torch
     import torch.distributed as dist
 
@@ -630,36 +813,6 @@ def run_extra(args, wl, rank, world):
             out["e"] = plan.ewald_reciprocal(qd, L, 0.6)
         points_per_step = len(q)
         plans = [plan]
-    else:   # picker
-        from paper_2001_01583_gb300 import picker
-        eps, std = 1e-5, 0.01
-        pk = picker.load_default(stream=stream)
-        s_, m_, w_, fb = pk.pick(N, M, std, eps)
-        rs, rm, rw = picker.rule_of_thumb(eps)
-        x = torch.from_numpy(inputs.clustered_points(M, 3, 64, std, seed=100 * rank)).to(dev)
-        f = torch.from_numpy(inputs.complex_normal(M, seed=100 * rank + 1, dtype=np.complex64)).to(dev)
-        fh = torch.from_numpy(inputs.complex_normal(N, seed=100 * rank + 2, dtype=np.complex64)).to(dev)
-        oa = torch.empty((1,) + N, dtype=torch.complex64, device=dev)
-        of = torch.empty((1, M), dtype=torch.complex64, device=dev)
-        plans = [Plan(N, M, s_, m_, w_, "fp32", stream=stream), Plan(N, M, rs, rm, rw, "fp32", stream=stream)]
-        if args.autotune:
-            with torch.cuda.stream(stream):
-                for p in plans:
-                    p.set_points(x)
-                    p.autotune(reps=3)
-
-        def make(p):
-            def st():
-                p.set_points(x)
-                p.adjoint(f, out=oa)
-                p.forward(fh, out=of)
-            return st
-        ms_rule, _, _ = _timed(make(plans[1]), stream, dev, max(2, args.steps // 2), args.warmup, flush)
-        step = make(plans[0])
-        points_per_step = 2 * M
-        extra = {"picked": {"sigma": s_, "m": m_, "window": "gaussian" if w_ == 0 else "kaiser_bessel",
-                            "fallback": fb}, "rule_of_thumb": {"sigma": rs, "m": rm, "window": "kaiser_bessel"},
-                 "rule_ms_per_step": ms_rule, "eps": eps}
     ms, clocks, launches = _timed(step, stream, dev, args.steps, args.warmup, flush, plans=plans[:1])
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -685,7 +838,7 @@ def run_extra(args, wl, rank, world):
                  "real_space": {"energy": ur, "rcut": 10.0, "ms": float(np.median(rs_ms))},
                  "madelung": madelung}
     cfg = {"workload": wl["name"], "points_per_step_per_gpu": points_per_step, "precision": prec,
-           "autotuned": bool(args.autotune) and args.workload in ("fluorite", "picker"),
+           "autotuned": bool(args.autotune) and args.workload == "fluorite",
            "l2": "flushed between timed steps (512 MB write outside the step events)",
            "parallelism": "independent replicas x%d" % world}
     cfg.update(extra)
@@ -696,8 +849,6 @@ def run_extra(args, wl, rank, world):
     real = 4 if prec == "fp32" else 8
     if args.workload == "fluorite":
         hbm = _transform_bytes(N, points_per_step, SIGMA, 1, real, forward=False, ewald=True)
-    elif args.workload == "picker":
-        hbm = _transform_bytes(N, M, s_, 1, real)
     else:
         hbm = _transform_bytes(N, M, SIGMA, 1, real)
     line["roofline"] = _step_roofline(hbm, ms, "set_points and the transforms of one step; per-kernel roofline "
@@ -821,7 +972,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip timing the plain FP64 form of the plan workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

@@ -155,6 +155,9 @@ typedef struct {
   int owner_spread;          /* 1: sparse bins are spread by the owner kernel */
   int64_t kernel_launches;   /* this library's kernels launched by the plan so far
                                 (cuFFT's own kernels and memsets not included) */
+  int spread_block_threads;  /* threads per block of the last launch of the tiled spreading
+                                kernel (3-D plane kernels: 32 x warps; 0 = none yet) */
+  int interp_block_threads;  /* the same for interpolation */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling
@@ -221,7 +224,10 @@ int nfft_ewald_reciprocal_sum(nfft_plan* plan, const void* S_dev, double L, doub
  * device array of the library, held on every GPU that loads it until the
  * process exits.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress, with the device current); make that first
- * call outside any stream capture.  All calls share the array: calls whose
+ * call outside any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys and
+ * recreates the device's primary context) the array may move and this entry
+ * point must not be called again in that process.  All calls share the array: calls whose
  * work overlaps on the GPU (different streams, different host threads) race
  * and must be serialised by the caller.  Returns NFFT_ERR_UNSUPPORTED without
  * touching the GPU when |I_N| > NFFT_NOALLOC_MAX_MODES, NFFT_ERR_INVALID_ARG
@@ -307,7 +313,10 @@ typedef struct {
 } nfft_batch_item;
 
 /* Create a batch of `count` items (allocates everything, including one grid
- * per right-hand side of every item and the cuFFT plans). */
+ * per right-hand side of every item and the cuFFT plans).  Returns
+ * NFFT_ERR_UNSUPPORTED, before any device work, when the items' M add up to
+ * more than INT32_MAX (the bin sort indexes all points of a batch with 32-bit
+ * integers). */
 int nfft_batch_create(nfft_batch** out, int count, const nfft_batch_item* items, int precision, void* cuda_stream);
 
 int nfft_batch_destroy(nfft_batch* batch);

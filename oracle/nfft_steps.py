@@ -32,11 +32,16 @@ summation sum_{l in I_n} phi~(x - l/n) exp(-2 pi i k l / n)
 = n sum_r phihat(k + r n) exp(-2 pi i (k + r n) x), whose r = 0 term is
 n phihat(k) exp(-2 pi i k x).
 
-Truncation: a point with u = n (x_t - floor(x_t)), c = floor(u) reaches the
-2m + 2 cells l = c - m, ..., c + m + 1 of each dimension, taken modulo n (the
-grid is periodic, Eq. 5 being 1-periodic in x, so reducing x modulo 1 changes
-nothing).  The grid array index of cell l is l mod n, so the FFT in step 2 is
-numpy's unshifted DFT.
+Truncation: every coordinate is first brought into the paper's torus
+Pi = [-1/2, 1/2) of Section 1 as x_t - floor(x_t + 1/2); Eq. 5 is 1-periodic
+in x because k is an integer vector, so this changes no exact sum.  A point
+with u = n x_t, c = floor(u) then reaches the 2m + 2 cells l = c - m, ...,
+c + m + 1 of each dimension, taken modulo n (the oversampled grid is
+periodic).  The grid array index of cell l is l mod n, so the FFT in step 2 is
+numpy's unshifted DFT.  Where u is an integer up to rounding (a point on a
+cell boundary), another reduction of x may put it in the neighbouring cell
+with offset 1 instead of 0: the same position, a tap set shifted by one cell,
+and a result that differs by the window's truncation error at most.
 """
 import math
 
@@ -157,7 +162,7 @@ def _taps(x, n, m, window, N):
     idx, wts = [], []
     off = np.arange(-m, m + 2)
     for t in range(d):
-        xt = x[:, t] - np.floor(x[:, t])            # x mod 1 in [0, 1] (Eq. 5 is 1-periodic)
+        xt = x[:, t] - np.floor(x[:, t] + 0.5)      # into Pi = [-1/2, 1/2) (Section 1)
         u = n[t] * xt                               # cell coordinate; cell l sits at index l mod n
         c = np.floor(u)
         l = c[:, None] + off[None, :]                # cells c - m .. c + m + 1

@@ -63,6 +63,8 @@ class PlanInfo(ctypes.Structure):
         ("sparse_points_interp", ctypes.c_int),
         ("owner_spread", ctypes.c_int),
         ("kernel_launches", ctypes.c_int64),
+        ("spread_block_threads", ctypes.c_int),
+        ("interp_block_threads", ctypes.c_int),
     ]
 
 

@@ -32,6 +32,9 @@ int nfft_batch_create(nfft_batch** out, int count, const nfft_batch_item* items,
     const int st = validate_spec(s, precision);
     if (st != NFFT_OK) return st;
   }
+  // the sort indexes every point of the batch with 32-bit integers (bin
+  // starts, ranks, scatter positions): checked before any device work
+  if (total_points_exceed_int32(specs)) return NFFT_ERR_UNSUPPORTED;
   nfft_batch* p = new (std::nothrow) nfft_batch();
   if (!p) return NFFT_ERR_OOM;
   const int st = p->eng.init(specs, precision, static_cast<cudaStream_t>(cuda_stream), false);

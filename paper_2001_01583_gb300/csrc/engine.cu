@@ -259,9 +259,19 @@ Engine::~Engine() {
   }
 }
 
+bool total_points_exceed_int32(const std::vector<ItemSpec>& specs) {
+  int64_t total = 0;
+  for (const auto& s : specs) {
+    total += s.M;
+    if (total > (int64_t)INT32_MAX) return true;
+  }
+  return false;
+}
+
 int Engine::init(const std::vector<ItemSpec>& in_specs, int prec, cudaStream_t st, bool is_single) {
   if (in_specs.empty()) return NFFT_ERR_INVALID_ARG;
   for (const auto& s : in_specs) TRY(validate_spec(s, prec));
+  if (total_points_exceed_int32(in_specs)) return NFFT_ERR_UNSUPPORTED;
   specs = in_specs;
   precision = prec;
   csize = prec == NFFT_FP64 ? 16 : 8;
@@ -606,6 +616,7 @@ int Engine::build_layout() {
     kc.max_subs += nb_total + s.M / max_sub + 1;
   }
   total_points = pts_off[nitems];
+  if (total_points > (int64_t)INT32_MAX) return NFFT_ERR_UNSUPPORTED;   // 32-bit sort indices
   // an FFT class needs no clearing before spreading when the owner kernel
   // writes every grid in it
   for (auto& fc : fclasses) fc.owner_written = true;
@@ -903,6 +914,7 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
   CK(cudaFuncSetAttribute(best_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
   CK(cudaLaunchKernel(best_fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
   ++kernel_launches;
+  (spread ? last_spread_threads : last_interp_threads) = 32 * best_nw;
   return NFFT_OK;
 }
 
@@ -947,6 +959,7 @@ int Engine::run_wpp(const KClass& kc, PointKernelArgs<Real>& a, bool spread, int
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
   ++kernel_launches;
+  (spread ? last_spread_threads : last_interp_threads) = 32 * best_nw;
   return NFFT_OK;
 }
 
@@ -978,6 +991,7 @@ int Engine::run_tiled(const KClass& kc, PointKernelArgs<Real>& a, bool spread, i
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, stream));
   ++kernel_launches;
+  (spread ? last_spread_threads : last_interp_threads) = threads;
   return NFFT_OK;
 }
 
@@ -1428,6 +1442,8 @@ int Engine::info(nfft_plan_info* out) const {
   out->owner_spread = kclasses.empty() ? 0 : (kclasses[0].owner ? 1 : 0);
   out->kernel_launches = kernel_launches;
   out->interp_threads = interp_threads_opt;
+  out->spread_block_threads = last_spread_threads;
+  out->interp_block_threads = last_interp_threads;
   return NFFT_OK;
 }
 

@@ -63,6 +63,9 @@ struct EventPair {
 int64_t oversampled_size(int64_t N, double sigma);
 int window_taps(int window, int m);
 int validate_spec(const ItemSpec& s, int precision);
+// true when the items' point counts add up to more than INT32_MAX (the sort's
+// bin starts, ranks and scatter positions are 32-bit)
+bool total_points_exceed_int32(const std::vector<ItemSpec>& specs);
 double shape_param(int window, int m, double sigma);
 // centred cardinal B-spline M_order(u) (support |u| < order / 2), host FP64
 double cardinal_bspline(int order, double u);
@@ -144,6 +147,9 @@ class Engine {
   int threads_opt = 0;
   int spread_threads_opt = 0;
   int interp_threads_opt = 0;
+  // block threads of the last tiled spreading / interpolation launch (reported by get_info)
+  int last_spread_threads = 0;
+  int last_interp_threads = 0;
   int rhs_cap = 1;
   const double* last_x = nullptr;      // single item: the points of the last set_points
   std::vector<const double*> batch_x;  // batch: the points of the last set_points (user order)

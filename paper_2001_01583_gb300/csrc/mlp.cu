@@ -320,12 +320,15 @@ int nfft_mlp_num_params(const nfft_mlp* p, int64_t* n) {
 int nfft_mlp_set_params(nfft_mlp* p, const float* host) {
   if (!p || !host) return NFFT_ERR_INVALID_ARG;
   const size_t np = (size_t)p->d.n_params;
-  CK(cudaMemcpy(p->master, host, np * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemset(p->adam_m, 0, np * 4));
-  CK(cudaMemset(p->adam_v, 0, np * 4));
-  k_to_half<<<(unsigned)((np + 255) / 256), 256>>>((int)np, p->master, p->w16);
+  // kernels of earlier calls on the network's stream may still read or
+  // update these buffers: wait for them before overwriting
+  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaMemcpyAsync(p->master, host, np * 4, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemsetAsync(p->adam_m, 0, np * 4, p->stream));
+  CK(cudaMemsetAsync(p->adam_v, 0, np * 4, p->stream));
+  k_to_half<<<(unsigned)((np + 255) / 256), 256, 0, p->stream>>>((int)np, p->master, p->w16);
   CK(cudaGetLastError());
-  CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(p->stream));
   p->step = 0;
   return NFFT_OK;
 }
@@ -340,8 +343,9 @@ int nfft_mlp_get_params(nfft_mlp* p, float* host, int fp16_copy) {
   }
   float* tmp = nullptr;
   CK(cudaMalloc(&tmp, np * 4));
-  k_from_half<<<(unsigned)((np + 255) / 256), 256>>>((int)np, p->w16, tmp);
-  cudaError_t e = cudaMemcpy(host, tmp, np * 4, cudaMemcpyDeviceToHost);
+  k_from_half<<<(unsigned)((np + 255) / 256), 256, 0, p->stream>>>((int)np, p->w16, tmp);
+  cudaError_t e = cudaMemcpyAsync(host, tmp, np * 4, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   cudaFree(tmp);
   CK(e);
   return NFFT_OK;

@@ -73,3 +73,22 @@ def test_plan_create_argument_errors_need_no_gpu(lib):
     assert lib.nfft_forward(None, None, None, 1) == _lib.ERR_INVALID_ARG
     assert lib.nfft_sync(None) == _lib.ERR_INVALID_ARG
     assert lib.nfft_plan_destroy(None) == _lib.OK
+
+
+def test_batch_total_points_beyond_int32_rejected_without_gpu(lib):
+    """Each item may hold up to INT32_MAX points, but the bin sort indexes a
+    whole batch with 32-bit integers: two items of 1.2e9 points are refused
+    before any device work (so this runs without a GPU)."""
+    items = (_lib.BatchItem * 2)()
+    for it in items:
+        it.d = 3
+        for t in range(3):
+            it.N[t] = 64
+        it.M = 1_200_000_000
+        it.sigma = 2.0
+        it.m = 4
+        it.window = _lib.KAISER_BESSEL
+        it.nrhs = 1
+    h = ctypes.c_void_p()
+    assert lib.nfft_batch_create(ctypes.byref(h), 2, items, _lib.FP32_MIXED, None) == _lib.ERR_UNSUPPORTED
+    assert not h.value

@@ -244,6 +244,33 @@ def test_plane_spread_uneven_warps(m, warps, precision):
         assert np.max(np.abs(a - sa) / amp) / np.sqrt(np.mean(np.abs(sa) ** 2)) <= FP32_ELEM
 
 
+# ---- every block size of the timed plane kernels -----------------------------
+# The bench's autotuner picks the threads per block of the spreading and the
+# interpolation kernel (32 x warps) among these; the 3-D configuration runs
+# 8 taps (Kaiser-Bessel m = 4), the largest one 6 (m = 3).  Each instantiation
+# is pinned element by element, uniform and clustered, and info() must report
+# the block size that ran.
+@pytest.mark.parametrize("m,threads", [(4, 32), (4, 64), (4, 128), (4, 256), (3, 32), (3, 64), (3, 128)])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_plane_kernels_at_every_block_size(m, threads, precision):
+    N, M = (40, 36, 32), 30000
+    x = np.concatenate([inputs.clustered_points(M // 2, 3, 8, 0.02, seed=121),
+                        inputs.uniform_points(M - M // 2, 3, seed=122)])
+    f = inputs.complex_normal(M, seed=123)
+    fh = inputs.complex_normal(N, seed=124)
+    a, b, info = _run(N, x, f, fh, 2.0, m, "kaiser_bessel", precision, method=3, spread_threads=threads,
+                      interp_threads=threads)
+    assert info["method"] == 3 and info["taps"] == 2 * m
+    assert info["spread_block_threads"] == threads and info["interp_block_threads"] == threads
+    sa = S.adjoint(x, f, N, 2.0, m, S.KAISER_BESSEL)
+    sb = S.forward(x, fh, N, 2.0, m, S.KAISER_BESSEL)
+    tol = 1e-12 if precision == "fp64" else FP32_ELEM
+    _elementwise(a, sa, tol)
+    _elementwise(b, sb, tol)
+    if precision == "fp32":
+        assert ndft.rel_l2(a, sa) <= FP32_L2 and ndft.rel_l2(b, sb) <= FP32_L2
+
+
 # ---- sparse subproblems on the grid-warp kernels, dense ones on tiles --------
 @pytest.mark.parametrize("N,M,window,m", [((40, 36, 32), 3000, "kaiser_bessel", 4), ((30, 28, 34), 2000, "gaussian", 6),
                                           ((96, 80), 3000, "kaiser_bessel", 5), ((2000,), 3000, "gaussian", 3),
@@ -436,32 +463,83 @@ def test_empty_point_set():
 
 
 def test_single_point_and_boundaries():
+    """Points on cell boundaries (n x_t an integer) and outside [-1/2, 1/2).
+    At such a tie the kernels may take the cell below with offset 1 where the
+    oracle takes offset 0: the same position, a tap set one cell lower.  The
+    bar that does not depend on that choice is the direct NDFT at the
+    window's error.  The Kaiser-Bessel window vanishes at |u| = m, so both
+    tap sets give the same sum to rounding (pinned in
+    test_oracle_nfft_steps.py), and the element-wise oracle bar holds too."""
     N = (16, 12, 10)
     pts = np.array([[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [0.49999999999, -0.25, 0.0], [3.75, -7.125, 12.5]])
     f = np.array([1.0 + 0.0j, 0.5 - 2j, -1j, 2.0])
     fh = inputs.complex_normal(N, seed=61)
     for precision, tol in (("fp64", 1e-12), ("fp32", FP32_ELEM)):
         a, b, _ = _run(N, pts, f, fh, 2.0, 5, "kaiser_bessel", precision)
-        _elementwise(a, S.adjoint(pts, f, N, 2.0, 5, S.KAISER_BESSEL), tol)
-        _elementwise(b, S.forward(pts, fh, N, 2.0, 5, S.KAISER_BESSEL), tol)
         # Kaiser-Bessel m = 5 is accurate to about 1e-9, so FP32 rounding sets the bar
         bar = 1e-8 if precision == "fp64" else FP32_L2
         assert ndft.rel_l2(a, ndft.adjoint(pts, f, N)) <= bar
+        assert ndft.rel_l2(b, ndft.forward(pts, fh, N)) <= bar
+        _elementwise(a, S.adjoint(pts, f, N, 2.0, 5, S.KAISER_BESSEL), tol)
+        _elementwise(b, S.forward(pts, fh, N, 2.0, 5, S.KAISER_BESSEL), tol)
         a1, _, _ = _run(N, pts[:1], f[:1], fh, 2.0, 5, "kaiser_bessel", precision)
         assert ndft.rel_l2(a1, ndft.adjoint(pts[:1], f[:1], N)) <= bar   # exp(-2 pi i k.x)
 
 
-def test_lattice_points_on_grid_nodes():
-    # fluorite lattice, 2 cells: n x_t lands exactly on cell boundaries
+@pytest.mark.parametrize("window,m", [("gaussian", 6), ("gaussian", 3)])
+def test_boundary_ties_gaussian_against_direct_ndft(window, m):
+    """The Gaussian does not vanish at the edge of its taps, so at a tie the
+    two tap sets differ by its truncation error: the bar is the direct NDFT at
+    twice the oracle NFFT's own error (the window error, tap-set independent
+    in size)."""
+    N = (16, 12, 10)
+    pts = np.array([[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [0.25, -0.25, 0.0], [3.75, -7.125, 12.5],
+                    [0.125, 0.375, -0.3]])
+    f = inputs.complex_normal(len(pts), seed=62)
+    fh = inputs.complex_normal(N, seed=63)
+    ea = ndft.rel_l2(S.adjoint(pts, f, N, 2.0, m, S.GAUSSIAN), ndft.adjoint(pts, f, N))
+    eb = ndft.rel_l2(S.forward(pts, fh, N, 2.0, m, S.GAUSSIAN), ndft.forward(pts, fh, N))
+    a, b, _ = _run(N, pts, f, fh, 2.0, m, window, "fp64")
+    assert ndft.rel_l2(a, ndft.adjoint(pts, f, N)) <= 2 * ea + 1e-14
+    assert ndft.rel_l2(b, ndft.forward(pts, fh, N)) <= 2 * eb + 1e-14
+
+
+@pytest.mark.parametrize("window,m,precision", [("kaiser_bessel", 6, "fp64"), ("kaiser_bessel", 6, "fp32"),
+                                                ("gaussian", 6, "fp64")])
+def test_lattice_points_on_grid_nodes(window, m, precision):
+    """Fluorite lattice, 2 cells: every n x_t is an even integer up to the
+    rounding of r / L, so every point is a tie.  Bars independent of the tap
+    set: the direct NDFT at the window error and, for the lattice's charges,
+    the closed form of the structure factor.  For Kaiser-Bessel (zero weight
+    at |u| = m) also element by element against the oracle."""
     r, q, L = inputs.fluorite(2)
     x = inputs.box_points(r, L)
     N = (16, 16, 16)
     f = q.astype(np.complex128)
     fh = inputs.complex_normal(N, seed=71)
-    a, b, _ = _run(N, x, f, fh, 2.0, 6, "kaiser_bessel", "fp64")
-    _elementwise(a, S.adjoint(x, f, N, 2.0, 6, S.KAISER_BESSEL), 1e-12)
-    _elementwise(b, S.forward(x, fh, N, 2.0, 6, S.KAISER_BESSEL), 1e-12)
-    assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 1e-9
+    a, b, _ = _run(N, x, f, fh, 2.0, m, window, precision)
+    ea = ndft.rel_l2(S.adjoint(x, f, N, 2.0, m, WIN[window]), ndft.adjoint(x, f, N))
+    eb = ndft.rel_l2(S.forward(x, fh, N, 2.0, m, WIN[window]), ndft.forward(x, fh, N))
+    slack = 1e-13 if precision == "fp64" else FP32_L2
+    assert ndft.rel_l2(a, ndft.adjoint(x, f, N)) <= 2 * ea + slack
+    assert ndft.rel_l2(b, ndft.forward(x, fh, N)) <= 2 * eb + slack
+    # the structure factor of lc^3 cells in closed form: with x = r / L - 1/2,
+    # sum_i q_i exp(-2 pi i k.x_i) = (-1)^(k0+k1+k2) lc^3 F(k / lc) for k in
+    # lc Z^3 (else 0), F(h) = sum over one cell's ions of q_b exp(-2 pi i h.b)
+    r1, q1, L1 = inputs.fluorite(1)
+    bfrac = r1 / L1
+    lc = 2
+    exact = np.zeros(N, dtype=np.complex128)
+    grids = np.meshgrid(*[np.arange(-n // 2, n // 2) for n in N], indexing="ij")
+    kk = np.stack(grids, -1).reshape(-1, 3)
+    on = np.all(kk % lc == 0, axis=1)
+    F = np.exp(-2j * np.pi * (kk[on] // lc) @ bfrac.T) @ q1
+    exact.reshape(-1)[on] = (-1.0) ** kk[on].sum(axis=1) * lc ** 3 * F
+    assert ndft.rel_l2(a, exact) <= 2 * ea + slack
+    if window == "kaiser_bessel":
+        tol = 1e-12 if precision == "fp64" else FP32_ELEM
+        _elementwise(a, S.adjoint(x, f, N, 2.0, m, S.KAISER_BESSEL), tol)
+        _elementwise(b, S.forward(x, fh, N, 2.0, m, S.KAISER_BESSEL), tol)
 
 
 def test_error_statuses():

@@ -114,6 +114,49 @@ def test_points_on_cell_boundaries_and_wrap():
     assert ndft.rel_l2(a, exact) < 1e-6
 
 
+def test_reduction_into_the_torus():
+    # the coordinate reduction lands in Pi = [-1/2, 1/2) (Section 1) and
+    # moves every coordinate by an integer
+    x = np.array([[-0.5, 0.5, 0.25], [3.75, -7.125, 12.5], [-0.2500001, 1e-17, -1e-17]])
+    n = [16, 16, 16]
+    idx, _ = S._taps(x, n, 3, S.KAISER_BESSEL, [8, 8, 8])
+    for t in range(3):
+        xt = x[:, t] - np.floor(x[:, t] + 0.5)
+        assert np.all((xt >= -0.5) & (xt < 0.5))
+        assert np.all(np.abs((x[:, t] - xt) - np.round(x[:, t] - xt)) == 0)
+        # the first tap is floor(n x) - m, modulo n
+        assert np.array_equal(idx[t][:, 0], np.mod(np.floor(n[t] * xt) - 3, n[t]))
+
+
+@pytest.mark.parametrize("window,m", [(S.KAISER_BESSEL, 4), (S.GAUSSIAN, 6), (S.B_SPLINE, 3), (S.SINC_POWER, 4)])
+def test_cell_choice_at_a_boundary_moves_the_result_by_truncation_only(window, m):
+    # a point exactly on a cell boundary can be taken as (cell c, offset 0) or
+    # (cell c - 1, offset 1): both tap sets place the window at the same
+    # position, so the two gridding results differ from each other no more
+    # than each differs from the exact sum (the window error)
+    N, n = (16,), [32]
+    x0 = np.array([[5.0 / 32]])                 # u = 5 exactly
+    f = np.array([0.7 - 0.2j])
+    a = S.adjoint(x0, f, N, 2.0, m, window)
+    # the same point taken as cell 4 at offset 1: every tap one cell lower,
+    # weights at the same distances u - l
+    idx, w = S._taps(x0, n, m, window, N)
+    lo_idx = np.mod(idx[0] - 1, n[0])
+    u = 5.0
+    lo_w = S.phi(window, u - (np.floor(u) - 1 + np.arange(-m, m + 2)), m, n[0], N[0])
+    g = np.zeros(n[0], dtype=np.complex128)
+    np.add.at(g, lo_idx[0], f[0] * lo_w)
+    ghat = np.fft.fft(g)[np.mod(np.arange(-8, 8), 32)]
+    b = ghat / S.scaling_weights(window, m, N, n)[0]
+    exact = ndft.adjoint(x0, f, N)
+    e_a = ndft.rel_l2(a, exact)
+    assert ndft.rel_l2(b, exact) <= 1.5 * max(e_a, 1e-15)
+    assert ndft.rel_l2(a, b) <= 2.5 * max(e_a, 1e-15)
+    if window in (S.KAISER_BESSEL, S.B_SPLINE, S.SINC_POWER):
+        # these windows vanish at |u| = m, so the extra tap of either set is 0
+        assert ndft.rel_l2(a, b) < 1e-14
+
+
 # ---- B-spline and sinc-power windows (Section 4, Fig. 12) ----------------------
 def test_cardinal_bspline_textbook_values():
     # the hat function and the cubic B-spline, and the general properties
