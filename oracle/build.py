@@ -3,11 +3,12 @@
 Plain gcc, no vendor flags, so the same source builds on x86-64 and aarch64.
 """
 import os
+import platform
 import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-BUILD_DIR = os.path.join(HERE, "_build")
+BUILD_DIR = os.path.join(HERE, "_build", platform.machine())   # one per host architecture
 LIB_PATH = os.path.join(BUILD_DIR, "libndft_oracle.so")
 SOURCES = [os.path.join(HERE, "ndft.c")]
 

@@ -7,6 +7,7 @@ newer than they are.
 import concurrent.futures
 import glob
 import os
+import platform
 import subprocess
 import sys
 
@@ -14,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())   # objects per host architecture
 LIB = os.path.join(HERE, "libgbnfft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
