@@ -19,6 +19,7 @@ m = 4, sigma = 2, on two point sets (uniform, and 32 Gaussian clusters of std
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload picker|config|small|sparse|batch|1d|fluorite|fig13|fig16]
                   [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline] [--no-fp64-form]
+                  [--tensor-spread]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  "--workload fig13" and "fig16" sweep the
@@ -488,6 +489,9 @@ def run_ours(args, wl, rank, world):
         outs_f = [torch.empty((1, M), dtype=tctype, device=dev) for _ in xs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
     plans = [Plan(N, M, sigma, mcut, window, args.precision, stream=stream) for _ in xs]
+    if args.tensor_spread:
+        for p in plans:
+            p.set_option(_lib.OPT_TENSOR_SPREAD, 1)
     if args.autotune:
         # the library's autotuner, once per point set, outside the timed region
         with torch.cuda.stream(stream):
@@ -646,7 +650,7 @@ def run_ours(args, wl, rank, world):
             "rel_l2": rel["value"] if rel else None,
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points_per_step,
                        "precision": args.precision, "sigma": sigma, "m": mcut, "window": window, "taps": taps,
-                       "autotuned": bool(args.autotune),
+                       "autotuned": bool(args.autotune), "tensor_spread": bool(info.get("tensor_spread")),
                        "autotuned_layout": {k: info[k] for k in ("bin", "max_subproblem", "spread_block_threads",
                                                                  "interp_block_threads", "sparse_points",
                                                                  "sparse_points_interp")},
@@ -973,6 +977,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--tensor-spread", action="store_true",
+                    help="plan workloads: spread the dense bins on the tensor cores (NFFT_OPT_TENSOR_SPREAD)")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip timing the plain FP64 form of the plan workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")

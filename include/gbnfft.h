@@ -110,13 +110,26 @@ typedef enum {
   NFFT_OPT_SPARSE_POINTS_INTERP = 11, /* the same for interpolation (0 = automatic:
                                    one point per W^d / 5 tile cells; gathers
                                    need no atomics, so the split sits higher) */
-  NFFT_OPT_OWNER_SPREAD = 12    /* d = 3: 1 spreads the sparse bins by their
+  NFFT_OPT_OWNER_SPREAD = 12,   /* d = 3: 1 spreads the sparse bins by their
                                    cells' owners (a warp per bin, no atomics,
                                    every cell written once) where the grid
                                    allows (n_t >= bin_t + W - 1); 0 (default)
                                    uses the grid-warp atomics, which measure
                                    faster (an owner pass repeats each point's
                                    weights for every owner it touches) */
+  NFFT_OPT_TENSOR_SPREAD = 13   /* d = 3, NFFT_FP32_MIXED, windows of 4, 6 or 8
+                                   taps, NFFT_METHOD_AUTO or _WARP: 1 spreads
+                                   the dense bins on the tensor cores (tcgen05
+                                   MMAs of TF32 operands split in two, so the
+                                   products keep FP32 accuracy; the tile is the
+                                   MMA accumulator in tensor memory).  Default
+                                   bins become (12 - W, 12 - W, 16), so that the
+                                   tile's (z, y) rows fit the MMA's 128; explicit
+                                   bins must satisfy (b0 + W - 1)(b1 + W - 1) <= 128
+                                   and 2 (b2 + W - 1) <= 112, else nfft_set_option
+                                   returns NFFT_ERR_UNSUPPORTED.  Interpolation
+                                   keeps the plane kernels.  0 (default): the
+                                   plane-owner shared-memory kernel */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -158,6 +171,7 @@ typedef struct {
   int spread_block_threads;  /* threads per block of the last launch of the tiled spreading
                                 kernel (3-D plane kernels: 32 x warps; 0 = none yet) */
   int interp_block_threads;  /* the same for interpolation */
+  int tensor_spread;         /* 1: dense bins are spread on the tensor cores (NFFT_OPT_TENSOR_SPREAD) */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling

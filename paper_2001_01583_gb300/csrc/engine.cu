@@ -353,6 +353,7 @@ int Engine::release_layout() {
   free_dev(bin_start);
   free_dev(sub_count);
   free_dev(sub_start);
+  free_dev(scan_partials);
   free_dev(num_subs);
   free_dev(subs);
   free_dev(bin_rank);
@@ -377,7 +378,7 @@ int Engine::build_layout() {
 
   struct Choice {
     int bin[3], tile[3], pitch, method, taps, sparse, sparse_interp;
-    bool owner;
+    bool owner, tensor;
   };
   std::vector<Choice> ch(nitems);
   for (int i = 0; i < nitems; ++i) {
@@ -431,6 +432,19 @@ int Engine::build_layout() {
         planes = true;
         for (int t = 0; t < 3; ++t) c.bin[t] = pb[t];
       }
+    }
+    // tensor-core spreading: the tile's (z, y) rows are the MMA's M = 128
+    // rows and its x columns (complex) its N <= 112 columns
+    c.tensor = false;
+    if (tensor_enabled && planes && precision == NFFT_FP32_MIXED && s.window != NFFT_B_SPLINE &&
+        (method_opt == NFFT_METHOD_AUTO || method_opt == NFFT_METHOD_WARP) && tc_spread_kernel_f32(c.taps)) {
+      if (!explicit_bins) {
+        const int want[3] = {12 - c.taps, 12 - c.taps, 16};
+        for (int t = 0; t < 3; ++t) c.bin[t] = (int)std::min<int64_t>(want[t], n[t]);
+      }
+      const int t0 = c.bin[0] + c.taps - 1, t1 = c.bin[1] + c.taps - 1, t2 = c.bin[2] + c.taps - 1;
+      if (t0 * t1 > kTcRowsHost || 2 * t2 > kTcMaxColsHost) return NFFT_ERR_UNSUPPORTED;
+      c.tensor = true;
     }
     if (!planes)
       while (tile_bytes(c.bin) > budget && !explicit_bins && halve_largest(c.bin)) {
@@ -603,6 +617,7 @@ int Engine::build_layout() {
       kc.sparse_points = c.sparse;
       kc.sparse_points_interp = c.sparse_interp;
       kc.owner = c.owner;
+      kc.tensor = c.tensor;
       kc.item_begin = k;
       kc.bin_begin = bin_off[k];
       kc.max_nrhs = 0;
@@ -634,6 +649,7 @@ int Engine::build_layout() {
   TRY(alloc_dev(bin_start, sizeof(int) * B, device_bytes));
   TRY(alloc_dev(sub_count, sizeof(int) * B, device_bytes));
   TRY(alloc_dev(sub_start, sizeof(int) * B, device_bytes));
+  TRY(alloc_dev(scan_partials, sizeof(int) * (size_t)scan_partials_needed((int)B), device_bytes));
   TRY(alloc_dev(num_subs, sizeof(int), device_bytes));
   TRY(alloc_dev(subs, sizeof(SubProblem) * (size_t)max_subs_total, device_bytes));
   TRY(alloc_dev(bin_rank, sizeof(int2) * P, device_bytes));
@@ -808,6 +824,7 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   const int max_nrhs = in ? nrhs : kc.max_nrhs;
   a.sub_min_count = 0;
   a.sub_max_count = INT_MAX;
+  a.err = err_flag;
   if (kc.method == NFFT_METHOD_GRID_WARP) return run_gm<Real>(kc, a, spread);
   if (kc.method == NFFT_METHOD_GLOBAL) return run_global<Real>(kc, a, spread);
   // tiled kernels take the bins of at least `split` points, the owner
@@ -821,9 +838,20 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
                                          : run_tiled<Real>(kc, a, spread, max_nrhs);
   }
   a.sub_min_count = split;
-  const int st = kc.method == NFFT_METHOD_WARP
-                     ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
-                     : run_tiled<Real>(kc, a, spread, max_nrhs);
+  int st;
+  if constexpr (sizeof(Real) == 4) {
+    if (spread && kc.tensor) {
+      st = run_tc(kc, a);
+    } else {
+      st = kc.method == NFFT_METHOD_WARP
+               ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
+               : run_tiled<Real>(kc, a, spread, max_nrhs);
+    }
+  } else {
+    st = kc.method == NFFT_METHOD_WARP
+             ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
+             : run_tiled<Real>(kc, a, spread, max_nrhs);
+  }
   if (st != NFFT_OK || split <= 0) return st;
   a.sub_min_count = 0;
   a.sub_max_count = split;
@@ -915,6 +943,33 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
   CK(cudaLaunchKernel(best_fn, dim3((unsigned)blocks), dim3(32 * best_nw), args, best_smem, stream));
   ++kernel_launches;
   (spread ? last_spread_threads : last_interp_threads) = 32 * best_nw;
+  return NFFT_OK;
+}
+
+// 3-D dense bins spread on the tensor cores: a block of kTcThreadsHost
+// threads per subproblem, the tile in tensor memory (points_tc.cuh).
+int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a) {
+  const void* fn = tc_spread_kernel_f32(kc.taps);
+  if (!fn) return NFFT_ERR_UNSUPPORTED;
+  TcLaunch lay{};
+  lay.ncols = (2 * kc.tile[2] + 15) / 16 * 16;
+  lay.tmem_cols = 32;
+  while (lay.tmem_cols < lay.ncols) lay.tmem_cols *= 2;
+  if (kc.tile[0] * kc.tile[1] > kTcRowsHost || lay.ncols > kTcMaxColsHost) return NFFT_ERR_UNSUPPORTED;
+  const size_t smem = tc_spread_smem_bytes(kc.taps, lay.ncols, kc.tile);
+  if (smem > smem_optin) return NFFT_ERR_UNSUPPORTED;
+  a.rhs_per_pass = 1;
+  int per_sm = std::max(1, blocks_per_sm(fn, kTcThreadsHost, smem));
+  // every resident block holds tmem_cols of the SM's 512 tensor-memory columns
+  per_sm = std::min(per_sm, 512 / lay.tmem_cols);
+  int64_t blocks = (int64_t)per_sm * num_sms;
+  if (blocks > kc.max_subs) blocks = kc.max_subs;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&a, &lay};
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kTcThreadsHost), args, smem, stream));
+  ++kernel_launches;
+  last_spread_threads = kTcThreadsHost;
   return NFFT_OK;
 }
 
@@ -1027,12 +1082,14 @@ int Engine::set_points_impl(const double* x_override) {
   TRY(stage_begin(NFFT_STAGE_SORT, &ev));
   CK(cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)std::max(total_bins, 1), stream));
   CK(launch_bin_count<Real>(s, bin_count, bin_rank, stream));
-  kernel_launches += s.total_points > 0 ? 6 : 4;   // bin count, 2 scans, scatter, subproblem count and fill
-  CK(launch_scan(bin_count, bin_start, total_bins, nullptr, stream));
+  // bin count, scatter, subproblem count and fill, two scans of three kernels (the first and
+  // last of a scan only when there are bins)
+  kernel_launches += (s.total_points > 0 ? 4 : 2) + (total_bins > 0 ? 6 : 2);
+  CK(launch_scan(bin_count, bin_start, total_bins, nullptr, scan_partials, stream));
   Real* d[3] = {static_cast<Real*>(delta[0]), static_cast<Real*>(delta[1]), static_cast<Real*>(delta[2])};
   CK(launch_scatter<Real>(s, bin_start, bin_rank, perm, local, d, stream));
   CK(launch_subproblem_count(bin_count, total_bins, max_sub, sub_count, stream));
-  CK(launch_scan(sub_count, sub_start, total_bins, num_subs, stream));
+  CK(launch_scan(sub_count, sub_start, total_bins, num_subs, scan_partials, stream));
   CK(launch_subproblem_fill(s, bin_count, bin_start, sub_start, max_sub, subs, stream));
   TRY(stage_end(&ev));
   return NFFT_OK;
@@ -1358,6 +1415,10 @@ int Engine::set_option(int option, int64_t value) {
       if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
       owner_enabled = value != 0;
       break;
+    case NFFT_OPT_TENSOR_SPREAD:
+      if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
+      tensor_enabled = value != 0;
+      break;
     case NFFT_OPT_SPARSE_POINTS:
     case NFFT_OPT_SPARSE_POINTS_INTERP:
       if (value < -1 || value > (1 << 20)) return NFFT_ERR_INVALID_ARG;
@@ -1442,6 +1503,7 @@ int Engine::info(nfft_plan_info* out) const {
   out->owner_spread = kclasses.empty() ? 0 : (kclasses[0].owner ? 1 : 0);
   out->kernel_launches = kernel_launches;
   out->interp_threads = interp_threads_opt;
+  out->tensor_spread = kclasses.empty() ? 0 : (kclasses[0].tensor ? 1 : 0);
   out->spread_block_threads = last_spread_threads;
   out->interp_block_threads = last_interp_threads;
   return NFFT_OK;
@@ -1544,7 +1606,14 @@ int Engine::autotune(int reps, double* best_ms) {
   };
   std::vector<Cand> cands;
   const int Ps[2] = {1024, 256};
-  if (dmax == 3) {
+  if (dmax == 3 && tensor_enabled && precision == NFFT_FP32_MIXED) {
+    // tensor-core spreading: (z, y) rows of the tile within the MMA's 128,
+    // x columns along the N dimension
+    const int b = std::max(1, 12 - taps_for(specs[0].window, specs[0].m));
+    const int bins[][3] = {{b, b, 16}, {b, b, 32}, {b, b, 8}, {b, b, 24}};
+    for (const auto& bb : bins)
+      for (int P : Ps) cands.push_back(Cand{{bb[0], bb[1], bb[2]}, P});
+  } else if (dmax == 3) {
     const int bins[][3] = {{8, 8, 16}, {8, 8, 8}, {4, 8, 16}, {8, 16, 16}, {8, 8, 32}, {4, 4, 32}};
     for (const auto& b : bins)
       for (int P : Ps) cands.push_back(Cand{{b[0], b[1], b[2]}, P});

@@ -42,6 +42,7 @@ struct KClass {
   int sparse_points;          // spreading subproblems below this many points: grid-warp kernel (0: none)
   int sparse_points_interp;   // the same for interpolation
   bool owner;                 // spreading of sparse bins by the owner kernel (3-D)
+  bool tensor;                // dense bins spread on the tensor cores (3-D, FP32)
 };
 
 struct FClass {
@@ -115,6 +116,7 @@ class Engine {
   template <typename Real> int run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
   template <typename Real> int run_owner(const KClass& kc, PointKernelArgs<Real>& a);
   template <typename Real> int run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
+  int run_tc(const KClass& kc, PointKernelArgs<float>& a);
   template <typename Real> int adjoint_table(bool in_graph);
   template <typename Real> int forward_table(bool in_graph);
   template <typename Real> int ewald_impl(const void* q, double L, double alpha);
@@ -140,6 +142,7 @@ class Engine {
   int max_sub_opt = 0;
   int sparse_opt = 0;          // NFFT_OPT_SPARSE_POINTS
   bool owner_enabled = false;  // NFFT_OPT_OWNER_SPREAD
+  bool tensor_enabled = false; // NFFT_OPT_TENSOR_SPREAD
   int64_t kernel_launches = 0;   // this library's kernels launched so far (graph replays included)
   int64_t graph_launches[2] = {0, 0};
   int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP
@@ -179,6 +182,7 @@ class Engine {
   int* bin_count = nullptr;
   int* bin_start = nullptr;
   int* sub_count = nullptr;
+  int* scan_partials = nullptr;   // scratch of the multi-block scans
   int* sub_start = nullptr;
   int* num_subs = nullptr;
   SubProblem* subs = nullptr;

@@ -180,7 +180,7 @@ extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const doubl
   size_t bytes = sizeof(double) * (size_t)(blocks + 1);
   if (nc > 1) {
     bytes += sizeof(int) * (size_t)(2 * cells + 2) + sizeof(int2) * (size_t)n + sizeof(float4) * (size_t)n +
-             sizeof(int) * (size_t)n + 64;
+             sizeof(int) * (size_t)n + sizeof(int) * (size_t)scan_partials_needed(cells + 1) + 64;
   }
   char* buf = nullptr;
   if (cudaMalloc(&buf, bytes) != cudaSuccess) {
@@ -200,10 +200,11 @@ extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const doubl
     int2* cell_rank = reinterpret_cast<int2*>(rec_cell + n + (n & 1));
     int* count = reinterpret_cast<int*>(cell_rank + n);
     int* start = count + cells + 1;
+    int* scan_scratch = start + cells + 1;
     ck(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cells + 1), st));
     k_rs_count<<<blocks, kRsThreads, 0, st>>>(n, r_dev, L, nc, count, cell_rank);
     ck(cudaGetLastError());
-    ck(launch_scan(count, start, cells + 1, nullptr, st));   // start[cells] = n
+    ck(launch_scan(count, start, cells + 1, nullptr, scan_scratch, st));   // start[cells] = n
     k_rs_scatter<<<blocks, kRsThreads, 0, st>>>(n, r_dev, q_dev, L, nc, start, cell_rank, rec, rec_cell);
     ck(cudaGetLastError());
     const double h = L / nc;

@@ -27,8 +27,10 @@ struct SortArgs {
 // Cell and global bin of every point, and its rank inside its bin.
 template <typename Real>
 cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st);
-// Exclusive prefix sum of n ints; *total = sum (may be null).
-cudaError_t launch_scan(const int* in, int* out, int n, int* total, cudaStream_t st);
+// Exclusive prefix sum of n ints; *total = sum (may be null).  partials:
+// scan_partials_needed(n) ints of device scratch.  Three launches.
+int scan_partials_needed(int n);
+cudaError_t launch_scan(const int* in, int* out, int n, int* total, int* partials, cudaStream_t st);
 // Write every point to its sorted slot: perm (index within its item), packed in-bin offsets, deltas.
 template <typename Real>
 cudaError_t launch_scatter(const SortArgs& s, const int* bin_start, const int2* bin_rank, int* perm, uint32_t* local,
@@ -53,6 +55,7 @@ struct PointKernelArgs {
   // subproblems whose bin holds sub_min_count <= points < sub_max_count are this launch's
   int sub_min_count, sub_max_count;
   int item_begin, item_end;   // the launch's items (internal order)
+  int* err;                   // device error flag: kernels that give up a wait set bit 1
 };
 
 // Points of the subproblem's whole bin (the sparse / dense split is per bin).
@@ -123,6 +126,19 @@ const void* planes_kernel_f32(int taps, int warps, bool spread);
 const void* planes_kernel_f64(int taps, int warps, bool spread);
 size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile);
 size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile);
+
+// 3-D spreading on the tensor cores (points_tc.cuh): FP32, taps 4, 6 or 8,
+// tiles of at most 128 (z, y) rows and 2 T2 <= kTcMaxColsHost real columns;
+// blocks of kTcThreadsHost threads.
+constexpr int kTcThreadsHost = 256;
+constexpr int kTcRowsHost = 128;
+constexpr int kTcMaxColsHost = 112;
+struct TcLaunch {
+  int ncols;       // N of the MMAs: 2 T2 rounded up to 16
+  int tmem_cols;   // tensor-memory columns per block: a power of two >= max(32, ncols)
+};
+const void* tc_spread_kernel_f32(int taps);
+size_t tc_spread_smem_bytes(int taps, int ncols, const int* tile);
 
 // ---- scaling (deconv.cu) --------------------------------------------------
 // Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.

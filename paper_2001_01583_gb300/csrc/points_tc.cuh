@@ -1,0 +1,353 @@
+// 3-D spreading on the tensor cores (tcgen05), one tile per block.
+//
+// The spreading step of Section 2 (Fig. 1, Algorithm 2) adds, for every
+// point j of a bin, f_j wz_j(z) wy_j(y) wx_j(x) into the bin's tile of
+// T0 x T1 x T2 cells.  Taking the tile's (z, y) rows as the M dimension
+// (T0 T1 <= 128) and its x columns, real and imaginary part side by side, as
+// the N dimension (2 T2, rounded up to a multiple of 16), a chunk of K points
+// adds the product of two dense matrices:
+//   D[(z,y), (x,c)] += sum_k A[(z,y), k] B[k, (x,c)],
+//   A[(z,y), k] = wz_k(z - z0_k) wy_k(y - y0_k),  B[k, (x,c)] = (f_k)_c wx_k(x - x0_k),
+// both zero outside the point's W x W x W footprint (z0, y0, x0: its first
+// tap in tile coordinates).  D is the tile itself; it stays in tensor memory
+// (TMEM) for the whole subproblem and is added to the grid once, like the
+// shared tile of the plane kernels (halos of neighbouring bins overlap).
+//
+// FP32 accuracy from TF32 products: each operand is split as v = hi + lo with
+// hi = tf32(v) and lo = tf32(v - hi) (round to nearest), and the MMAs add
+// hi*hi + hi*lo + lo*hi.  The split represents v to 2^-24 relative and the
+// dropped lo*lo term is below 2^-24 of the product, so a product carries
+// about three FP32 roundings, as the plane kernels' weight products do; the
+// tensor cores accumulate in FP32.
+//
+// Block of 256 threads, chunks of kTcChunk = 32 points (four K = 8 steps,
+// three products each = 12 MMAs per chunk), operands double-buffered in
+// shared memory in the canonical K-major layout without swizzle: 8 x 16-byte
+// core matrices, 8-row groups kTcSbo = 128 bytes apart, 4-column (K) groups
+// LBO bytes apart.  Per chunk: all threads stage the points' window weights
+// (thread (p, i): tap i of point p in each dimension); then all threads build
+// A and B (16-byte stores of 4 consecutive points of one row: a warp covers
+// 32 consecutive rows, conflict-free) into the buffer whose previous MMAs
+// have completed (mbarrier, bounded wait); one thread issues the MMAs and a
+// commit to that buffer's mbarrier, so the tensor cores work on chunk c
+// while the threads build chunk c + 1.  After the subproblem the block reads
+// D from TMEM (tcgen05.ld, warp w reads lanes 32w..32w+31), stages it in
+// shared memory and adds it to the grid with a warp per tile row.
+//
+// Every wait on an mbarrier gives up after kTcMaxWaits polls: the block then
+// sets bit 1 of the error flag (NFFT_ERR_TIMEOUT at the next nfft_sync),
+// waits once more (bounded) for its MMAs in flight, frees its TMEM and
+// returns.
+#pragma once
+
+#include "points_tiled.cuh"
+
+namespace gbnfft {
+
+constexpr int kTcChunk = 32;            // points per chunk
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;            // M of every MMA
+constexpr uint32_t kTcSbo = 128;        // bytes between 8-row core-matrix groups
+constexpr uint32_t kTcLboA = (kTcRows / 8) * 128;              // bytes between 4-column groups of A
+constexpr uint32_t kTcABytes = (kTcChunk / 4) * kTcLboA;        // one split of one A buffer (16 KB)
+constexpr int kTcMaxWaits = 1 << 22;
+
+// ncols: N of the MMAs (2 T2 rounded up to 16, at most kTcMaxCols);
+// tmem_cols: TMEM columns allocated (a power of two >= max(32, ncols)).
+constexpr int kTcMaxCols = 112;         // the epilogue stages D (128 x (N + 1) floats) in the A buffers
+static_assert(kTcMaxCols == kTcMaxColsHost && kTcThreads == kTcThreadsHost && kTcRows == kTcRowsHost,
+              "host and device limits of the tensor-core kernel");
+static_assert(kTcRows * (kTcMaxCols + 1) * 4 <= 4 * kTcABytes, "the epilogue's staging fits the A buffers");
+using TcLayout = TcLaunch;
+
+__host__ __device__ inline uint32_t tc_b_bytes(int ncols) { return (uint32_t)(kTcChunk / 4) * (uint32_t)(ncols / 8) * 128u; }
+
+// Dynamic shared memory of k_spread_tc: A (2 buffers x hi/lo), B likewise,
+// kTcChunk point records and weight rows, the tile's index tables, two
+// mbarriers and the TMEM address slot.
+__host__ __device__ inline size_t tc_smem_bytes(int taps, int ncols, const int* tile) {
+  return 4 * (size_t)kTcABytes + 4 * (size_t)tc_b_bytes(ncols) + (size_t)kTcChunk * (16 + 8) +
+         (size_t)kTcChunk * 3 * taps * 4 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 + 16;
+}
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (8-row) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::tf32: D F32, A and B TF32, both K-major,
+// M = 128, N = ncols.
+__device__ __forceinline__ uint32_t tc_idesc(int ncols) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ncols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ float tc_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_sts4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+
+// Split four values and store hi at `hi`, lo at `lo` (16 bytes each).
+__device__ __forceinline__ void tc_store_split(uint32_t hi, uint32_t lo, const float* v) {
+  float h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = tc_tf32(v[q]);
+    l[q] = tc_tf32(v[q] - h[q]);
+  }
+  tc_sts4(hi, h[0], h[1], h[2], h[3]);
+  tc_sts4(lo, l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kTcMaxWaits; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<float> a, TcLayout lay) {
+  static_assert(W >= 2 && W <= 8 && W % 2 == 0, "8 threads stage one point, one tap each");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int S = 3 * W;   // weight row of a staged point: wz | wy | wx
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = lay.ncols;
+  const uint32_t lboB = (uint32_t)(N / 8) * 128u;
+  const uint32_t bBytes = tc_b_bytes(N);
+  unsigned char* const sA = smem_raw;
+  unsigned char* const sB = smem_raw + 4 * kTcABytes;
+  int4* const pos = reinterpret_cast<int4*>(sB + 4 * bBytes);          // z0, y0, x0 of a point's first tap
+  float2* const fv = reinterpret_cast<float2*>(pos + kTcChunk);          // its value
+  float* const wts = reinterpret_cast<float*>(fv + kTcChunk);            // [kTcChunk][S]
+  int64_t* const gz = reinterpret_cast<int64_t*>(wts + kTcChunk * S);    // 8-byte aligned: kTcChunk * S * 4 % 8 == 0
+  const uint32_t sA_a = tc_smem_u32(sA), sB_a = tc_smem_u32(sB);
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  // the index tables and the barriers follow the largest tile of the launch
+  const int T0m = a.items[a.item_begin].geom.tile[0], T1m = a.items[a.item_begin].geom.tile[1],
+            T2m = a.items[a.item_begin].geom.tile[2];
+  int64_t* const gy = gz + T0m;
+  int64_t* const gx = gy + T1m;
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(gx + T2m);
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const uint32_t bar_a[2] = {tc_smem_u32(&bars[0]), tc_smem_u32(&bars[1])};
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tmem_slot)),
+                 "r"(lay.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a[0]));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = tc_idesc(N);
+
+  uint32_t cc = 0;       // chunks committed by this block (uniform)
+  bool failed = false;   // a wait gave up (uniform)
+  for (int sp = lo + blockIdx.x; sp < hi && !failed; sp += gridDim.x) {
+    const SubProblem sub = a.pts.subs[sp];
+    if (!sub_selected(a, sub)) continue;   // block-uniform
+    const ItemDev& it = a.items[sub.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    const float2* f_in = static_cast<const float2*>(call.in);
+    float2* grid = static_cast<float2*>(it.grid);
+    const int T1 = g.tile[1], T2 = g.tile[2];
+    const int rows = g.tile[0] * T1;
+    const WindowDev& win = it.win;
+    int bc[kMaxDim], origin[kMaxDim];
+    bin_coords(sub.bin, g, bc);
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - win.m + win.shift;
+    __syncthreads();   // the previous subproblem's flush no longer reads the tables
+    for (int i = tid; i < g.tile[0] + T1 + T2; i += kTcThreads) {
+      if (i < g.tile[0]) {
+        gz[i] = (int64_t)wrap_mod(origin[0] + i, g.n[0]) * g.n[1] * g.n[2];
+      } else if (i < g.tile[0] + T1) {
+        gy[i - g.tile[0]] = (int64_t)wrap_mod(origin[1] + i - g.tile[0], g.n[1]) * g.n[2];
+      } else {
+        const int x = i - g.tile[0] - T1;
+        gx[x] = wrap_mod(origin[2] + x, g.n[2]);
+      }
+    }
+    for (int r = 0; r < call.nrhs && !failed; ++r) {
+      bool first = true;
+      for (int pb = 0; pb < sub.count; pb += kTcChunk) {
+        const int nb = min(kTcChunk, sub.count - pb);
+        const int buf = (int)(cc & 1u);
+        // stage: thread (p, i) evaluates tap i of point p in each dimension
+        {
+          const int p = tid >> 3, i = tid & 7;
+          if (p < nb) {
+            const int idx = sub.start + pb + p;
+            const float sh = (float)(win.m - win.shift);
+            if (i < W) {
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+                wts[p * S + d * W + i] = window_psi<float>(win, d, a.pts.delta[d][idx] + sh - (float)i);
+            }
+            if (i == 0) {
+              const uint32_t loc = a.pts.local[idx];
+              pos[p] = make_int4(unpack_local(loc, 3, 0), unpack_local(loc, 3, 1), unpack_local(loc, 3, 2), 0);
+              fv[p] = f_in[(int64_t)r * it.M + a.pts.perm[idx]];
+            }
+          } else if (i == 0) {
+            pos[p] = make_int4(-1024, -1024, -1024, 0);   // past the chunk: a zero column of A and row of B
+            fv[p] = make_float2(0.0f, 0.0f);
+          }
+        }
+        __syncthreads();
+        // the MMAs that last read this buffer (chunk cc - 2) must be done
+        bool ok = true;
+        if (cc >= 2) ok = tc_wait(bar_a[buf], ((cc - 2) >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        // build A (rows of (z, y)) and B (rows of (x, re / im)) of the chunk:
+        // item e < 1024: A row e & 127, points 4 (e >> 7) ..; then B
+        const uint32_t aHi = sA_a + (uint32_t)(2 * buf) * kTcABytes, aLo = aHi + kTcABytes;
+        const uint32_t bHi = sB_a + (uint32_t)(2 * buf) * bBytes, bLo = bHi + bBytes;
+        const int nA = kTcRows * (kTcChunk / 4), nItems = nA + N * (kTcChunk / 4);
+        for (int e = tid; e < nItems; e += kTcThreads) {
+          float v[4];
+          if (e < nA) {
+            const int m = e & (kTcRows - 1), k4 = (e >> 7) * 4;
+            const int z = m / T1, y = m - z * T1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int k = k4 + q;
+              const int4 ps = pos[k];
+              const int dz = z - ps.x, dy = y - ps.y;
+              const bool in = m < rows && (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
+              const float wz = wts[k * S + (in ? dz : 0)];
+              const float wy = wts[k * S + W + (in ? dy : 0)];
+              v[q] = in ? wz * wy : 0.0f;
+            }
+            const uint32_t off = (uint32_t)m * 16u + (uint32_t)(k4 >> 2) * kTcLboA;
+            tc_store_split(aHi + off, aLo + off, v);
+          } else {
+            const int eb = e - nA;
+            const int n = eb % N, k4 = (eb / N) * 4;
+            const int x = n >> 1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int k = k4 + q;
+              const int dx = x - pos[k].z;
+              const bool in = x < T2 && (unsigned)dx < (unsigned)W;
+              const float wx = wts[k * S + 2 * W + (in ? dx : 0)];
+              const float2 f = fv[k];
+              v[q] = in ? wx * ((n & 1) ? f.y : f.x) : 0.0f;
+            }
+            const uint32_t off = (uint32_t)n * 16u + (uint32_t)(k4 >> 2) * lboB;
+            tc_store_split(bHi + off, bLo + off, v);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int ks = 0; ks < kTcChunk / 8; ++ks) {
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+              const uint32_t ad = (pr == 2 ? aLo : aHi) + (uint32_t)(2 * ks) * kTcLboA;
+              const uint32_t bd = (pr == 1 ? bLo : bHi) + (uint32_t)(2 * ks) * lboB;
+              tc_mma(tmem, tc_desc(ad, kTcLboA, kTcSbo), tc_desc(bd, lboB, kTcSbo), idesc,
+                     (first && ks == 0 && pr == 0) ? 0u : 1u);
+            }
+          }
+          tc_commit(bar_a[buf]);
+        }
+        first = false;
+        ++cc;
+      }
+      if (failed || first) continue;   // first: the subproblem had no points
+      // the subproblem's last commit covers every MMA before it
+      const uint32_t last = cc - 1;
+      const bool ok = tc_wait(bar_a[last & 1u], (last >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // D -> shared (the A buffers: every MMA reading them is done), row m at pitch N + 1
+      float* const scratch = reinterpret_cast<float*>(sA);
+      const int pitch = N + 1;
+      if (warp < 4) {
+        const int m = warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) scratch[m * pitch + c0 + j] = v[j];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      // add the tile to the grid: a warp per (z, y) row, lanes along x
+      for (int row = warp; row < rows; row += kTcThreads / 32) {
+        const int z = row / T1, y = row - z * T1;
+        const int64_t gb = (int64_t)r * g.grid_cells + gz[z] + gy[y];
+        for (int x = lane; x < T2; x += 32) {
+          const float2 c = make_float2(scratch[row * pitch + 2 * x], scratch[row * pitch + 2 * x + 1]);
+          if (c.x != 0.0f || c.y != 0.0f) grid_add(grid + gb + gx[x], c);
+        }
+      }
+      __syncthreads();   // scratch read before the next chunk's operands overwrite it
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.err, 2);
+    // one more bounded wait for the MMAs in flight before the memory goes away
+    if (cc > 0) tc_wait(bar_a[(cc - 1) & 1u], ((cc - 1) >> 1) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
+}
+
+}  // namespace gbnfft

@@ -24,10 +24,10 @@ __device__ __forceinline__ int find_item(const T* offs, int n, T v) {
   return lo;
 }
 
-// Reduce one coordinate: x -> x - floor(x) in [0, 1) (exact for Eq. 5, which
-// is 1-periodic), u = n x, cell c = floor(u) in [0, n), offset u - c, rounded
-// once to Real.  An offset that rounds up to 1 moves to the next cell with
-// offset 0 (the same position).
+// Reduce one coordinate to a cell c in [0, n) and the offset u - c of the
+// cell coordinate u (Eq. 5 is 1-periodic in x, so any integer shift of x
+// changes no exact sum), rounded once to Real.  An offset that rounds up to 1
+// moves to the next cell with offset 0 (the same position).
 //
 // FP32 offsets: integer arithmetic throughout (FP64 is a slow pipe here).
 // The fraction of |x| is taken from its mantissa bits as a 64-bit binary
@@ -35,9 +35,12 @@ __device__ __forceinline__ int find_item(const T* offs, int n, T v) {
 // dropped), the fraction of x is F or 1 - F, and the 96-bit product n F
 // splits into the cell (its bits 64 and up) and the offset (the 64 below),
 // whose top 32 bits are rounded to float.
-// FP64 offsets: x - floor(x) and n (x - floor(x)) in FP64, so the offset
-// carries the rounding of that product (about n 2^-53 cells) like any FP64
-// evaluation of the same formula.
+// FP64 offsets: the paper's reduction written out in FP64: x is brought into
+// the torus [-1/2, 1/2) of Section 1 as x - floor(x + 1/2), u = n times
+// that, c = floor(u) (then taken mod n) and the offset u - floor(u), so the
+// offset carries only the rounding of that product, at most n/2 2^-53 cells
+// (a reduction to [0, 1) would add the rounding of x + 1 for negative x, up
+// to n 2^-53 cells).
 __device__ __forceinline__ unsigned long long frac64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
@@ -63,10 +66,11 @@ __device__ __forceinline__ void reduce_cell<float>(double x, int n, int& c, floa
 }
 template <>
 __device__ __forceinline__ void reduce_cell<double>(double x, int n, int& c, double& delta) {
-  const double xw = x - floor(x);
+  const double xw = x - floor(x + 0.5);
   const double u = (double)n * xw;
   const double cf = floor(u);
   c = (int)cf;
+  if (c < 0) c += n;   // u >= -n/2 - 1 (x + 1/2 may round up to the next integer)
   delta = u - cf;
 }
 
@@ -155,6 +159,7 @@ __global__ void k_scatter(SortArgs s, const int* __restrict__ bin_start, const i
 
 // Exclusive scan of n ints with one block of 1024 threads: each thread scans a
 // contiguous chunk sequentially, the chunk totals are scanned in shared memory.
+// Used for the per-tile partial sums of the multi-block scan below.
 __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* __restrict__ out, int n,
                                                 int* __restrict__ total) {
   __shared__ int part[1024];
@@ -180,6 +185,67 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* 
     run += v;
   }
   if (total && threadIdx.x == T - 1) *total = part[T - 1];
+}
+
+// Multi-block exclusive scan: tiles of kScanTile ints.  k_scan_reduce sums
+// each tile (coalesced), k_scan scans the tile sums, k_scan_apply scans each
+// tile (16 consecutive ints per thread, then the block's thread totals) and
+// adds its tile's offset.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+// Exclusive prefix of v over the block's threads (in thread order).
+__device__ __forceinline__ int block_exclusive(int v) {
+  __shared__ int wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < w; ++k) before += wsum[k];
+  return before + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restrict__ in, int n,
+                                                               int* __restrict__ partials) {
+  __shared__ int wsum[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int s = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+    if (base + i < n) s += in[base + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < kScanThreads / 32; ++k) t += wsum[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n,
+                                                              const int* __restrict__ offsets) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = base + q < n ? in[base + q] : 0;
+    s += v[q];
+  }
+  int run = block_exclusive(s) + offsets[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < n) out[base + q] = run;
+    run += v[q];
+  }
 }
 
 __global__ void k_sub_count(const int* __restrict__ bin_count, int nbins, int P, int* __restrict__ sub_count) {
@@ -217,8 +283,14 @@ cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const int* in, int* out, int n, int* total, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(in, out, n, total);
+int scan_partials_needed(int n) { return 2 * ((n + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t launch_scan(const int* in, int* out, int n, int* total, int* partials, cudaStream_t st) {
+  const int tiles = (n + kScanTile - 1) / kScanTile;
+  int* const offsets = partials + tiles;   // the scanned tile sums
+  if (tiles > 0) k_scan_reduce<<<tiles, kScanThreads, 0, st>>>(in, n, partials);
+  k_scan<<<1, 1024, 0, st>>>(partials, offsets, tiles, total);
+  if (tiles > 0) k_scan_apply<<<tiles, kScanThreads, 0, st>>>(in, out, n, offsets);
   return cudaGetLastError();
 }
 

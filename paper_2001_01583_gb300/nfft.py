@@ -193,7 +193,7 @@ class Plan:
                     sparse_points=inf.sparse_points, sparse_points_interp=inf.sparse_points_interp,
                     owner_spread=inf.owner_spread, kernel_launches=inf.kernel_launches,
                     interp_threads=inf.interp_threads, spread_block_threads=inf.spread_block_threads,
-                    interp_block_threads=inf.interp_block_threads)
+                    interp_block_threads=inf.interp_block_threads, tensor_spread=inf.tensor_spread)
 
     def autotune(self, reps=3):
         """Time candidate layouts on the points set and keep the fastest;
