@@ -68,3 +68,68 @@ def test_structure_factor_closed_form():
                 else:
                     expect = 0.0
                 assert abs(S[a, b, c] - expect) < 1e-10
+
+
+# ---- forces: the negative gradients of Eqs. 11 and 12 -----------------------
+def _random_ions(n, L, seed):
+    rng = np.random.default_rng(seed)
+    r = rng.random((n, 3)) * L
+    q = rng.choice([-1.0, 2.0], size=n)
+    return r, q - q.mean()   # a neutral box
+
+
+def _fd_force(energy, r, i, t, h=1e-5):
+    rp, rm = r.copy(), r.copy()
+    rp[i, t] += h
+    rm[i, t] -= h
+    return -(energy(rp) - energy(rm)) / (2 * h)
+
+
+def test_real_space_forces_are_the_energy_gradient():
+    # central differences of Eq. 11 itself, component by component: a dropped
+    # term, a wrong sign or a wrong power of d fails
+    L, alpha, rc = 7.0, 0.9, 3.0
+    r, q = _random_ions(24, L, seed=3)
+    F = ewald.real_space_forces(r, q, L, alpha, rc)
+    for i, t in [(0, 0), (3, 1), (11, 2), (23, 0)]:
+        fd = _fd_force(lambda rr: ewald.real_space_energy(rr, q, L, alpha, rc), r, i, t)
+        assert abs(F[i, t] - fd) <= 1e-7 * np.abs(F).max(), (i, t, F[i, t], fd)
+
+
+def test_reciprocal_forces_are_the_energy_gradient():
+    L, alpha, N = 7.0, 0.9, (8, 10, 8)
+    r, q = _random_ions(20, L, seed=4)
+    F = ewald.reciprocal_forces(r, q, L, alpha, N)
+
+    def energy(rr):
+        return ewald.reciprocal_sum(ewald.structure_factor(rr, q, L, N), L, alpha)
+    for i, t in [(0, 0), (5, 1), (13, 2), (19, 1)]:
+        fd = _fd_force(energy, r, i, t)
+        assert abs(F[i, t] - fd) <= 1e-7 * np.abs(F).max(), (i, t, F[i, t], fd)
+
+
+def test_forces_sum_to_zero():
+    # Newton's third law for the pair sum; sum_i F^K_i = (2/L^2) sum_n w n
+    # Im(S(n) conj(S(n))) = 0 for the reciprocal part
+    L, alpha = 8.0, 0.8
+    r, q = _random_ions(30, L, seed=5)
+    FR = ewald.real_space_forces(r, q, L, alpha, 3.5)
+    FK = ewald.reciprocal_forces(r, q, L, alpha, (10, 10, 10))
+    assert np.all(np.abs(FR.sum(axis=0)) <= 1e-12 * np.abs(FR).sum())
+    assert np.all(np.abs(FK.sum(axis=0)) <= 1e-12 * np.abs(FK).sum())
+
+
+def test_perfect_fluorite_has_no_net_force_on_any_ion():
+    # every ion of the perfect crystal sits on a site whose symmetry leaves no
+    # invariant vector, so both parts vanish ion by ion, while a displaced
+    # ion is pulled back (a restoring force along the displacement)
+    r, q, L = inputs.fluorite(2)
+    alpha = 0.9
+    FR = ewald.real_space_forces(r, q, L, alpha, 0.49 * L)
+    FK = ewald.reciprocal_forces(r, q, L, alpha, (12, 12, 12))
+    scale = np.abs(q).max() ** 2 * alpha ** 2
+    assert np.abs(FR).max() <= 1e-10 * scale and np.abs(FK).max() <= 1e-10 * scale
+    r2 = r.copy()
+    r2[0, 0] += 0.05
+    F2 = ewald.real_space_forces(r2, q, L, alpha, 0.49 * L) + ewald.reciprocal_forces(r2, q, L, alpha, (12, 12, 12))
+    assert F2[0, 0] < 0
