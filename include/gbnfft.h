@@ -223,6 +223,21 @@ int nfft_ewald_reciprocal(nfft_plan* plan, const void* q_dev, double L, double a
  * (fixed tiles of 8192 elements, fixed summation tree). */
 int nfft_ewald_reciprocal_sum(nfft_plan* plan, const void* S_dev, double L, double alpha, double* sum_dev);
 
+/* Reciprocal-space Ewald forces on the points set (d = 3 only, else
+ * NFFT_ERR_UNSUPPORTED): the negative gradient of Eq. 12 (Section 5; the
+ * paper names molecular dynamics as the use of the method but prints no
+ * force formula, so this is the derivative written out).  With x_i = r_i / L
+ * (up to an integer shift, e.g. x = r / L - 1/2) and S(n) = sum_j q_j
+ * exp(-2 pi i n.x_j),
+ *   F_i = (2 q_i / L^2) sum_{n in I_N, n != 0} exp(-pi^2 |n|^2 / (alpha L)^2) / |n|^2
+ *         n Im(S(n) exp(2 pi i n.x_i)):
+ * an adjoint NFFT of the charges (Eq. 5), the weights w(n) n_t on I_N, and a
+ * forward NFFT (Eq. 6) of three right-hand sides.  q_dev: M complex of the
+ * plan's precision (real part = charge); F_dev: device, M x 3 doubles,
+ * point-major, written asynchronously on the plan's stream.  The first call
+ * allocates 3 |I_N| + 3 M complex values of scratch kept by the plan. */
+int nfft_ewald_reciprocal_forces(nfft_plan* plan, const void* q_dev, double L, double alpha, double* F_dev);
+
 /* Largest |I_N| nfft_ewald_reciprocal_sum_noalloc accepts (4096 tiles of 8192). */
 #define NFFT_NOALLOC_MAX_MODES 33554432
 
@@ -265,6 +280,17 @@ int nfft_ewald_reciprocal_sum_noalloc(int d, const int64_t* N, int precision, co
  * Madelung check (Eq. 10) runs on the GPU. */
 int nfft_ewald_real_space(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha, double rcut,
                           double* energy, void* cuda_stream);
+
+/* Real-space Ewald forces, the negative gradient of Eq. 11 (Section 5; no
+ * formula in the paper, the derivative written out):
+ *   F_i = q_i sum_j q_j (erfc(alpha d)/d + 2 alpha/sqrt(pi) exp(-alpha^2 d^2)) (r_i - r_j + n L) / d^2
+ * over the pairs and images with d = |r_i - r_j + n L| < rcut, by the same
+ * two forms as nfft_ewald_real_space (cell list with FP32 pair terms and FP64
+ * sums per ion, or all pairs in FP64).  F_dev: device, n x 3 doubles in the
+ * input order; *energy gets U^R as nfft_ewald_real_space would.  Allocates
+ * scratch, runs on cuda_stream and waits for it. */
+int nfft_ewald_real_space_forces(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha,
+                                 double rcut, double* F_dev, double* energy, void* cuda_stream);
 
 /* Wait for the plan's stream, then report (and clear) the device error flag. */
 int nfft_sync(nfft_plan* plan);

@@ -10,11 +10,11 @@ The CUDA library (libgbnfft.so) is loaded on first use; importing this
 package alone (for example for the input generators) needs no GPU.
 """
 
-__all__ = ["Plan", "Batch", "plan_params", "ewald_real_space"]
+__all__ = ["Plan", "Batch", "plan_params", "ewald_real_space", "ewald_real_space_forces"]
 
 
 def __getattr__(name):
-    if name in ("Plan", "Batch", "plan_params", "ewald_real_space"):
+    if name in ("Plan", "Batch", "plan_params", "ewald_real_space", "ewald_real_space_forces"):
         from . import nfft
         return getattr(nfft, name)
     raise AttributeError(name)

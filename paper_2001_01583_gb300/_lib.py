@@ -111,10 +111,13 @@ def _declare(lib):
         "nfft_ewald_reciprocal": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(ctypes.c_double)]),
         "nfft_ewald_reciprocal_sum": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, vp]),
+        "nfft_ewald_reciprocal_forces": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, vp]),
         "nfft_ewald_reciprocal_sum_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_double,
                                                               ctypes.c_double, vp, vp]),
         "nfft_ewald_real_space": (ctypes.c_int, [ctypes.c_int64, vp, vp, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]),
+        "nfft_ewald_real_space_forces": (ctypes.c_int, [ctypes.c_int64, vp, vp, ctypes.c_double, ctypes.c_double,
+                                                         ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "nfft_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int,
                                               vp]),
         "nfft_batch_destroy": (ctypes.c_int, [vp]),

@@ -244,6 +244,8 @@ Engine::~Engine() {
   free_dev(err_flag);
   free_dev(ewald_partials);
   free_dev(ewald_out);
+  free_dev(force_modes);
+  free_dev(force_vals);
   free_dev(d_items);
   for (int k = 0; k < 2; ++k) {
     if (h_table[k]) cudaFreeHost(h_table[k]);
@@ -953,10 +955,17 @@ int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a) {
   if (!fn) return NFFT_ERR_UNSUPPORTED;
   TcLaunch lay{};
   lay.ncols = (2 * kc.tile[2] + 15) / 16 * 16;
-  lay.tmem_cols = 32;
-  while (lay.tmem_cols < lay.ncols) lay.tmem_cols *= 2;
+  int part = 32;   // columns of a chunk partial; two partials and the tile, allocated as four
+  while (part < lay.ncols) part *= 2;
+  lay.tmem_cols = 4 * part;
   if (kc.tile[0] * kc.tile[1] > kTcRowsHost || lay.ncols > kTcMaxColsHost) return NFFT_ERR_UNSUPPORTED;
-  const size_t smem = tc_spread_smem_bytes(kc.taps, lay.ncols, kc.tile);
+  size_t smem = tc_spread_smem_bytes(kc.taps, lay.ncols, kc.tile);
+  // blocks resident on an SM must not ask for more than its 512 tensor-memory
+  // columns (an allocation that does not fit waits for another block to
+  // free its columns): pad the shared memory so that at most 512 / tmem_cols
+  // blocks fit
+  const size_t max_blocks = (size_t)(512 / lay.tmem_cols);
+  if (max_blocks >= 1 && smem * (max_blocks + 1) <= smem_per_sm) smem = smem_per_sm / (max_blocks + 1) + 1024;
   if (smem > smem_optin) return NFFT_ERR_UNSUPPORTED;
   a.rhs_per_pass = 1;
   int per_sm = std::max(1, blocks_per_sm(fn, kTcThreadsHost, smem));
@@ -1082,9 +1091,8 @@ int Engine::set_points_impl(const double* x_override) {
   TRY(stage_begin(NFFT_STAGE_SORT, &ev));
   CK(cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)std::max(total_bins, 1), stream));
   CK(launch_bin_count<Real>(s, bin_count, bin_rank, stream));
-  // bin count, scatter, subproblem count and fill, two scans of three kernels (the first and
-  // last of a scan only when there are bins)
-  kernel_launches += (s.total_points > 0 ? 4 : 2) + (total_bins > 0 ? 6 : 2);
+  // bin count, scatter, subproblem count and fill, two scans
+  kernel_launches += (s.total_points > 0 ? 4 : 2) + 2 * scan_launches(total_bins);
   CK(launch_scan(bin_count, bin_start, total_bins, nullptr, scan_partials, stream));
   Real* d[3] = {static_cast<Real*>(delta[0]), static_cast<Real*>(delta[1]), static_cast<Real*>(delta[2])};
   CK(launch_scatter<Real>(s, bin_start, bin_rank, perm, local, d, stream));
@@ -1359,6 +1367,41 @@ int Engine::ewald(const void* q, double L, double alpha, double* out) {
   out[1] = parts[0];
   out[2] = parts[1];
   return NFFT_OK;
+}
+
+template <typename Real>
+int Engine::ewald_forces_impl(const void* q, double L, double alpha, double* F) {
+  using C = typename Cplx<Real>::type;
+  const ItemDev& it = items[0];
+  if (!force_modes) TRY(alloc_dev(force_modes, (size_t)3 * (size_t)it.NN * csize, device_bytes));
+  if (!force_vals && it.M > 0) TRY(alloc_dev(force_vals, (size_t)3 * (size_t)it.M * csize, device_bytes));
+  // S(n): the adjoint NFFT (Eq. 5) of the charges, into the first block
+  TRY(adjoint_single(q, force_modes, 1));
+  EwaldGeom g{};
+  g.d = it.geom.d;
+  g.NN = it.NN;
+  for (int t = 0; t < kMaxDim; ++t) {
+    g.N[t] = it.N[t];
+    g.n[t] = it.geom.n[t];
+    g.inv_c[t] = nullptr;
+  }
+  const double al = alpha * L;
+  g.coef = M_PI * M_PI / (al * al);
+  CK(launch_force_modes<Real>(static_cast<C*>(force_modes), g, stream));
+  kernel_launches += it.NN > 0 ? 1 : 0;
+  if (it.M == 0) return NFFT_OK;
+  // sum_n w(n) n_t S(n) exp(+2 pi i n.x_i): the forward NFFT (Eq. 6), three right-hand sides
+  TRY(forward_single(force_modes, force_vals, 3));
+  CK(launch_force_finish<Real>(static_cast<const C*>(force_vals), static_cast<const C*>(q), it.M, 2.0 / (L * L), F,
+                               stream));
+  kernel_launches += 1;
+  return NFFT_OK;
+}
+
+int Engine::ewald_forces(const void* q, double L, double alpha, double* F) {
+  if (specs[0].d != 3) return NFFT_ERR_UNSUPPORTED;
+  return precision == NFFT_FP64 ? ewald_forces_impl<double>(q, L, alpha, F)
+                                : ewald_forces_impl<float>(q, L, alpha, F);
 }
 
 int Engine::ewald_sum(const void* S, double L, double alpha, double* sum_dev) {

@@ -92,6 +92,10 @@ class Engine {
   int stage_times(double* ms, int64_t* launches, int reset);
   int ewald(const void* q, double L, double alpha, double* out3);
   int ewald_sum(const void* S, double L, double alpha, double* sum_dev);
+  // Reciprocal-space forces (negative gradient of Eq. 12) at the points set:
+  // F (device, M x 3 doubles).  Allocates its mode and value buffers on the
+  // first call.
+  int ewald_forces(const void* q, double L, double alpha, double* F);
   int info(nfft_plan_info* out) const;
   int64_t launched() const { return kernel_launches; }
   // Time candidate layouts on the points already set and keep the fastest
@@ -120,6 +124,7 @@ class Engine {
   template <typename Real> int adjoint_table(bool in_graph);
   template <typename Real> int forward_table(bool in_graph);
   template <typename Real> int ewald_impl(const void* q, double L, double alpha);
+  template <typename Real> int ewald_forces_impl(const void* q, double L, double alpha, double* F);
   int run_fft(FClass& fc, int batch, int64_t grid_offset, int direction);
   int fft_handle(FClass& fc, int batch, cufftHandle* out);
   int blocks_per_sm(const void* fn, int threads, size_t smem);
@@ -193,6 +198,8 @@ class Engine {
   int* err_flag = nullptr;
   double* ewald_partials = nullptr;
   double* ewald_out = nullptr;
+  void* force_modes = nullptr;   // 3 |I_N| complex (forces)
+  void* force_vals = nullptr;    // 3 M complex (forces)
   int64_t device_bytes = 0;
   int64_t layout_bytes = 0;
 

@@ -9,6 +9,8 @@
 // per-thread stride, then a fixed shuffle tree), and a second single-block
 // kernel adds the per-tile partials in a fixed tree.  The partials are the
 // only scratch memory; ewald_partials_needed() gives their count.
+#include <algorithm>
+
 #include "ewald.h"
 
 namespace gbnfft {
@@ -114,7 +116,59 @@ __global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ 
   if (threadIdx.x == 0) *out = scale * acc + add;
 }
 
+// w(n) n_t S(n) for t = 0, 1, 2 from S in block 0 (each thread reads its
+// S(n) before writing the three blocks at the same index).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_force_modes(typename Cplx<Real>::type* __restrict__ modes, EwaldGeom g) {
+  using C = typename Cplx<Real>::type;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < g.NN; e += (int64_t)gridDim.x * kThreads) {
+    int a[kMaxDim];
+    const double w = ewald_weight(e, g, a);
+    const C S = modes[e];
+    const double sr = (double)S.x, si = (double)S.y;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const double f = w * (double)(a[t] - g.N[t] / 2);
+      modes[t * g.NN + e] = cmake<C>(f * sr, f * si);
+    }
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_force_finish(const typename Cplx<Real>::type* __restrict__ vals,
+                                                          const typename Cplx<Real>::type* __restrict__ q, int64_t M,
+                                                          double scale, double* __restrict__ F) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < M; i += (int64_t)gridDim.x * kThreads) {
+    const double qi = (double)q[i].x;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) F[i * 3 + t] = scale * qi * (double)vals[t * M + i].y;
+  }
+}
+
 }  // namespace
+
+template <typename Real>
+cudaError_t launch_force_modes(typename Cplx<Real>::type* modes, const EwaldGeom& g, cudaStream_t st) {
+  if (g.NN == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((g.NN + kThreads - 1) / kThreads, 65535);
+  k_force_modes<Real><<<(unsigned)blocks, kThreads, 0, st>>>(modes, g);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_force_finish(const typename Cplx<Real>::type* vals, const typename Cplx<Real>::type* q, int64_t M,
+                                double scale, double* F, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((M + kThreads - 1) / kThreads, 65535);
+  k_force_finish<Real><<<(unsigned)blocks, kThreads, 0, st>>>(vals, q, M, scale, F);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_force_modes<float>(float2*, const EwaldGeom&, cudaStream_t);
+template cudaError_t launch_force_modes<double>(double2*, const EwaldGeom&, cudaStream_t);
+template cudaError_t launch_force_finish<float>(const float2*, const float2*, int64_t, double, double*, cudaStream_t);
+template cudaError_t launch_force_finish<double>(const double2*, const double2*, int64_t, double, double*,
+                                                 cudaStream_t);
 
 int64_t ewald_partials_needed(int64_t count) { return (count + kEwaldTile - 1) / kEwaldTile; }
 

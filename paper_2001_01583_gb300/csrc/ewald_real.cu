@@ -17,6 +17,11 @@
 //     shifts by L, all in FP64, which is the definition itself (r_c < L).
 // The energy 1/2 sum_i q_i phi_i is reduced in FP64 in a fixed order (block
 // partials, then one block over the partials), so it is the same run to run.
+//
+// Forces (the negative gradient of Eq. 11; the paper names MD as the use but
+// prints no force formula): F_i = q_i sum_j q_j g(d) (r_i - r_j + n L) with
+// g(d) = (erfc(alpha d) / d + 2 alpha / sqrt(pi) exp(-alpha^2 d^2)) / d^2,
+// summed by the same two forms (each ion sums its own force, no atomics).
 #include <cmath>
 #include <cstdint>
 
@@ -67,7 +72,7 @@ __global__ void k_rs_count(int64_t n, const double* __restrict__ r, double L, in
 // Sorted record: offset from the cell centre (FP32) and the charge.
 __global__ void k_rs_scatter(int64_t n, const double* __restrict__ r, const double* __restrict__ q, double L, int nc,
                              const int* __restrict__ start, const int2* __restrict__ cell_rank,
-                             float4* __restrict__ rec, int* __restrict__ rec_cell) {
+                             float4* __restrict__ rec, int* __restrict__ rec_cell, int* __restrict__ rec_idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int2 cr = cell_rank[i];
@@ -83,21 +88,29 @@ __global__ void k_rs_scatter(int64_t n, const double* __restrict__ r, const doub
   const int p = start[cr.x] + cr.y;
   rec[p] = make_float4(o[0], o[1], o[2], (float)q[i]);
   rec_cell[p] = cr.x;
+  if (rec_idx) rec_idx[p] = (int)i;
 }
 
+constexpr float kTwoOverSqrtPiF = 1.1283791670955126f;
+constexpr double kTwoOverSqrtPi = 1.1283791670955126;
+
 // Potential of each sorted ion from the 27 cells around its own; block
-// partials of q_i phi_i.
+// partials of q_i phi_i.  FORCES: also the ion's force, written to its
+// original index (F: n x 3 doubles).
+template <bool FORCES>
 __global__ void __launch_bounds__(kRsThreads) k_rs_cells(int n, int nc, float h, float rc2, float alpha,
                                                          const float4* __restrict__ rec,
                                                          const int* __restrict__ rec_cell,
-                                                         const int* __restrict__ start, double* __restrict__ partial) {
+                                                         const int* __restrict__ start, double* __restrict__ partial,
+                                                         const int* __restrict__ rec_idx, double* __restrict__ F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < n) {
     const float4 pi = rec[i];
     const int cell = rec_cell[i];
     const int cz = cell % nc, cy = (cell / nc) % nc, cx = cell / (nc * nc);
-    double phi = 0.0;
+    double phi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    const float c2 = kTwoOverSqrtPiF * alpha, a2 = alpha * alpha;
     for (int dx = -1; dx <= 1; ++dx) {
       const int x = cx + dx < 0 ? cx + dx + nc : (cx + dx >= nc ? cx + dx - nc : cx + dx);
       for (int dy = -1; dy <= 1; ++dy) {
@@ -106,44 +119,79 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_cells(int n, int nc, float h,
           const int z = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
           const int nb = (x * nc + y) * nc + z;
           const float sx = dx * h - pi.x, sy = dy * h - pi.y, sz = dz * h - pi.z;
-          float acc = 0.0f;
+          float acc = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
           for (int j = start[nb]; j < start[nb + 1]; ++j) {
             const float4 pj = rec[j];
-            const float rx = pj.x + sx, ry = pj.y + sy, rz = pj.z + sz;
+            const float rx = pj.x + sx, ry = pj.y + sy, rz = pj.z + sz;   // r_j - r_i
             const float d2 = rx * rx + ry * ry + rz * rz;
             if (d2 < rc2 && d2 > 0.0f) {
               const float rinv = rsqrtf(d2);
-              acc += pj.w * erfcf(alpha * d2 * rinv) * rinv;
+              const float ec = erfcf(alpha * d2 * rinv) * rinv;
+              acc += pj.w * ec;
+              if (FORCES) {
+                const float g = pj.w * (ec + c2 * __expf(-a2 * d2)) * rinv * rinv;
+                ax -= g * rx;
+                ay -= g * ry;
+                az -= g * rz;
+              }
             }
           }
           phi += (double)acc;
+          if (FORCES) {
+            fx += (double)ax;
+            fy += (double)ay;
+            fz += (double)az;
+          }
         }
       }
     }
     e = (double)pi.w * phi;
+    if (FORCES) {
+      const int64_t o = (int64_t)rec_idx[i] * 3;
+      F[o] = (double)pi.w * fx;
+      F[o + 1] = (double)pi.w * fy;
+      F[o + 2] = (double)pi.w * fz;
+    }
   }
   block_partial(e, partial);
 }
 
-// All pairs with the minimum image and the 26 shifts by L, FP64.
+// All pairs with the minimum image and the 26 shifts by L, FP64.  FORCES:
+// also each ion's force (F: n x 3 doubles, input order).
+template <bool FORCES>
 __global__ void __launch_bounds__(kRsThreads) k_rs_pairs(int n, const double* __restrict__ r,
                                                          const double* __restrict__ q, double L, double rc,
-                                                         double alpha, double* __restrict__ partial) {
+                                                         double alpha, double* __restrict__ partial,
+                                                         double* __restrict__ F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < n) {
     const double xi = r[3 * i], yi = r[3 * i + 1], zi = r[3 * i + 2];
-    double phi = 0.0;
+    double phi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
     for (int j = 0; j < n; ++j) {
       double d[3] = {xi - r[3 * j], yi - r[3 * j + 1], zi - r[3 * j + 2]};
       for (int t = 0; t < 3; ++t) d[t] -= L * rint(d[t] / L);
       for (int s = 0; s < 27; ++s) {
         const double ax = d[0] + (s / 9 - 1) * L, ay = d[1] + ((s / 3) % 3 - 1) * L, az = d[2] + (s % 3 - 1) * L;
         const double dist = sqrt(ax * ax + ay * ay + az * az);
-        if (dist > 0.0 && dist < rc) phi += q[j] * erfc(alpha * dist) / dist;
+        if (dist > 0.0 && dist < rc) {
+          const double ec = erfc(alpha * dist) / dist;
+          phi += q[j] * ec;
+          if (FORCES) {
+            const double g = q[j] * (ec + kTwoOverSqrtPi * alpha * exp(-alpha * alpha * dist * dist)) / (dist * dist);
+            fx += g * ax;   // (r_i - r_j + n L)
+            fy += g * ay;
+            fz += g * az;
+          }
+        }
       }
     }
     e = q[i] * phi;
+    if (FORCES) {
+      F[3 * i] = q[i] * fx;
+      F[3 * i + 1] = q[i] * fy;
+      F[3 * i + 2] = q[i] * fz;
+    }
   }
   block_partial(e, partial);
 }
@@ -160,9 +208,12 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_total(const double* __restric
 }  // namespace
 }  // namespace gbnfft
 
-extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha,
-                                     double rcut, double* energy, void* cuda_stream) {
-  using namespace gbnfft;
+namespace gbnfft {
+namespace {
+
+// The energy (and with F the forces) of Eq. 11: shared by both entry points.
+int real_space_impl(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha, double rcut,
+                    double* energy, double* F_dev, void* cuda_stream) {
   if (n < 0 || !energy || (n > 0 && (!r_dev || !q_dev))) return NFFT_ERR_INVALID_ARG;
   if (!(L > 0.0) || !(alpha > 0.0) || !(rcut > 0.0) || !(rcut < L) || !std::isfinite(L) || !std::isfinite(alpha))
     return NFFT_ERR_INVALID_ARG;
@@ -176,11 +227,12 @@ extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const doubl
   const int blocks = (ni + kRsThreads - 1) / kRsThreads;
   const int cells = nc * nc * nc;
   // scratch: partials (blocks + 1), and for the cell list counts, starts,
-  // (cell, rank), records and record cells
+  // scan scratch, (cell, rank), records, record cells and record indices
   size_t bytes = sizeof(double) * (size_t)(blocks + 1);
   if (nc > 1) {
     bytes += sizeof(int) * (size_t)(2 * cells + 2) + sizeof(int2) * (size_t)n + sizeof(float4) * (size_t)n +
-             sizeof(int) * (size_t)n + sizeof(int) * (size_t)scan_partials_needed(cells + 1) + 64;
+             sizeof(int) * (size_t)n + sizeof(int) * (size_t)scan_partials_needed(cells + 1) +
+             (F_dev ? sizeof(int) * (size_t)n : 0) + 64;
   }
   char* buf = nullptr;
   if (cudaMalloc(&buf, bytes) != cudaSuccess) {
@@ -201,18 +253,26 @@ extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const doubl
     int* count = reinterpret_cast<int*>(cell_rank + n);
     int* start = count + cells + 1;
     int* scan_scratch = start + cells + 1;
+    int* rec_idx = F_dev ? scan_scratch + scan_partials_needed(cells + 1) : nullptr;
     ck(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cells + 1), st));
     k_rs_count<<<blocks, kRsThreads, 0, st>>>(n, r_dev, L, nc, count, cell_rank);
     ck(cudaGetLastError());
     ck(launch_scan(count, start, cells + 1, nullptr, scan_scratch, st));   // start[cells] = n
-    k_rs_scatter<<<blocks, kRsThreads, 0, st>>>(n, r_dev, q_dev, L, nc, start, cell_rank, rec, rec_cell);
+    k_rs_scatter<<<blocks, kRsThreads, 0, st>>>(n, r_dev, q_dev, L, nc, start, cell_rank, rec, rec_cell, rec_idx);
     ck(cudaGetLastError());
     const double h = L / nc;
-    k_rs_cells<<<blocks, kRsThreads, 0, st>>>(ni, nc, (float)h, (float)(rcut * rcut), (float)alpha, rec, rec_cell,
-                                               start, partial);
+    if (F_dev)
+      k_rs_cells<true><<<blocks, kRsThreads, 0, st>>>(ni, nc, (float)h, (float)(rcut * rcut), (float)alpha, rec,
+                                                      rec_cell, start, partial, rec_idx, F_dev);
+    else
+      k_rs_cells<false><<<blocks, kRsThreads, 0, st>>>(ni, nc, (float)h, (float)(rcut * rcut), (float)alpha, rec,
+                                                       rec_cell, start, partial, nullptr, nullptr);
     ck(cudaGetLastError());
   } else {
-    k_rs_pairs<<<blocks, kRsThreads, 0, st>>>(ni, r_dev, q_dev, L, rcut, alpha, partial);
+    if (F_dev)
+      k_rs_pairs<true><<<blocks, kRsThreads, 0, st>>>(ni, r_dev, q_dev, L, rcut, alpha, partial, F_dev);
+    else
+      k_rs_pairs<false><<<blocks, kRsThreads, 0, st>>>(ni, r_dev, q_dev, L, rcut, alpha, partial, nullptr);
     ck(cudaGetLastError());
   }
   k_rs_total<<<1, kRsThreads, 0, st>>>(partial, blocks, 0.5, total);
@@ -223,4 +283,19 @@ extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const doubl
   cudaFree(buf);
   if (status == NFFT_OK) *energy = host;
   return status;
+}
+
+}  // namespace
+}  // namespace gbnfft
+
+extern "C" int nfft_ewald_real_space(int64_t n, const double* r_dev, const double* q_dev, double L, double alpha,
+                                     double rcut, double* energy, void* cuda_stream) {
+  return gbnfft::real_space_impl(n, r_dev, q_dev, L, alpha, rcut, energy, nullptr, cuda_stream);
+}
+
+extern "C" int nfft_ewald_real_space_forces(int64_t n, const double* r_dev, const double* q_dev, double L,
+                                            double alpha, double rcut, double* F_dev, double* energy,
+                                            void* cuda_stream) {
+  if (n > 0 && !F_dev) return NFFT_ERR_INVALID_ARG;
+  return gbnfft::real_space_impl(n, r_dev, q_dev, L, alpha, rcut, energy, n > 0 ? F_dev : nullptr, cuda_stream);
 }

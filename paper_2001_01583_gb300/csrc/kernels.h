@@ -28,8 +28,9 @@ struct SortArgs {
 template <typename Real>
 cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st);
 // Exclusive prefix sum of n ints; *total = sum (may be null).  partials:
-// scan_partials_needed(n) ints of device scratch.  Three launches.
+// scan_partials_needed(n) ints of device scratch.  scan_launches(n) kernels.
 int scan_partials_needed(int n);
+int scan_launches(int n);
 cudaError_t launch_scan(const int* in, int* out, int n, int* total, int* partials, cudaStream_t st);
 // Write every point to its sorted slot: perm (index within its item), packed in-bin offsets, deltas.
 template <typename Real>
@@ -135,7 +136,7 @@ constexpr int kTcRowsHost = 128;
 constexpr int kTcMaxColsHost = 112;
 struct TcLaunch {
   int ncols;       // N of the MMAs: 2 T2 rounded up to 16
-  int tmem_cols;   // tensor-memory columns per block: a power of two >= max(32, ncols)
+  int tmem_cols;   // tensor-memory columns per block: 4 x a power of two >= max(32, ncols)
 };
 const void* tc_spread_kernel_f32(int taps);
 size_t tc_spread_smem_bytes(int taps, int ncols, const int* tile);

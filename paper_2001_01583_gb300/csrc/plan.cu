@@ -144,6 +144,14 @@ int nfft_ewald_reciprocal(nfft_plan* p, const void* q_dev, double L, double alph
   return p->eng.ewald(q_dev, L, alpha, out);
 }
 
+int nfft_ewald_reciprocal_forces(nfft_plan* p, const void* q_dev, double L, double alpha, double* F_dev) {
+  if (!p || !F_dev || !(L > 0.0) || !(alpha > 0.0) || !std::isfinite(L) || !std::isfinite(alpha))
+    return NFFT_ERR_INVALID_ARG;
+  if (!q_dev && p->eng.specs[0].M > 0) return NFFT_ERR_INVALID_ARG;
+  if (!p->eng.points_set) return NFFT_ERR_NOT_READY;
+  return p->eng.ewald_forces(q_dev, L, alpha, F_dev);
+}
+
 int nfft_ewald_reciprocal_sum(nfft_plan* p, const void* S_dev, double L, double alpha, double* sum_dev) {
   if (!p || !S_dev || !sum_dev || !(L > 0.0) || !(alpha > 0.0) || !std::isfinite(L) || !std::isfinite(alpha))
     return NFFT_ERR_INVALID_ARG;

@@ -17,8 +17,14 @@
 // hi = tf32(v) and lo = tf32(v - hi) (round to nearest), and the MMAs add
 // hi*hi + hi*lo + lo*hi.  The split represents v to 2^-24 relative and the
 // dropped lo*lo term is below 2^-24 of the product, so a product carries
-// about three FP32 roundings, as the plane kernels' weight products do; the
-// tensor cores accumulate in FP32.
+// about three FP32 roundings, as the plane kernels' weight products do.  The
+// MMAs' own FP32 accumulation does not round to nearest: its error grows
+// with the number of MMAs adding into a value (measured: 2e-5 of the rms
+// for dense clusters, against 2e-6 for the plane kernels).  So each chunk
+// accumulates in a fresh TMEM partial (two, alternating) and the block adds
+// the completed partial into a third TMEM region, the tile, with ordinary
+// FP32 adds (round to nearest): the MMA accumulation error is that of 12
+// MMAs, whatever the subproblem's size.
 //
 // Block of 256 threads, chunks of kTcChunk = 32 points (four K = 8 steps,
 // three products each = 12 MMAs per chunk), operands double-buffered in
@@ -53,7 +59,8 @@ constexpr uint32_t kTcABytes = (kTcChunk / 4) * kTcLboA;        // one split of 
 constexpr int kTcMaxWaits = 1 << 22;
 
 // ncols: N of the MMAs (2 T2 rounded up to 16, at most kTcMaxCols);
-// tmem_cols: TMEM columns allocated (a power of two >= max(32, ncols)).
+// tmem_cols: TMEM columns allocated, 4 x a power of two >= max(32, ncols):
+// the chunk partials at columns 0 and tmem_cols / 4, the tile at tmem_cols / 2.
 constexpr int kTcMaxCols = 112;         // the epilogue stages D (128 x (N + 1) floats) in the A buffers
 static_assert(kTcMaxCols == kTcMaxColsHost && kTcThreads == kTcThreadsHost && kTcRows == kTcRowsHost,
               "host and device limits of the tensor-core kernel");
@@ -143,6 +150,38 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+// Warps 0-3: tile (TMEM columns sum_col..) += partial (src_col..), or = when
+// `copy`; lane 32 w + l of TMEM is row 32 w + l of both.
+__device__ __forceinline__ void tc_fold(uint32_t tmem, int warp, int ncols, uint32_t src_col, uint32_t sum_col,
+                                        bool copy) {
+  if (warp >= 4) return;
+  const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < ncols; c0 += 16) {
+    float v[16];
+    tc_ld16(base + src_col + (uint32_t)c0, v);
+    if (!copy) {
+      float t[16];
+      tc_ld16(base + sum_col + (uint32_t)c0, t);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] += t[j];
+    }
+    tc_st16(base + sum_col + (uint32_t)c0, v);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 template <int W>
 __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<float> a, TcLayout lay) {
   static_assert(W >= 2 && W <= 8 && W % 2 == 0, "8 threads stage one point, one tap each");
@@ -185,6 +224,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = tc_idesc(N);
+  const uint32_t part_cols = (uint32_t)lay.tmem_cols / 4;   // chunk partials at 0 and part_cols
+  const uint32_t sum_col = 2 * part_cols;                    // the tile
 
   uint32_t cc = 0;       // chunks committed by this block (uniform)
   bool failed = false;   // a wait gave up (uniform)
@@ -214,8 +255,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
       }
     }
     for (int r = 0; r < call.nrhs && !failed; ++r) {
-      bool first = true;
-      for (int pb = 0; pb < sub.count; pb += kTcChunk) {
+      int k = 0;          // chunks of this subproblem so far
+      bool copy = true;   // the next fold starts the tile
+      for (int pb = 0; pb < sub.count; pb += kTcChunk, ++k) {
         const int nb = min(kTcChunk, sub.count - pb);
         const int buf = (int)(cc & 1u);
         // stage: thread (p, i) evaluates tap i of point p in each dimension
@@ -240,12 +282,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
           }
         }
         __syncthreads();
-        // the MMAs that last read this buffer (chunk cc - 2) must be done
+        // the MMAs that last read this buffer and this partial (chunk cc - 2)
+        // must be done; a partial of this subproblem is then added to the tile
         bool ok = true;
         if (cc >= 2) ok = tc_wait(bar_a[buf], ((cc - 2) >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
           failed = true;
           break;
+        }
+        if (k >= 2) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          tc_fold(tmem, warp, N, (uint32_t)buf * part_cols, sum_col, copy);
+          copy = false;
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         // build A (rows of (z, y)) and B (rows of (x, re / im)) of the chunk:
         // item e < 1024: A row e & 127, points 4 (e >> 7) ..; then B
@@ -296,17 +345,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
             for (int pr = 0; pr < 3; ++pr) {
               const uint32_t ad = (pr == 2 ? aLo : aHi) + (uint32_t)(2 * ks) * kTcLboA;
               const uint32_t bd = (pr == 1 ? bLo : bHi) + (uint32_t)(2 * ks) * lboB;
-              tc_mma(tmem, tc_desc(ad, kTcLboA, kTcSbo), tc_desc(bd, lboB, kTcSbo), idesc,
-                     (first && ks == 0 && pr == 0) ? 0u : 1u);
+              tc_mma(tmem + (uint32_t)buf * part_cols, tc_desc(ad, kTcLboA, kTcSbo), tc_desc(bd, lboB, kTcSbo),
+                     idesc, (ks == 0 && pr == 0) ? 0u : 1u);
             }
           }
           tc_commit(bar_a[buf]);
         }
-        first = false;
         ++cc;
       }
-      if (failed || first) continue;   // first: the subproblem had no points
-      // the subproblem's last commit covers every MMA before it
+      if (failed || k == 0) continue;   // k == 0: the subproblem had no points
+      // the subproblem's last commit covers every MMA before it; its last
+      // one or two partials are still to be added
       const uint32_t last = cc - 1;
       const bool ok = tc_wait(bar_a[last & 1u], (last >> 1) & 1u);
       if (__syncthreads_or(!ok)) {
@@ -314,14 +363,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // D -> shared (the A buffers: every MMA reading them is done), row m at pitch N + 1
+      if (k >= 2) {
+        tc_fold(tmem, warp, N, ((cc - 2) & 1u) * part_cols, sum_col, copy);
+        copy = false;
+      }
+      tc_fold(tmem, warp, N, ((cc - 1) & 1u) * part_cols, sum_col, copy);
+      // the tile -> shared (the A buffers: every MMA reading them is done), row m at pitch N + 1
       float* const scratch = reinterpret_cast<float*>(sA);
       const int pitch = N + 1;
       if (warp < 4) {
         const int m = warp * 32 + lane;
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
-          tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + sum_col + (uint32_t)c0, v);
 #pragma unroll
           for (int j = 0; j < 16; ++j) scratch[m * pitch + c0 + j] = v[j];
         }

@@ -285,7 +285,17 @@ cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, 
 
 int scan_partials_needed(int n) { return 2 * ((n + kScanTile - 1) / kScanTile) + 1; }
 
+// Up to kScanSingle ints one block scans them in one launch (a few per
+// thread); longer arrays take the three tiled launches.
+constexpr int kScanSingle = 4 * kScanTile;
+
+int scan_launches(int n) { return n <= kScanSingle ? 1 : 3; }
+
 cudaError_t launch_scan(const int* in, int* out, int n, int* total, int* partials, cudaStream_t st) {
+  if (n <= kScanSingle) {
+    k_scan<<<1, 1024, 0, st>>>(in, out, n, total);
+    return cudaGetLastError();
+  }
   const int tiles = (n + kScanTile - 1) / kScanTile;
   int* const offsets = partials + tiles;   // the scanned tile sums
   if (tiles > 0) k_scan_reduce<<<tiles, kScanThreads, 0, st>>>(in, n, partials);

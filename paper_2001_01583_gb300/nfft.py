@@ -162,6 +162,21 @@ class Plan:
                                                    out), "nfft_ewald_reciprocal")
         return out[0], out[1], out[2]
 
+    def ewald_reciprocal_forces(self, q, L, alpha, out=None):
+        """Reciprocal-space Ewald forces, the negative gradient of Eq. 12, on
+        the points set (x = r / L - 1/2, 3-D): returns an (M, 3) float64 CUDA
+        tensor (asynchronous on the plan's stream)."""
+        qd, _ = self._to_device(q.reshape(self.M), self.cdtype)
+        if out is None:
+            out = torch.empty((self.M, 3), dtype=torch.float64, device=self.device)
+            out.record_stream(self.stream)
+        elif out.dtype != torch.float64 or out.numel() != 3 * self.M or not out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA float64 tensor of M x 3 values")
+        _lib.check(self._lib.nfft_ewald_reciprocal_forces(self._h, ctypes.c_void_p(qd.data_ptr()), float(L),
+                                                          float(alpha), ctypes.c_void_p(out.data_ptr())),
+                   "nfft_ewald_reciprocal_forces")
+        return out
+
     def ewald_reciprocal_sum(self, S, L, alpha, out=None):
         """The n-sum term of Eq. 12 from a structure factor S on I_N; returns
         a 1-element float64 CUDA tensor (asynchronous)."""
@@ -341,3 +356,24 @@ def ewald_real_space(r, q, L, alpha, rcut, stream=None):
                                          ctypes.c_void_p(qd.data_ptr()), float(L), float(alpha), float(rcut),
                                          ctypes.byref(out), _stream_handle(st)), "nfft_ewald_real_space")
     return out.value
+
+
+def ewald_real_space_forces(r, q, L, alpha, rcut, stream=None):
+    """The negative gradient of Eq. 11: forces (n x 3 float64 CUDA tensor) and
+    the real-space energy (float) of charges q at positions r, pairs and
+    images closer than rcut (0 < rcut < L).  Waits for the stream."""
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(st):
+        rd = r.to(device=dev, dtype=torch.float64).contiguous()
+        qd = q.to(device=dev, dtype=torch.float64).contiguous()
+        F = torch.empty((rd.shape[0], 3), dtype=torch.float64, device=dev)
+    if rd.dim() != 2 or rd.shape[1] != 3 or qd.numel() != rd.shape[0]:
+        raise ValueError("r must be (n, 3) and q must hold n charges")
+    e = ctypes.c_double()
+    _lib.check(lib.nfft_ewald_real_space_forces(int(rd.shape[0]), ctypes.c_void_p(rd.data_ptr()),
+                                                ctypes.c_void_p(qd.data_ptr()), float(L), float(alpha), float(rcut),
+                                                ctypes.c_void_p(F.data_ptr()), ctypes.byref(e), _stream_handle(st)),
+               "nfft_ewald_real_space_forces")
+    return F, e.value
