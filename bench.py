@@ -17,9 +17,9 @@ m = 4, sigma = 2, on two point sets (uniform, and 32 Gaussian clusters of std
 0.02).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload picker|config|small|sparse|batch|1d|fluorite|fig13|fig16]
+                  [--workload picker|config|small|sparse|profile|batch|1d|fluorite|fig13|fig16]
                   [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline] [--no-fp64-form]
-                  [--tensor-spread]
+                  [--tensor-spread] [--tensor-interp]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  "--workload fig13" and "fig16" sweep the
@@ -67,6 +67,10 @@ WORKLOADS = {
                    name="learned parameter picker applied to 3-D N=256^3, M=3x10^7 clustered points (64 Gaussian "
                         "clusters, std 0.01), complex64, eps=1e-5, vs the rule-of-thumb parameters: one step = "
                         "set_points + adjoint + forward NFFT with the picked window parameters, mixed FP32"),
+    "profile": dict(N=(128, 128, 128), M=4_000_000, sets=("clustered64",), picked=True, eps=1e-5,
+                    seeds=dict(x=(0,), f=1, fh=2),
+                    name="scaled-down largest configuration for ncu's multi-pass captures: 3-D N=128^3, M=4x10^6 "
+                         "points in 64 Gaussian clusters (std 0.01), eps=1e-5, picked window parameters, mixed FP32"),
     "fig13": dict(N=(128, 128, 128), M=120 ** 3, sets=("uniform",), sweep=True,
                   name="sweep shaped like Fig. 13: 3-D adjoint+forward NFFT of 58^3, 80^3, 100^3 and 120^3 uniform "
                        "points at N=64^3 and 128^3, Kaiser-Bessel m=4, sigma=2, mixed FP32; value at 120^3, N=128^3"),
@@ -489,9 +493,11 @@ def run_ours(args, wl, rank, world):
         outs_f = [torch.empty((1, M), dtype=tctype, device=dev) for _ in xs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
     plans = [Plan(N, M, sigma, mcut, window, args.precision, stream=stream) for _ in xs]
-    if args.tensor_spread:
-        for p in plans:
+    for p in plans:
+        if args.tensor_spread:
             p.set_option(_lib.OPT_TENSOR_SPREAD, 1)
+        if args.tensor_interp:
+            p.set_option(_lib.OPT_TENSOR_INTERP, 1)
     if args.autotune:
         # the library's autotuner, once per point set, outside the timed region
         with torch.cuda.stream(stream):
@@ -651,6 +657,7 @@ def run_ours(args, wl, rank, world):
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points_per_step,
                        "precision": args.precision, "sigma": sigma, "m": mcut, "window": window, "taps": taps,
                        "autotuned": bool(args.autotune), "tensor_spread": bool(info.get("tensor_spread")),
+                       "tensor_interp": bool(info.get("tensor_interp")),
                        "autotuned_layout": {k: info[k] for k in ("bin", "max_subproblem", "spread_block_threads",
                                                                  "interp_block_threads", "sparse_points",
                                                                  "sparse_points_interp")},
@@ -979,6 +986,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--tensor-spread", action="store_true",
                     help="plan workloads: spread the dense bins on the tensor cores (NFFT_OPT_TENSOR_SPREAD)")
+    ap.add_argument("--tensor-interp", action="store_true",
+                    help="plan workloads: interpolate the dense bins on the tensor cores (NFFT_OPT_TENSOR_INTERP)")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip timing the plain FP64 form of the plan workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -117,7 +117,7 @@ typedef enum {
                                    uses the grid-warp atomics, which measure
                                    faster (an owner pass repeats each point's
                                    weights for every owner it touches) */
-  NFFT_OPT_TENSOR_SPREAD = 13   /* d = 3, NFFT_FP32_MIXED, windows of 4, 6 or 8
+  NFFT_OPT_TENSOR_SPREAD = 13,  /* d = 3, NFFT_FP32_MIXED, windows of 4, 6 or 8
                                    taps, NFFT_METHOD_AUTO or _WARP: 1 spreads
                                    the dense bins on the tensor cores (tcgen05
                                    MMAs of TF32 operands split in two, so the
@@ -128,8 +128,16 @@ typedef enum {
                                    bins must satisfy (b0 + W - 1)(b1 + W - 1) <= 128
                                    and 2 (b2 + W - 1) <= 112, else nfft_set_option
                                    returns NFFT_ERR_UNSUPPORTED.  Interpolation
-                                   keeps the plane kernels.  0 (default): the
+                                   keeps the plane kernels unless
+                                   NFFT_OPT_TENSOR_INTERP is set.  0 (default): the
                                    plane-owner shared-memory kernel */
+  NFFT_OPT_TENSOR_INTERP = 14   /* the same conditions: 1 interpolates the dense
+                                   bins on the tensor cores (the chunk's points
+                                   as the MMA's rows, the tile's (z, y) rows as
+                                   its K; each point then sums its own x
+                                   columns).  Takes the same bins as
+                                   NFFT_OPT_TENSOR_SPREAD; either option alone
+                                   or both.  0 (default): the plane kernels */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -172,6 +180,7 @@ typedef struct {
                                 kernel (3-D plane kernels: 32 x warps; 0 = none yet) */
   int interp_block_threads;  /* the same for interpolation */
   int tensor_spread;         /* 1: dense bins are spread on the tensor cores (NFFT_OPT_TENSOR_SPREAD) */
+  int tensor_interp;         /* 1: dense bins are interpolated on the tensor cores (NFFT_OPT_TENSOR_INTERP) */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling

@@ -380,7 +380,7 @@ int Engine::build_layout() {
 
   struct Choice {
     int bin[3], tile[3], pitch, method, taps, sparse, sparse_interp;
-    bool owner, tensor;
+    bool owner, tensor, tensor_interp;
   };
   std::vector<Choice> ch(nitems);
   for (int i = 0; i < nitems; ++i) {
@@ -437,16 +437,18 @@ int Engine::build_layout() {
     }
     // tensor-core spreading: the tile's (z, y) rows are the MMA's M = 128
     // rows and its x columns (complex) its N <= 112 columns
-    c.tensor = false;
-    if (tensor_enabled && planes && precision == NFFT_FP32_MIXED && s.window != NFFT_B_SPLINE &&
-        (method_opt == NFFT_METHOD_AUTO || method_opt == NFFT_METHOD_WARP) && tc_spread_kernel_f32(c.taps)) {
+    c.tensor = c.tensor_interp = false;
+    if ((tensor_enabled || tensor_interp_enabled) && planes && precision == NFFT_FP32_MIXED &&
+        s.window != NFFT_B_SPLINE && (method_opt == NFFT_METHOD_AUTO || method_opt == NFFT_METHOD_WARP) &&
+        tc_spread_kernel_f32(c.taps)) {
       if (!explicit_bins) {
         const int want[3] = {12 - c.taps, 12 - c.taps, 16};
         for (int t = 0; t < 3; ++t) c.bin[t] = (int)std::min<int64_t>(want[t], n[t]);
       }
       const int t0 = c.bin[0] + c.taps - 1, t1 = c.bin[1] + c.taps - 1, t2 = c.bin[2] + c.taps - 1;
       if (t0 * t1 > kTcRowsHost || 2 * t2 > kTcMaxColsHost) return NFFT_ERR_UNSUPPORTED;
-      c.tensor = true;
+      c.tensor = tensor_enabled;
+      c.tensor_interp = tensor_interp_enabled;
     }
     if (!planes)
       while (tile_bytes(c.bin) > budget && !explicit_bins && halve_largest(c.bin)) {
@@ -620,6 +622,7 @@ int Engine::build_layout() {
       kc.sparse_points_interp = c.sparse_interp;
       kc.owner = c.owner;
       kc.tensor = c.tensor;
+      kc.tensor_interp = c.tensor_interp;
       kc.item_begin = k;
       kc.bin_begin = bin_off[k];
       kc.max_nrhs = 0;
@@ -842,8 +845,8 @@ int Engine::run_points(const KClass& kc, bool spread, const void* in, void* out,
   a.sub_min_count = split;
   int st;
   if constexpr (sizeof(Real) == 4) {
-    if (spread && kc.tensor) {
-      st = run_tc(kc, a);
+    if (spread ? kc.tensor : kc.tensor_interp) {
+      st = run_tc(kc, a, spread);
     } else {
       st = kc.method == NFFT_METHOD_WARP
                ? (kc.d == 3 ? run_planes<Real>(kc, a, spread, max_nrhs) : run_wpp<Real>(kc, a, spread, max_nrhs))
@@ -950,16 +953,17 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
 
 // 3-D dense bins spread on the tensor cores: a block of kTcThreadsHost
 // threads per subproblem, the tile in tensor memory (points_tc.cuh).
-int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a) {
-  const void* fn = tc_spread_kernel_f32(kc.taps);
+int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a, bool spread) {
+  const void* fn = spread ? tc_spread_kernel_f32(kc.taps) : tc_interp_kernel_f32(kc.taps);
   if (!fn) return NFFT_ERR_UNSUPPORTED;
   TcLaunch lay{};
   lay.ncols = (2 * kc.tile[2] + 15) / 16 * 16;
-  int part = 32;   // columns of a chunk partial; two partials and the tile, allocated as four
+  int part = 32;   // columns of one accumulator: spreading holds two chunk partials and the tile (four)
   while (part < lay.ncols) part *= 2;
-  lay.tmem_cols = 4 * part;
+  lay.tmem_cols = spread ? 4 * part : part;
   if (kc.tile[0] * kc.tile[1] > kTcRowsHost || lay.ncols > kTcMaxColsHost) return NFFT_ERR_UNSUPPORTED;
-  size_t smem = tc_spread_smem_bytes(kc.taps, lay.ncols, kc.tile);
+  size_t smem = spread ? tc_spread_smem_bytes(kc.taps, lay.ncols, kc.tile)
+                       : tc_interp_smem_bytes_host(kc.taps, lay.ncols, kc.tile);
   // blocks resident on an SM must not ask for more than its 512 tensor-memory
   // columns (an allocation that does not fit waits for another block to
   // free its columns): pad the shared memory so that at most 512 / tmem_cols
@@ -978,7 +982,7 @@ int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a) {
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kTcThreadsHost), args, smem, stream));
   ++kernel_launches;
-  last_spread_threads = kTcThreadsHost;
+  (spread ? last_spread_threads : last_interp_threads) = kTcThreadsHost;
   return NFFT_OK;
 }
 
@@ -1459,8 +1463,9 @@ int Engine::set_option(int option, int64_t value) {
       owner_enabled = value != 0;
       break;
     case NFFT_OPT_TENSOR_SPREAD:
+    case NFFT_OPT_TENSOR_INTERP:
       if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
-      tensor_enabled = value != 0;
+      (option == NFFT_OPT_TENSOR_SPREAD ? tensor_enabled : tensor_interp_enabled) = value != 0;
       break;
     case NFFT_OPT_SPARSE_POINTS:
     case NFFT_OPT_SPARSE_POINTS_INTERP:
@@ -1547,6 +1552,7 @@ int Engine::info(nfft_plan_info* out) const {
   out->kernel_launches = kernel_launches;
   out->interp_threads = interp_threads_opt;
   out->tensor_spread = kclasses.empty() ? 0 : (kclasses[0].tensor ? 1 : 0);
+  out->tensor_interp = kclasses.empty() ? 0 : (kclasses[0].tensor_interp ? 1 : 0);
   out->spread_block_threads = last_spread_threads;
   out->interp_block_threads = last_interp_threads;
   return NFFT_OK;
@@ -1649,7 +1655,7 @@ int Engine::autotune(int reps, double* best_ms) {
   };
   std::vector<Cand> cands;
   const int Ps[2] = {1024, 256};
-  if (dmax == 3 && tensor_enabled && precision == NFFT_FP32_MIXED) {
+  if (dmax == 3 && (tensor_enabled || tensor_interp_enabled) && precision == NFFT_FP32_MIXED) {
     // tensor-core spreading: (z, y) rows of the tile within the MMA's 128,
     // x columns along the N dimension
     const int b = std::max(1, 12 - taps_for(specs[0].window, specs[0].m));

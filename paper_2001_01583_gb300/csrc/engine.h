@@ -43,6 +43,7 @@ struct KClass {
   int sparse_points_interp;   // the same for interpolation
   bool owner;                 // spreading of sparse bins by the owner kernel (3-D)
   bool tensor;                // dense bins spread on the tensor cores (3-D, FP32)
+  bool tensor_interp;         // dense bins interpolated on the tensor cores (3-D, FP32)
 };
 
 struct FClass {
@@ -120,7 +121,7 @@ class Engine {
   template <typename Real> int run_gm(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
   template <typename Real> int run_owner(const KClass& kc, PointKernelArgs<Real>& a);
   template <typename Real> int run_global(const KClass& kc, PointKernelArgs<Real>& a, bool spread);
-  int run_tc(const KClass& kc, PointKernelArgs<float>& a);
+  int run_tc(const KClass& kc, PointKernelArgs<float>& a, bool spread);
   template <typename Real> int adjoint_table(bool in_graph);
   template <typename Real> int forward_table(bool in_graph);
   template <typename Real> int ewald_impl(const void* q, double L, double alpha);
@@ -148,6 +149,7 @@ class Engine {
   int sparse_opt = 0;          // NFFT_OPT_SPARSE_POINTS
   bool owner_enabled = false;  // NFFT_OPT_OWNER_SPREAD
   bool tensor_enabled = false; // NFFT_OPT_TENSOR_SPREAD
+  bool tensor_interp_enabled = false;  // NFFT_OPT_TENSOR_INTERP
   int64_t kernel_launches = 0;   // this library's kernels launched so far (graph replays included)
   int64_t graph_launches[2] = {0, 0};
   int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP

@@ -140,6 +140,9 @@ struct TcLaunch {
 };
 const void* tc_spread_kernel_f32(int taps);
 size_t tc_spread_smem_bytes(int taps, int ncols, const int* tile);
+// Interpolation on the tensor cores (the same tiles): one block per SM.
+const void* tc_interp_kernel_f32(int taps);
+size_t tc_interp_smem_bytes_host(int taps, int ncols, const int* tile);
 
 // ---- scaling (deconv.cu) --------------------------------------------------
 // Adjoint step 3 for every item: fhat[r][k] = grid[r][k mod n] * inv_c(k), k in I_N.

@@ -404,4 +404,218 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
 }
 
+
+// ---------------------------------------------------------------------------
+// Interpolation on the tensor cores (the interpolating step of Section 2,
+// Fig. 2, Algorithm 5): f_j = sum_{z,y,x} G[z,y,x] wz_j(z - z0_j) wy_j(y - y0_j)
+// wx_j(x - x0_j).  With the chunk's points as the M dimension (128 points),
+// the tile's (z, y) rows as K (128) and the tile's x columns, real and
+// imaginary part side by side, as N:
+//   D[j, (x,c)] = sum_m A[j, m] B[(x,c), m],  A[j, (z,y)] = wz_j(z - z0_j) wy_j(y - y0_j),
+//   B[(x,c), (z,y)] = the tile's component c at (z, y, x),
+// and f_j = sum_x wx_j(x - x0_j) (D[j, (x,0)] + i D[j, (x,1)]): TMEM lane j
+// holds point j's row, so each thread finishes its own point's sum over x.
+// B (the tile) is loaded and split once per subproblem; A is built per chunk
+// of 128 points (hi and lo, 64 KB each); 16 K steps x 3 products = 48 MMAs
+// (M = 128, N = 2 T2 rounded to 16, K = 8) per chunk, whose FP32 accumulation
+// error is that of 48 MMAs.  One block per SM (about 190 KB of shared
+// memory); the chunk steps run in sequence: stage, build A, MMAs, wait
+// (bounded), read D.
+constexpr int kTcIChunk = 128;                                  // points per chunk (M)
+constexpr uint32_t kTcILboA = (kTcIChunk / 8) * 128;            // K groups of A 2048 bytes apart
+constexpr uint32_t kTcIABytes = (kTcRows / 4) * kTcILboA;       // one split of A: 128 x 128 floats (64 KB)
+__host__ __device__ inline uint32_t tc_ib_bytes(int ncols) { return (uint32_t)(kTcRows / 4) * (uint32_t)(ncols / 8) * 128u; }
+
+// Dynamic shared memory of k_interp_tc: A hi/lo, B hi/lo, kTcIChunk point
+// records (position, output index) and weight rows, index tables, one
+// mbarrier and the TMEM slot.
+__host__ __device__ inline size_t tc_interp_smem_bytes(int taps, int ncols, const int* tile) {
+  return 2 * (size_t)kTcIABytes + 2 * (size_t)tc_ib_bytes(ncols) + (size_t)kTcIChunk * (16 + 8) +
+         (size_t)kTcIChunk * 3 * taps * 4 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 + 16;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kTcThreads, 1) k_interp_tc(PointKernelArgs<float> a, TcLayout lay) {
+  static_assert(W >= 2 && W <= 8 && W % 2 == 0, "windows of 2 to 8 taps");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int S = 3 * W;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = lay.ncols;
+  const uint32_t lboB = (uint32_t)(N / 8) * 128u;
+  const uint32_t bBytes = tc_ib_bytes(N);
+  unsigned char* const sA = smem_raw;
+  unsigned char* const sB = smem_raw + 2 * kTcIABytes;
+  int4* const pos = reinterpret_cast<int4*>(sB + 2 * bBytes);         // z0, y0, x0 of a point's first tap
+  int* const jt = reinterpret_cast<int*>(pos + kTcIChunk);              // its index in the output
+  float* const wts = reinterpret_cast<float*>(jt + 2 * kTcIChunk);      // [kTcIChunk][S] (8-byte aligned)
+  int64_t* const gz = reinterpret_cast<int64_t*>(wts + kTcIChunk * S);
+  const uint32_t sA_a = tc_smem_u32(sA), sB_a = tc_smem_u32(sB);
+  int lo, hi;
+  launch_subs(a, lo, hi);
+  const int T0m = a.items[a.item_begin].geom.tile[0], T1m = a.items[a.item_begin].geom.tile[1],
+            T2m = a.items[a.item_begin].geom.tile[2];
+  int64_t* const gy = gz + T0m;
+  int64_t* const gx = gy + T1m;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(gx + T2m);
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const uint32_t bar_a = tc_smem_u32(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tmem_slot)),
+                 "r"(lay.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = tc_idesc(N);
+  const uint32_t aHi = sA_a, aLo = sA_a + kTcIABytes, bHi = sB_a, bLo = sB_a + bBytes;
+
+  uint32_t cc = 0;   // chunks committed (uniform): the mbarrier's phase
+  bool failed = false;
+  for (int sp = lo + blockIdx.x; sp < hi && !failed; sp += gridDim.x) {
+    const SubProblem sub = a.pts.subs[sp];
+    if (!sub_selected(a, sub)) continue;   // block-uniform
+    const ItemDev& it = a.items[sub.item];
+    const GridGeom& g = it.geom;
+    const ItemCall call = item_call(a, it);
+    float2* f_out = static_cast<float2*>(call.out);
+    const float2* grid_in = static_cast<const float2*>(it.grid);
+    const int T1 = g.tile[1], T2 = g.tile[2];
+    const int rows = g.tile[0] * T1;
+    const WindowDev& win = it.win;
+    int bc[kMaxDim], origin[kMaxDim];
+    bin_coords(sub.bin, g, bc);
+    for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - win.m + win.shift;
+    __syncthreads();   // the previous subproblem's readers of B and the tables are done
+    for (int i = tid; i < g.tile[0] + T1 + T2; i += kTcThreads) {
+      if (i < g.tile[0]) {
+        gz[i] = (int64_t)wrap_mod(origin[0] + i, g.n[0]) * g.n[1] * g.n[2];
+      } else if (i < g.tile[0] + T1) {
+        gy[i - g.tile[0]] = (int64_t)wrap_mod(origin[1] + i - g.tile[0], g.n[1]) * g.n[2];
+      } else {
+        const int x = i - g.tile[0] - T1;
+        gx[x] = wrap_mod(origin[2] + x, g.n[2]);
+      }
+    }
+    __syncthreads();
+    for (int r = 0; r < call.nrhs && !failed; ++r) {
+      // B: the tile of right-hand side r, B[(x, c), m] at rows n = 2x + c,
+      // K = the tile row m = (z, y); zero outside the tile
+      for (int e = tid; e < N * (kTcRows / 4); e += kTcThreads) {
+        const int n = e % N, m4 = (e / N) * 4;
+        const int x = n >> 1;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int m = m4 + q;
+          v[q] = 0.0f;
+          if (m < rows && x < T2) {
+            const int z = m / T1, y = m - z * T1;
+            const float2 c = grid_in[(int64_t)r * g.grid_cells + gz[z] + gy[y] + gx[x]];
+            v[q] = (n & 1) ? c.y : c.x;
+          }
+        }
+        const uint32_t off = (uint32_t)n * 16u + (uint32_t)(m4 >> 2) * lboB;
+        tc_store_split(bHi + off, bLo + off, v);
+      }
+      for (int pb = 0; pb < sub.count; pb += kTcIChunk) {
+        const int nb = min(kTcIChunk, sub.count - pb);
+        // stage: the chunk's window weights, positions and output indices
+        for (int e = tid; e < kTcIChunk * W; e += kTcThreads) {
+          const int p = e / W, i = e - p * W;
+          if (p < nb) {
+            const int idx = sub.start + pb + p;
+            const float sh = (float)(win.m - win.shift);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              wts[p * S + d * W + i] = window_psi<float>(win, d, a.pts.delta[d][idx] + sh - (float)i);
+            if (i == 0) {
+              const uint32_t loc = a.pts.local[idx];
+              pos[p] = make_int4(unpack_local(loc, 3, 0), unpack_local(loc, 3, 1), unpack_local(loc, 3, 2), 0);
+              jt[p] = a.pts.perm[idx];
+            }
+          } else if (i == 0) {
+            pos[p] = make_int4(-1024, -1024, -1024, 0);   // a zero row of A
+          }
+        }
+        __syncthreads();
+        // A[j, m] = wz_j(z - z0_j) wy_j(y - y0_j); item e: point e & 127, rows 4 (e >> 7) ..
+        for (int e = tid; e < kTcIChunk * (kTcRows / 4); e += kTcThreads) {
+          const int j = e & (kTcIChunk - 1), m4 = (e >> 7) * 4;
+          const int4 ps = pos[j];
+          float v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int m = m4 + q;
+            const int z = m / T1, y = m - z * T1;
+            const int dz = z - ps.x, dy = y - ps.y;
+            const bool in = m < rows && (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
+            const float wz = wts[j * S + (in ? dz : 0)];
+            const float wy = wts[j * S + W + (in ? dy : 0)];
+            v[q] = in ? wz * wy : 0.0f;
+          }
+          const uint32_t off = (uint32_t)j * 16u + (uint32_t)(m4 >> 2) * kTcILboA;
+          tc_store_split(aHi + off, aLo + off, v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int ks = 0; ks < kTcRows / 8; ++ks) {
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+              const uint32_t ad = (pr == 2 ? aLo : aHi) + (uint32_t)(2 * ks) * kTcILboA;
+              const uint32_t bd = (pr == 1 ? bLo : bHi) + (uint32_t)(2 * ks) * lboB;
+              tc_mma(tmem, tc_desc(ad, kTcILboA, kTcSbo), tc_desc(bd, lboB, kTcSbo), idesc,
+                     (ks == 0 && pr == 0) ? 0u : 1u);
+            }
+          }
+          tc_commit(bar_a);
+        }
+        const bool ok = tc_wait(bar_a, cc & 1u);
+        ++cc;
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // point j = 32 warp + lane: its row of D, summed over x with its x weights
+        if (warp < 4) {
+          const int j = warp * 32 + lane;
+          float sr = 0.0f, si = 0.0f;
+          const int x0 = pos[j].z;
+          for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+              const int dx = (c0 >> 1) + h - x0;
+              const bool in = (unsigned)dx < (unsigned)W;
+              const float wx = wts[j * S + 2 * W + (in ? dx : 0)];
+              sr = fmaf(in ? wx : 0.0f, v[2 * h], sr);
+              si = fmaf(in ? wx : 0.0f, v[2 * h + 1], si);
+            }
+          }
+          if (j < nb) f_out[(int64_t)r * it.M + jt[j]] = make_float2(sr, si);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // D read and the chunk's tables used before the next chunk overwrites them
+      }
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.err, 2);
+    if (cc > 0) tc_wait(bar_a, (cc - 1) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
+}
+
 }  // namespace gbnfft

@@ -66,7 +66,8 @@ def test_real_space_forces_against_oracle(L, rc, tol):
     err = np.abs(got - want).max() / np.abs(want).max()
     print("real-space forces (L / rc = %.1f): max |dF| / max |F| = %.2e" % (L / rc, err))
     assert err <= tol
-    assert e == ewald_real_space(torch.from_numpy(r), torch.from_numpy(q), L, alpha, rc)
+    e0 = ewald_real_space(torch.from_numpy(r), torch.from_numpy(q), L, alpha, rc)
+    assert abs(e - e0) <= 1e-6 * abs(e0)   # the same pair terms (FP32 in the cell list, contracted alike or not)
 
 
 def test_perfect_fluorite_forces_vanish_and_a_displaced_ion_is_pulled_back():

@@ -114,3 +114,69 @@ def test_tensor_spread_full_size_3d_configuration(kind):
     e = _elementwise(a[0], sa, FP32_ELEM)
     assert ndft.rel_l2(a[0], sa) <= FP32_L2
     print("full size %s: max element error / rms %.2e, rel-l2 %.2e" % (kind, e, ndft.rel_l2(a[0], sa)))
+
+
+# ---- interpolation on the tensor cores (NFFT_OPT_TENSOR_INTERP) -------------
+def _forward_tc(N, x, H, m, window, spread=False, **opts):
+    from paper_2001_01583_gb300 import Plan, _lib
+    R = H.shape[0]
+    with Plan(N, x.shape[0], 2.0, m, window, "fp32") as p:
+        p.set_option(_lib.OPT_TENSOR_INTERP, 1)
+        if spread:
+            p.set_option(_lib.OPT_TENSOR_SPREAD, 1)
+        if R > 1:
+            p.set_option(_lib.OPT_RHS_CAPACITY, R)
+        for k, v in opts.items():
+            p.set_option(getattr(_lib, "OPT_" + k.upper()), v)
+        p.set_points(torch.from_numpy(x).cuda())
+        b = p.forward(torch.from_numpy(H.astype(np.complex64)).cuda())
+        p.sync()
+        return b.cpu().numpy().astype(np.complex128), p.info()
+
+
+@pytest.mark.parametrize("window,m", [("kaiser_bessel", 4), ("kaiser_bessel", 3), ("kaiser_bessel", 2),
+                                      ("gaussian", 3)])
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_tensor_interp_against_oracle(window, m, kind):
+    N, M = (40, 36, 44), 40000
+    if kind == "uniform":
+        x = inputs.uniform_points(M, 3, seed=161)
+    else:
+        x = inputs.clustered_points(M, 3, 6, 0.02, seed=162)
+    H = inputs.complex_normal((1,) + N, seed=163)
+    b, info = _forward_tc(N, x, H, m, window, sparse_points_interp=-1)
+    taps = 2 * m if window == "kaiser_bessel" else 2 * m + 2
+    assert info["tensor_interp"] == 1 and info["interp_block_threads"] == 256
+    sb = S.forward(x, H[0].astype(np.complex64).astype(np.complex128), N, 2.0, m, WIN[window])
+    e = _elementwise(b[0], sb, FP32_ELEM)
+    assert ndft.rel_l2(b[0], sb) <= FP32_L2
+    print("interp %s m=%d %s: max element error / rms %.2e, rel-l2 %.2e" % (window, m, kind, e, ndft.rel_l2(b[0], sb)))
+
+
+def test_tensor_interp_several_right_hand_sides_and_both_directions():
+    N, M, R = (36, 40, 32), 20000, 3
+    x = np.concatenate([inputs.clustered_points(M // 2, 3, 4, 0.03, seed=171),
+                        inputs.uniform_points(M - M // 2, 3, seed=172)])
+    H = inputs.complex_normal((R,) + N, seed=173)
+    b, info = _forward_tc(N, x, H, 4, "kaiser_bessel", spread=True, sparse_points_interp=30)
+    assert info["tensor_interp"] == 1 and info["tensor_spread"] == 1
+    for r in range(R):
+        sb = S.forward(x, H[r].astype(np.complex64).astype(np.complex128), N, 2.0, 4, S.KAISER_BESSEL)
+        _elementwise(b[r], sb, FP32_ELEM)
+        assert ndft.rel_l2(b[r], sb) <= FP32_L2
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_tensor_interp_full_size_3d_configuration(kind):
+    N, M = (64, 64, 64), 10 ** 6
+    if kind == "uniform":
+        x = inputs.uniform_points(M, 3, seed=0)
+    else:
+        x = inputs.clustered_points(M, 3, 32, 0.02, seed=1)
+    H = inputs.complex_normal((1,) + N, seed=8, dtype=np.complex64)
+    b, info = _forward_tc(N, x, H, 4, "kaiser_bessel")
+    assert info["tensor_interp"] == 1
+    sb = S.forward(x, H[0].astype(np.complex128), N, 2.0, 4, S.KAISER_BESSEL)
+    e = _elementwise(b[0], sb, FP32_ELEM)
+    assert ndft.rel_l2(b[0], sb) <= FP32_L2
+    print("interp full size %s: max element error / rms %.2e, rel-l2 %.2e" % (kind, e, ndft.rel_l2(b[0], sb)))
