@@ -460,8 +460,14 @@ int Engine::build_layout() {
     const size_t wtile = rows * (size_t)c.pitch * csize;
     const bool tiled_ok = tile_bytes(c.bin) <= budget && c.taps <= (s.d == 3 ? 26 : 32);
     const bool warp_ok = s.d == 3 ? planes : (s.d == 2 && c.taps <= 16 && 2 * wtile + 4096 <= budget);
+    const bool gm_ok = (precision == NFFT_FP64 ? gm_kernel_f64(s.d, c.taps, true) : gm_kernel_f32(s.d, c.taps, true)) !=
+                       nullptr;
     int method = method_opt;
-    if (method == NFFT_METHOD_AUTO) method = warp_ok ? NFFT_METHOD_WARP : (tiled_ok ? NFFT_METHOD_TILED : NFFT_METHOD_GLOBAL);
+    // no tile fits (wide FP64 windows): a warp per point straight on the grid
+    // (vector atomics along grid rows) before the thread-per-point global kernel
+    if (method == NFFT_METHOD_AUTO)
+      method = warp_ok ? NFFT_METHOD_WARP
+                       : (tiled_ok ? NFFT_METHOD_TILED : (gm_ok ? NFFT_METHOD_GRID_WARP : NFFT_METHOD_GLOBAL));
     // B-spline windows run on the global kernels only (the others keep their
     // registers free of its evaluation)
     if (s.window == NFFT_B_SPLINE) {
@@ -470,8 +476,6 @@ int Engine::build_layout() {
     }
     if (method == NFFT_METHOD_TILED && !tiled_ok) return NFFT_ERR_UNSUPPORTED;
     if (method == NFFT_METHOD_WARP && !warp_ok) return NFFT_ERR_UNSUPPORTED;
-    const bool gm_ok = (precision == NFFT_FP64 ? gm_kernel_f64(s.d, c.taps, true) : gm_kernel_f32(s.d, c.taps, true)) !=
-                       nullptr;
     if (method == NFFT_METHOD_GRID_WARP && !gm_ok) return NFFT_ERR_UNSUPPORTED;
     c.method = method;
     // with AUTO, subproblems too small to pay for a tile go to the grid-warp
@@ -972,8 +976,9 @@ int Engine::run_tc(const KClass& kc, PointKernelArgs<float>& a, bool spread) {
   if (max_blocks >= 1 && smem * (max_blocks + 1) <= smem_per_sm) smem = smem_per_sm / (max_blocks + 1) + 1024;
   if (smem > smem_optin) return NFFT_ERR_UNSUPPORTED;
   a.rhs_per_pass = 1;
-  int per_sm = std::max(1, blocks_per_sm(fn, kTcThreadsHost, smem));
-  // every resident block holds tmem_cols of the SM's 512 tensor-memory columns
+  // blocks that fit an SM's shared memory (each also holds 1 KB for the
+  // system) and its 512 tensor-memory columns
+  int per_sm = std::max(1, (int)(smem_per_sm / (smem + 1024)));
   per_sm = std::min(per_sm, 512 / lay.tmem_cols);
   int64_t blocks = (int64_t)per_sm * num_sms;
   if (blocks > kc.max_subs) blocks = kc.max_subs;

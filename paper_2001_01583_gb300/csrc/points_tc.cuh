@@ -20,11 +20,11 @@
 // about three FP32 roundings, as the plane kernels' weight products do.  The
 // MMAs' own FP32 accumulation does not round to nearest: its error grows
 // with the number of MMAs adding into a value (measured: 2e-5 of the rms
-// for dense clusters, against 2e-6 for the plane kernels).  So each chunk
-// accumulates in a fresh TMEM partial (two, alternating) and the block adds
-// the completed partial into a third TMEM region, the tile, with ordinary
-// FP32 adds (round to nearest): the MMA accumulation error is that of 12
-// MMAs, whatever the subproblem's size.
+// for dense clusters, against 2e-6 for the plane kernels).  So each pair of
+// chunks accumulates in a fresh TMEM partial (two, alternating) and the
+// block adds the completed partial into a third TMEM region, the tile, with
+// ordinary FP32 adds (round to nearest): the MMA accumulation error is that
+// of 24 MMAs, whatever the subproblem's size.
 //
 // Block of 256 threads, chunks of kTcChunk = 32 points (four K = 8 steps,
 // three products each = 12 MMAs per chunk), operands double-buffered in
@@ -74,7 +74,7 @@ __host__ __device__ inline uint32_t tc_b_bytes(int ncols) { return (uint32_t)(kT
 // mbarriers and the TMEM address slot.
 __host__ __device__ inline size_t tc_smem_bytes(int taps, int ncols, const int* tile) {
   return 4 * (size_t)kTcABytes + 4 * (size_t)tc_b_bytes(ncols) + (size_t)kTcChunk * (16 + 8) +
-         (size_t)kTcChunk * 3 * taps * 4 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 + 16;
+         (size_t)kTcChunk * 3 * taps * 4 + (size_t)kTcRows * 8 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 + 16;
 }
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
   int4* const pos = reinterpret_cast<int4*>(sB + 4 * bBytes);          // z0, y0, x0 of a point's first tap
   float2* const fv = reinterpret_cast<float2*>(pos + kTcChunk);          // its value
   float* const wts = reinterpret_cast<float*>(fv + kTcChunk);            // [kTcChunk][S]
-  int64_t* const gz = reinterpret_cast<int64_t*>(wts + kTcChunk * S);    // 8-byte aligned: kTcChunk * S * 4 % 8 == 0
+  int2* const zyt = reinterpret_cast<int2*>(wts + kTcChunk * S);         // (z, y) of tile row m (8-byte aligned)
+  int64_t* const gz = reinterpret_cast<int64_t*>(zyt + kTcRows);
   const uint32_t sA_a = tc_smem_u32(sA), sB_a = tc_smem_u32(sB);
   int lo, hi;
   launch_subs(a, lo, hi);
@@ -254,6 +255,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
         gx[x] = wrap_mod(origin[2] + x, g.n[2]);
       }
     }
+    // (z, y) of every MMA row; rows past the tile get a position no footprint reaches
+    for (int m = tid; m < kTcRows; m += kTcThreads)
+      zyt[m] = m < rows ? make_int2(m / T1, m % T1) : make_int2(-4096, -4096);
     for (int r = 0; r < call.nrhs && !failed; ++r) {
       int k = 0;          // chunks of this subproblem so far
       bool copy = true;   // the next fold starts the tile
@@ -290,9 +294,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
           failed = true;
           break;
         }
-        if (k >= 2) {
+        // chunks 2p and 2p + 1 accumulate into partial p & 1; the wait above
+        // (for chunk k - 2) completes pair (k - 3) / 2 at odd k >= 3, whose
+        // partial pair (k + 1) / 2 reuses from chunk k + 1 on
+        if (k >= 3 && (k & 1)) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          tc_fold(tmem, warp, N, (uint32_t)buf * part_cols, sum_col, copy);
+          tc_fold(tmem, warp, N, (uint32_t)(((k - 3) >> 1) & 1) * part_cols, sum_col, copy);
           copy = false;
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
@@ -305,15 +312,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
           float v[4];
           if (e < nA) {
             const int m = e & (kTcRows - 1), k4 = (e >> 7) * 4;
-            const int z = m / T1, y = m - z * T1;
+            const int2 zy = zyt[m];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const int k = k4 + q;
-              const int4 ps = pos[k];
-              const int dz = z - ps.x, dy = y - ps.y;
-              const bool in = m < rows && (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
-              const float wz = wts[k * S + (in ? dz : 0)];
-              const float wy = wts[k * S + W + (in ? dy : 0)];
+              const int kk = k4 + q;
+              const int4 ps = pos[kk];
+              const int dz = zy.x - ps.x, dy = zy.y - ps.y;
+              const bool in = (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
+              const float wz = wts[kk * S + (in ? dz : 0)];
+              const float wy = wts[kk * S + W + (in ? dy : 0)];
               v[q] = in ? wz * wy : 0.0f;
             }
             const uint32_t off = (uint32_t)m * 16u + (uint32_t)(k4 >> 2) * kTcLboA;
@@ -324,11 +331,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
             const int x = n >> 1;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const int k = k4 + q;
-              const int dx = x - pos[k].z;
+              const int kk = k4 + q;
+              const int dx = x - pos[kk].z;
               const bool in = x < T2 && (unsigned)dx < (unsigned)W;
-              const float wx = wts[k * S + 2 * W + (in ? dx : 0)];
-              const float2 f = fv[k];
+              const float wx = wts[kk * S + 2 * W + (in ? dx : 0)];
+              const float2 f = fv[kk];
               v[q] = in ? wx * ((n & 1) ? f.y : f.x) : 0.0f;
             }
             const uint32_t off = (uint32_t)n * 16u + (uint32_t)(k4 >> 2) * lboB;
@@ -345,8 +352,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
             for (int pr = 0; pr < 3; ++pr) {
               const uint32_t ad = (pr == 2 ? aLo : aHi) + (uint32_t)(2 * ks) * kTcLboA;
               const uint32_t bd = (pr == 1 ? bLo : bHi) + (uint32_t)(2 * ks) * lboB;
-              tc_mma(tmem + (uint32_t)buf * part_cols, tc_desc(ad, kTcLboA, kTcSbo), tc_desc(bd, lboB, kTcSbo),
-                     idesc, (ks == 0 && pr == 0) ? 0u : 1u);
+              tc_mma(tmem + (uint32_t)((k >> 1) & 1) * part_cols, tc_desc(ad, kTcLboA, kTcSbo),
+                     tc_desc(bd, lboB, kTcSbo), idesc, ((k & 1) || ks > 0 || pr > 0) ? 1u : 0u);
             }
           }
           tc_commit(bar_a[buf]);
@@ -363,11 +370,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (k >= 2) {
-        tc_fold(tmem, warp, N, ((cc - 2) & 1u) * part_cols, sum_col, copy);
-        copy = false;
+      {
+        // pairs folded in the loop: one per odd k in [3, K - 1]; the rest (one or two) now
+        const int pairs = (k + 1) >> 1;
+        const int folded = k >= 4 ? ((k - 4) >> 1) + 1 : 0;
+        for (int pp = folded; pp < pairs; ++pp) {
+          tc_fold(tmem, warp, N, (uint32_t)(pp & 1) * part_cols, sum_col, copy);
+          copy = false;
+        }
       }
-      tc_fold(tmem, warp, N, ((cc - 1) & 1u) * part_cols, sum_col, copy);
       // the tile -> shared (the A buffers: every MMA reading them is done), row m at pitch N + 1
       float* const scratch = reinterpret_cast<float*>(sA);
       const int pitch = N + 1;
@@ -431,7 +442,8 @@ __host__ __device__ inline uint32_t tc_ib_bytes(int ncols) { return (uint32_t)(k
 // mbarrier and the TMEM slot.
 __host__ __device__ inline size_t tc_interp_smem_bytes(int taps, int ncols, const int* tile) {
   return 2 * (size_t)kTcIABytes + 2 * (size_t)tc_ib_bytes(ncols) + (size_t)kTcIChunk * (16 + 8) +
-         (size_t)kTcIChunk * 3 * taps * 4 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 + 16;
+         (size_t)kTcIChunk * 3 * taps * 4 + (size_t)kTcRows * 8 + (size_t)(tile[0] + tile[1] + tile[2]) * 8 + 16 +
+         16;
 }
 
 template <int W>
@@ -448,7 +460,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_interp_tc(PointKernelArgs<flo
   int4* const pos = reinterpret_cast<int4*>(sB + 2 * bBytes);         // z0, y0, x0 of a point's first tap
   int* const jt = reinterpret_cast<int*>(pos + kTcIChunk);              // its index in the output
   float* const wts = reinterpret_cast<float*>(jt + 2 * kTcIChunk);      // [kTcIChunk][S] (8-byte aligned)
-  int64_t* const gz = reinterpret_cast<int64_t*>(wts + kTcIChunk * S);
+  int2* const zyt = reinterpret_cast<int2*>(wts + kTcIChunk * S);        // (z, y) of tile row m
+  int64_t* const gz = reinterpret_cast<int64_t*>(zyt + kTcRows);
   const uint32_t sA_a = tc_smem_u32(sA), sB_a = tc_smem_u32(sB);
   int lo, hi;
   launch_subs(a, lo, hi);
@@ -503,6 +516,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_interp_tc(PointKernelArgs<flo
         gx[x] = wrap_mod(origin[2] + x, g.n[2]);
       }
     }
+    for (int m = tid; m < kTcRows; m += kTcThreads)
+      zyt[m] = m < rows ? make_int2(m / T1, m % T1) : make_int2(-4096, -4096);
     __syncthreads();
     for (int r = 0; r < call.nrhs && !failed; ++r) {
       // B: the tile of right-hand side r, B[(x, c), m] at rows n = 2x + c,
@@ -516,8 +531,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_interp_tc(PointKernelArgs<flo
           const int m = m4 + q;
           v[q] = 0.0f;
           if (m < rows && x < T2) {
-            const int z = m / T1, y = m - z * T1;
-            const float2 c = grid_in[(int64_t)r * g.grid_cells + gz[z] + gy[y] + gx[x]];
+            const int2 zy = zyt[m];
+            const float2 c = grid_in[(int64_t)r * g.grid_cells + gz[zy.x] + gy[zy.y] + gx[x]];
             v[q] = (n & 1) ? c.y : c.x;
           }
         }
@@ -552,10 +567,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_interp_tc(PointKernelArgs<flo
           float v[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int m = m4 + q;
-            const int z = m / T1, y = m - z * T1;
-            const int dz = z - ps.x, dy = y - ps.y;
-            const bool in = m < rows && (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
+            const int2 zy = zyt[m4 + q];
+            const int dz = zy.x - ps.x, dy = zy.y - ps.y;
+            const bool in = (unsigned)dz < (unsigned)W && (unsigned)dy < (unsigned)W;
             const float wz = wts[j * S + (in ? dz : 0)];
             const float wy = wts[j * S + W + (in ? dy : 0)];
             v[q] = in ? wz * wy : 0.0f;
