@@ -75,10 +75,22 @@ struct SpreadRow {
   static constexpr int STRIDE = 3 * W;   // W is even: 8-byte aligned rows
 };
 
-// Weight-row stride of both kernels.
-template <int W>
+// FP32 spreading with 6 taps, where 32 / W = 5 rows of W lanes fill no
+// plane's 6 rows evenly (per plane a pass of 5 rows and one of 1: 56% of the
+// lanes busy), and warps that divide the taps: each warp walks its planes'
+// rows as one list (the flat layout), so a pass can finish one plane and
+// start the next (90% busy).  Staged per point: wx | the products
+// wz(plane) wy(row) of every warp's rows, warp-major.  Wider windows would
+// need too many per-lane pass offsets in registers.
+template <int W, typename Real>
+__host__ __device__ constexpr bool plane_flat_ok() {
+  return sizeof(Real) == 4 && W == 6;
+}
+
+// Weight-row stride of both kernels (the flat layout needs W + W^2 floats).
+template <int W, typename Real>
 __host__ __device__ inline int plane_wt_stride(int) {
-  return 3 * W;
+  return plane_flat_ok<W, Real>() ? (3 * W > W + W * W ? 3 * W : W + W * W) : 3 * W;
 }
 
 // Shared layout after the tiles (bp points per batch, np right-hand sides):
@@ -87,7 +99,7 @@ __host__ __device__ inline int plane_wt_stride(int) {
 //   gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
 template <int W, typename Real>
 __host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile) {
-  return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W>(nw) * sizeof(Real) +
+  return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W, Real>(nw) * sizeof(Real) +
          (size_t)(np - 1) * bp * 2 * sizeof(Real) + (size_t)(bp + 1) * sizeof(int) +
          (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) + (size_t)nw * 64 * sizeof(Real);
 }
@@ -114,7 +126,7 @@ __device__ __forceinline__ PlaneSmem<W, Real> plane_smem(unsigned char* raw, int
   const size_t rec_at = ((size_t)np_max * tile_elems * sizeof(C) + 15) & ~(size_t)15;
   s.rec = reinterpret_cast<PlaneRec<Real>*>(raw + rec_at);
   s.wt = reinterpret_cast<Real*>(s.rec + bp);
-  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * plane_wt_stride<W>(nw));
+  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * plane_wt_stride<W, Real>(nw));
   s.jt = reinterpret_cast<int*>(s.vt + (size_t)(np_max - 1) * bp);
   s.gz = reinterpret_cast<int64_t*>(s.jt + bp + (bp & 1));   // keep 8-byte alignment
   s.gy = s.gz + g.tile[0];
@@ -366,6 +378,98 @@ __device__ __forceinline__ void spread_points_fast(const PlaneSmem<W, Real>& s, 
   }
 }
 
+// Stage a batch in the flat layout (FP32, one right-hand side): thread t
+// handles point first + t; its row holds wx[W], then for warp w = 0..NW-1
+// the products wz(tap (w - z0) mod NW + u NW) wy(y) at u W + y, u < W / NW.
+template <int W, int NW>
+__device__ __forceinline__ void plane_stage_flat(const PointKernelArgs<float>& a, const PlaneSmem<W, float>& s,
+                                                 const WindowDev& win, const float2* f_in, int64_t M, int first,
+                                                 int nb, int r0, int T1, int pitch, int stride) {
+  constexpr int TAPS = W / NW;
+  const int t = threadIdx.x;
+  if (t >= nb) return;
+  const int idx = first + t;
+  const int j = a.pts.perm[idx];
+  const uint32_t loc = a.pts.local[idx];
+  const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
+  PlaneRec<float> rec;
+  rec.off = (l0 * T1 + l1) * pitch + l2;
+  rec.z = l0;
+  const float2 v0 = f_in[(int64_t)r0 * M + j];
+  rec.vx = v0.x;
+  rec.vy = v0.y;
+  float base[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) base[d] = a.pts.delta[d][idx] + (float)(win.m - win.shift);
+  float wz[W], wy[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    wz[i] = window_psi<float>(win, 0, base[0] - (float)i);
+    wy[i] = window_psi<float>(win, 1, base[1] - (float)i);
+  }
+  float* w = s.wt + (size_t)t * stride;
+#pragma unroll
+  for (int i = 0; i < W; ++i) w[i] = window_psi<float>(win, 2, base[2] - (float)i);
+#pragma unroll
+  for (int ww = 0; ww < NW; ++ww) {
+    const int i0 = (ww - l0) & (NW - 1);
+#pragma unroll
+    for (int u = 0; u < TAPS; ++u) {
+      const float z = wz[i0 + u * NW];
+#pragma unroll
+      for (int y = 0; y < W; ++y) w[W + (ww * TAPS + u) * W + y] = z * wy[y];
+    }
+  }
+  s.rec[t] = rec;
+}
+
+// The plane-owner loop over a batch staged in the flat layout: lane (ix, q)
+// takes the rows q, q + Q, ... (Q = 32 / W) of the warp's TAPS planes walked
+// as one list of TAPS W rows, column ix.
+template <int W, int NW>
+__device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s, int nb, int warp, int lane,
+                                                   int pitch, int pstride, int stride) {
+  constexpr int TAPS = W / NW;
+  constexpr int Q = 32 / W;
+  constexpr int R = TAPS * W;                  // rows of a point this warp updates
+  constexpr int KP = (R + Q - 1) / Q;          // passes
+  const int ix = lane % W, q = lane / W;
+  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile);
+  const uint32_t rec_a = (uint32_t)__cvta_generic_to_shared(s.rec);
+  const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
+  const uint32_t rowb = 4u * (uint32_t)stride;
+  uint32_t coff[KP], poff[KP];
+  bool ok[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int r = q + Q * k;
+    ok[k] = q < Q && r < R;
+    const int u = ok[k] ? r / W : 0, y = ok[k] ? r % W : 0;
+    coff[k] = 8u * (uint32_t)(u * NW * pstride + y * pitch + ix);
+    poff[k] = 4u * (uint32_t)(W + warp * R + (ok[k] ? r : 0));
+  }
+  const uint32_t wx_off = 4u * (uint32_t)ix;
+  for (int pp = 0; pp < nb; ++pp) {
+    const float4 rc = lds_f4(rec_a + 16u * (uint32_t)pp);
+    const uint32_t row = wt_a + rowb * (uint32_t)pp;
+    const float wx = lds_f1(row + wx_off);
+    const float vr = rc.x * wx, vi = rc.y * wx;
+    const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);
+    const uint32_t base = tile_a + 8u * (uint32_t)(__float_as_int(rc.z) + i0 * pstride);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      if (ok[k]) {
+        const float pw = lds_f1(row + poff[k]);
+        float2 c = lds_f2(base + coff[k]);
+        c.x = fmaf(vr, pw, c.x);
+        c.y = fmaf(vi, pw, c.y);
+        sts_f2(base + coff[k], c);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int W, int NW, typename Real>
 __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real> a, WppLayout lay) {
   using C = typename Cplx<Real>::type;
@@ -376,6 +480,8 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
   // FP32, every lane busy on every pass, rotated and permuted weight rows:
   // the single-right-hand-side loop runs on 32-bit shared addresses
   constexpr bool FAST = sizeof(Real) == 4 && EVEN && S::FULL && R::ROT && R::PERM && S::PASSES % 2 == 0;
+  // FP32, warps dividing the taps, rows that do not fill a warp: the flat layout
+  constexpr bool FLAT = EVEN && plane_flat_ok<W, Real>();
   constexpr int BP = 32 * NW;    // points per batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -410,6 +516,15 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
       for (int pb = 0; pb < sub.count; pb += BP) {
         const int nb = min(BP, sub.count - pb);
         __syncthreads();   // tile zeroed / previous batch no longer read
+        if constexpr (FLAT) {
+          if (np == 1) {
+            const int fstride = plane_wt_stride<W, Real>(NW);
+            plane_stage_flat<W, NW>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, T1, pitch, fstride);
+            __syncthreads();
+            spread_points_flat<W, NW>(s, nb, warp, lane, pitch, pstride, fstride);
+            continue;
+          }
+        }
         plane_stage_batch<W, NW, Real>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, np, BP, T1, pitch,
                                        R::STRIDE);
         __syncthreads();

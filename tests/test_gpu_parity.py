@@ -304,7 +304,9 @@ def test_wide_windows_fp64_without_plane_kernels(N, M, window, m):
     f = inputs.complex_normal(M, seed=36)
     fh = inputs.complex_normal(N, seed=37)
     a, b, info = _run(N, x, f, fh, 2.0, m, window, "fp64")
-    assert info["method"] == 4   # no tile fits: the grid-warp kernels, not the thread-per-point global ones
+    # the thread-per-point tiled kernel where an FP64 tile still fits, else
+    # the grid-warp kernels; never the global-atomic thread-per-point kernel
+    assert info["method"] in (1, 4)
     _elementwise(a, S.adjoint(x, f, N, 2.0, m, WIN[window]), 1e-12)
     _elementwise(b, S.forward(x, fh, N, 2.0, m, WIN[window]), 1e-12)
 
