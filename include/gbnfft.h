@@ -278,8 +278,9 @@ int nfft_ewald_reciprocal_sum_noalloc(int d, const int64_t* N, int precision, co
  * with d = |r_i - r_j + n L| < rcut.  r_dev: n x 3 positions (device, FP64,
  * row-major, any finite values: reduced mod L per coordinate); q_dev: n
  * charges (device, FP64).  Requires 0 < rcut < L.  When L / rcut >= 3 the
- * ions are sorted into a cell list of edge >= rcut (only the minimum image
- * of a pair is then within rcut) and the pair terms are FP32 from offsets to
+ * ions are sorted into a cell list of edge >= rcut / 2 and each ion visits
+ * the 5^3 cells around its own (only the minimum image of a pair is within
+ * rcut) and the pair terms are FP32 from offsets to
  * the cells' centres, with FP64 sums per ion; otherwise every pair and its
  * 27 nearest images are summed in FP64 (n <= 65536, else
  * NFFT_ERR_UNSUPPORTED).  The total is a fixed-order FP64 reduction.

@@ -33,19 +33,61 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;  // valid in thread 0
 }
 
-// Ewald weight exp(-c |n|^2) / |n|^2 of the flat C-order index e of I_N (0 at n = 0).
-__device__ __forceinline__ double ewald_weight(int64_t e, const EwaldGeom& g, int* a) {
-  int64_t rem = e;
-  for (int t = g.d - 1; t >= 0; --t) {
-    a[t] = (int)(rem % g.N[t]);
-    rem /= g.N[t];
-  }
-  double n2 = 0.0;
+// The Gaussian factor is separable, exp(-c |n|^2) = prod_t exp(-c n_t^2): a
+// block tabulates exp(-c k^2), k = -N_t/2 .. N_t/2 - 1, per dimension in
+// shared memory (dimension t at offset N_0 + .. + N_(t-1)) when the tables
+// fit kEwaldTabMax doubles, so an element costs two FP64 products instead of
+// an FP64 exponential (a slow pipe on this GPU).
+constexpr int kEwaldTabMax = 3072;
+
+// Fills tab (block-wide; every thread must call) and returns whether it was used.
+__device__ __forceinline__ bool ewald_tables(const EwaldGeom& g, double* tab) {
+  int total = 0;
+  for (int t = 0; t < g.d; ++t) total += g.N[t];
+  if (total > kEwaldTabMax) return false;
+  int off = 0;
   for (int t = 0; t < g.d; ++t) {
-    const double k = (double)(a[t] - g.N[t] / 2);
+    for (int i = threadIdx.x; i < g.N[t]; i += blockDim.x) {
+      const double k = (double)(i - g.N[t] / 2);
+      tab[off + i] = exp(-g.coef * k * k);
+    }
+    off += g.N[t];
+  }
+  __syncthreads();
+  return true;
+}
+
+// Ewald weight exp(-c |n|^2) / |n|^2 of the flat C-order index e of I_N (0 at
+// n = 0); a[t] gets the digit of dimension t.  tab: the tables of
+// ewald_tables, or null for the exponential itself.
+__device__ __forceinline__ double ewald_weight(int64_t e, const EwaldGeom& g, int* a, const double* tab) {
+  if (g.NN <= (int64_t)INT32_MAX) {
+    unsigned rem = (unsigned)e;
+    for (int t = g.d - 1; t >= 0; --t) {
+      a[t] = (int)(rem % (unsigned)g.N[t]);
+      rem /= (unsigned)g.N[t];
+    }
+  } else {
+    int64_t rem = e;
+    for (int t = g.d - 1; t >= 0; --t) {
+      a[t] = (int)(rem % g.N[t]);
+      rem /= g.N[t];
+    }
+  }
+  int64_t n2 = 0;
+  for (int t = 0; t < g.d; ++t) {
+    const int64_t k = a[t] - g.N[t] / 2;
     n2 += k * k;
   }
-  return n2 > 0.0 ? exp(-g.coef * n2) / n2 : 0.0;
+  if (n2 == 0) return 0.0;
+  if (!tab) return exp(-g.coef * (double)n2) / (double)n2;
+  double E = 1.0;
+  int off = 0;
+  for (int t = 0; t < g.d; ++t) {
+    E *= tab[off + a[t]];
+    off += g.N[t];
+  }
+  return E / (double)n2;
 }
 
 // Partial sums of w(n) |S(n)|^2 with S read from an fhat array (C order over I_N).
@@ -54,10 +96,12 @@ __global__ void __launch_bounds__(kThreads) k_ewald_partial_fhat(const typename 
                                                                 EwaldGeom g, double* __restrict__ partials) {
   const int64_t lo = (int64_t)blockIdx.x * kEwaldTile;
   const int64_t hi = lo + kEwaldTile < g.NN ? lo + kEwaldTile : g.NN;
+  __shared__ double tab[kEwaldTabMax];
+  const double* tp = ewald_tables(g, tab) ? tab : nullptr;
   double acc = 0.0;
   int a[kMaxDim];
   for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads) {
-    const double w = ewald_weight(e, g, a);
+    const double w = ewald_weight(e, g, a, tp);
     const double sr = (double)S[e].x, si = (double)S[e].y;
     acc += w * (sr * sr + si * si);
   }
@@ -72,10 +116,12 @@ __global__ void __launch_bounds__(kThreads) k_ewald_partial_grid(const typename 
                                                                 EwaldGeom g, double* __restrict__ partials) {
   const int64_t lo = (int64_t)blockIdx.x * kEwaldTile;
   const int64_t hi = lo + kEwaldTile < g.NN ? lo + kEwaldTile : g.NN;
+  __shared__ double tab[kEwaldTabMax];
+  const double* tp = ewald_tables(g, tab) ? tab : nullptr;
   double acc = 0.0;
   int a[kMaxDim];
   for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads) {
-    const double w = ewald_weight(e, g, a);
+    const double w = ewald_weight(e, g, a, tp);
     int64_t flat = 0;
     double factor = 1.0;
     for (int t = 0; t < g.d; ++t) {
@@ -121,9 +167,11 @@ __global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ 
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) k_force_modes(typename Cplx<Real>::type* __restrict__ modes, EwaldGeom g) {
   using C = typename Cplx<Real>::type;
+  __shared__ double tab[kEwaldTabMax];
+  const double* tp = ewald_tables(g, tab) ? tab : nullptr;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < g.NN; e += (int64_t)gridDim.x * kThreads) {
     int a[kMaxDim];
-    const double w = ewald_weight(e, g, a);
+    const double w = ewald_weight(e, g, a, tp);
     const C S = modes[e];
     const double sr = (double)S.x, si = (double)S.y;
 #pragma unroll

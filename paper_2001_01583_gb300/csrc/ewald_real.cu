@@ -5,14 +5,19 @@
 //
 // Two forms, chosen by the box:
 //   - cell list (L / r_c >= 3): the box is cut into nc^3 cells of edge
-//     h = L / nc >= r_c, the ions are counting-sorted by cell, and each ion
-//     visits the 27 cells around its own.  With r_c <= L / 3 only the minimum
-//     image of a pair can be within r_c, and it is found exactly once.  Each
-//     ion is stored as its offset from its cell's centre in FP32 (|offset| <=
-//     h / 2), so a separation (d h + o_j - o_i, d in {-1, 0, 1}) carries about
-//     1e-6 of absolute error instead of FP32's 1e-5 on box coordinates; the
-//     pair term erfc(alpha r) / r is FP32, each neighbour cell's sum is added
-//     to the ion's FP64 potential;
+//     h = L / nc >= r_c / 2, the ions are counting-sorted by cell, and each
+//     ion visits the 5^3 cells around its own (a partner within r_c is at
+//     most two cells away).  That is 125 h^3 ~ 15.6 r_c^3 of candidates
+//     instead of 27 r_c^3 with cells of edge r_c: the kernel issues one pair
+//     term per candidate and warp (every lane takes the same candidate, so
+//     erfc runs whenever one lane of the 32 accepts), which made the kernel
+//     issue-bound.  With r_c <= L / 3 only the minimum image of a pair can be
+//     within r_c, and it is found exactly once.  Each ion is stored as its
+//     offset from its cell's centre in FP32 (|offset| <= h / 2), so a
+//     separation (d h + o_j - o_i, |d| <= 2) carries about 1e-6 of absolute
+//     error instead of FP32's 1e-5 on box coordinates; the pair term
+//     erfc(alpha r) / r is FP32, each neighbour cell's sum is added to the
+//     ion's FP64 potential;
 //   - all pairs (smaller boxes): the minimum image of every pair plus the 26
 //     shifts by L, all in FP64, which is the definition itself (r_c < L).
 // The energy 1/2 sum_i q_i phi_i is reduced in FP64 in a fixed order (block
@@ -32,6 +37,7 @@ namespace gbnfft {
 namespace {
 
 constexpr int kRsThreads = 256;
+constexpr int kRsReach = 2;   // neighbour cells per side (cell edge >= r_c / kRsReach)
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
@@ -111,11 +117,11 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_cells(int n, int nc, float h,
     const int cz = cell % nc, cy = (cell / nc) % nc, cx = cell / (nc * nc);
     double phi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
     const float c2 = kTwoOverSqrtPiF * alpha, a2 = alpha * alpha;
-    for (int dx = -1; dx <= 1; ++dx) {
+    for (int dx = -kRsReach; dx <= kRsReach; ++dx) {
       const int x = cx + dx < 0 ? cx + dx + nc : (cx + dx >= nc ? cx + dx - nc : cx + dx);
-      for (int dy = -1; dy <= 1; ++dy) {
+      for (int dy = -kRsReach; dy <= kRsReach; ++dy) {
         const int y = cy + dy < 0 ? cy + dy + nc : (cy + dy >= nc ? cy + dy - nc : cy + dy);
-        for (int dz = -1; dz <= 1; ++dz) {
+        for (int dz = -kRsReach; dz <= kRsReach; ++dz) {
           const int z = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
           const int nb = (x * nc + y) * nc + z;
           const float sx = dx * h - pi.x, sy = dy * h - pi.y, sz = dz * h - pi.z;
@@ -221,7 +227,9 @@ int real_space_impl(int64_t n, const double* r_dev, const double* q_dev, double 
   *energy = 0.0;
   if (n == 0) return NFFT_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int nc = (int)std::floor(L / rcut) < 3 ? 1 : std::min((int)std::floor(L / rcut), 256);
+  // cells of edge L / nc >= rcut / kRsReach (at least 2 kRsReach + 1 of them
+  // per side, so the neighbour cells are distinct); L / rcut < 3: all pairs
+  const int nc = (int)std::floor(L / rcut) < 3 ? 1 : std::min((int)std::floor(kRsReach * L / rcut), 256);
   if (nc == 1 && n > 65536) return NFFT_ERR_UNSUPPORTED;   // the all-pairs form is O(n^2)
   const int ni = (int)n;
   const int blocks = (ni + kRsThreads - 1) / kRsThreads;

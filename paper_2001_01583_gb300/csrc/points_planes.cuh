@@ -449,21 +449,41 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
     poff[k] = 4u * (uint32_t)(W + warp * R + (ok[k] ? r : 0));
   }
   const uint32_t wx_off = 4u * (uint32_t)ix;
+  // the next point's record, column weight and products are loaded one point
+  // ahead; a point's cells are all loaded before any is written back (the
+  // passes touch distinct cells)
+  float4 nrc = lds_f4(rec_a);
+  float nwx = lds_f1(wt_a + wx_off);
+  float npw[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) npw[k] = ok[k] ? lds_f1(wt_a + poff[k]) : 0.0f;
   for (int pp = 0; pp < nb; ++pp) {
-    const float4 rc = lds_f4(rec_a + 16u * (uint32_t)pp);
-    const uint32_t row = wt_a + rowb * (uint32_t)pp;
-    const float wx = lds_f1(row + wx_off);
+    const float4 rc = nrc;
+    const float wx = nwx;
+    float pw[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) pw[k] = npw[k];
+    {
+      const uint32_t pn = (uint32_t)min(pp + 1, nb - 1);
+      const uint32_t row = wt_a + rowb * pn;
+      nrc = lds_f4(rec_a + 16u * pn);
+      nwx = lds_f1(row + wx_off);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) npw[k] = ok[k] ? lds_f1(row + poff[k]) : 0.0f;
+    }
     const float vr = rc.x * wx, vi = rc.y * wx;
     const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);
     const uint32_t base = tile_a + 8u * (uint32_t)(__float_as_int(rc.z) + i0 * pstride);
+    float2 c[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+      if (ok[k]) c[k] = lds_f2(base + coff[k]);
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       if (ok[k]) {
-        const float pw = lds_f1(row + poff[k]);
-        float2 c = lds_f2(base + coff[k]);
-        c.x = fmaf(vr, pw, c.x);
-        c.y = fmaf(vi, pw, c.y);
-        sts_f2(base + coff[k], c);
+        c[k].x = fmaf(vr, pw[k], c[k].x);
+        c[k].y = fmaf(vi, pw[k], c[k].y);
+        sts_f2(base + coff[k], c[k]);
       }
     }
     __syncwarp();

@@ -97,64 +97,99 @@ __device__ __forceinline__ double load_coord(const double* x, int64_t j, int d, 
   return v;
 }
 
+// Points per thread of the two point passes: a thread's points are kSortThreads
+// apart (coalesced per slot) and every load and atomic of its points is
+// issued before any result is used, so each thread keeps kSortPer memory
+// requests in flight (the passes are bound by memory latency).
+constexpr int kSortThreads = 256;
+constexpr int kSortPer = 4;
+
 template <typename Real>
-__global__ void k_bin_count(SortArgs s, int* __restrict__ bin_count, int2* __restrict__ bin_rank) {
-  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = gidx < s.total_points;
-  int bin = -1;
-  if (valid) {
+__global__ void __launch_bounds__(kSortThreads) k_bin_count(SortArgs s, int* __restrict__ bin_count,
+                                                            int2* __restrict__ bin_rank) {
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortPer) + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int bin[kSortPer];
+  bool any_bad = false;
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    bin[k] = -1;
+    if (gidx < s.total_points) {
+      const int item = find_item<int64_t>(s.point_offsets, s.n_items, gidx);
+      const ItemDev& it = s.items[item];
+      const int64_t j = gidx - it.point_offset;
+      const double* x = s.x_override ? s.x_override : it.x;
+      const GridGeom& g = it.geom;
+      bool bad = false;
+      int local = 0;
+      for (int t = 0; t < g.d; ++t) {
+        int c;
+        Real dl;
+        reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
+        local = local * g.nbins[t] + c / g.bin[t];
+      }
+      any_bad |= bad;
+      bin[k] = it.bin_offset + local;
+    }
+  }
+  if (any_bad) atomicOr(s.err, 1);
+  // warp-aggregated ranks: lanes with the same bin share one atomic; the
+  // atomics of all slots are in flight before their results are read
+  unsigned peers[kSortPer];
+  int got[kSortPer];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    peers[k] = __match_any_sync(0xffffffffu, bin[k]);
+    got[k] = 0;
+    if (bin[k] >= 0 && lane == __ffs(peers[k]) - 1) got[k] = atomicAdd(&bin_count[bin[k]], __popc(peers[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int first = __shfl_sync(peers[k], got[k], __ffs(peers[k]) - 1);
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    if (bin[k] >= 0) bin_rank[gidx] = make_int2(bin[k], first + __popc(peers[k] & ((1u << lane) - 1u)));
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kSortThreads) k_scatter(SortArgs s, const int* __restrict__ bin_start,
+                                                          const int2* __restrict__ bin_rank, int* __restrict__ perm,
+                                                          uint32_t* __restrict__ local, Real* d0, Real* d1, Real* d2) {
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortPer) + threadIdx.x;
+  Real* dst[3] = {d0, d1, d2};
+  int2 br[kSortPer];
+  int pos[kSortPer];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    br[k] = gidx < s.total_points ? bin_rank[gidx] : make_int2(-1, 0);
+  }
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) pos[k] = br[k].x >= 0 ? bin_start[br[k].x] + br[k].y : -1;
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    if (pos[k] < 0) continue;
     const int item = find_item<int64_t>(s.point_offsets, s.n_items, gidx);
     const ItemDev& it = s.items[item];
     const int64_t j = gidx - it.point_offset;
     const double* x = s.x_override ? s.x_override : it.x;
     const GridGeom& g = it.geom;
     bool bad = false;
-    int local = 0;
+    uint32_t packed = 0;
+    const int bits = local_bits(g.d);
     for (int t = 0; t < g.d; ++t) {
       int c;
       Real dl;
       reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
-      local = local * g.nbins[t] + c / g.bin[t];
+      const uint32_t lc = (uint32_t)(c % g.bin[t]);
+      packed |= (g.d == 1) ? lc : (lc << (bits * t));
+      dst[t][pos[k]] = dl;
     }
-    if (bad) atomicOr(s.err, 1);
-    bin = it.bin_offset + local;
+    perm[pos[k]] = (int)j;
+    local[pos[k]] = packed;
   }
-  // warp-aggregated rank: lanes with the same bin share one atomic
-  const unsigned peers = __match_any_sync(0xffffffffu, bin);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (valid && lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  if (valid) bin_rank[gidx] = make_int2(bin, base + __popc(peers & ((1u << lane) - 1u)));
-}
-
-template <typename Real>
-__global__ void k_scatter(SortArgs s, const int* __restrict__ bin_start, const int2* __restrict__ bin_rank,
-                          int* __restrict__ perm, uint32_t* __restrict__ local, Real* d0, Real* d1, Real* d2) {
-  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gidx >= s.total_points) return;
-  const int item = find_item<int64_t>(s.point_offsets, s.n_items, gidx);
-  const ItemDev& it = s.items[item];
-  const int64_t j = gidx - it.point_offset;
-  const double* x = s.x_override ? s.x_override : it.x;
-  const GridGeom& g = it.geom;
-  const int2 br = bin_rank[gidx];
-  const int pos = bin_start[br.x] + br.y;
-  bool bad = false;
-  uint32_t packed = 0;
-  const int bits = local_bits(g.d);
-  Real* dst[3] = {d0, d1, d2};
-  for (int t = 0; t < g.d; ++t) {
-    int c;
-    Real dl;
-    reduce_coord<Real>(load_coord(x, j, g.d, t, bad), g.n[t], c, dl);
-    const uint32_t lc = (uint32_t)(c % g.bin[t]);
-    packed |= (g.d == 1) ? lc : (lc << (bits * t));
-    dst[t][pos] = dl;
-  }
-  perm[pos] = (int)j;
-  local[pos] = packed;
 }
 
 // Exclusive scan of n ints with one block of 1024 threads: each thread scans a
@@ -279,7 +314,8 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <typename Real>
 cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st) {
   if (s.total_points == 0) return cudaSuccess;
-  k_bin_count<Real><<<blocks_for(s.total_points, 256), 256, 0, st>>>(s, bin_count, bin_rank);
+  k_bin_count<Real><<<blocks_for(s.total_points, kSortThreads * kSortPer), kSortThreads, 0, st>>>(s, bin_count,
+                                                                                                  bin_rank);
   return cudaGetLastError();
 }
 
@@ -308,8 +344,8 @@ template <typename Real>
 cudaError_t launch_scatter(const SortArgs& s, const int* bin_start, const int2* bin_rank, int* perm, uint32_t* local,
                            Real* const* delta, cudaStream_t st) {
   if (s.total_points == 0) return cudaSuccess;
-  k_scatter<Real><<<blocks_for(s.total_points, 256), 256, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0],
-                                                                   delta[1], delta[2]);
+  k_scatter<Real><<<blocks_for(s.total_points, kSortThreads * kSortPer), kSortThreads, 0, st>>>(
+      s, bin_start, bin_rank, perm, local, delta[0], delta[1], delta[2]);
   return cudaGetLastError();
 }
 
