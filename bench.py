@@ -19,7 +19,7 @@ m = 4, sigma = 2, on two point sets (uniform, and 32 Gaussian clusters of std
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload picker|config|small|sparse|profile|batch|1d|fluorite|fig13|fig16]
                   [--precision fp32|fp64] [--no-autotune] [--no-cpu-baseline] [--no-fp64-form]
-                  [--tensor-spread] [--tensor-interp]
+                  [--tensor-spread] [--tensor-interp] [--owner-spread]
 
 "--workload small" (N = 64^3, M = 5e5, uniform only) is the case profiled
 with ncu's multi-pass sections.  "--workload fig13" and "fig16" sweep the
@@ -703,6 +703,8 @@ def run_batch(args, wl, rank, world):
         outs_f = [torch.empty_like(f) for f in fs]
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     b = Batch([dict(N=it["N"], M=it["M"], nrhs=it["nrhs"]) for it in items], args.precision, stream=stream)
+    if args.owner_spread:
+        b.set_option(_lib.OPT_OWNER_SPREAD, 1)
     with torch.cuda.stream(stream):
         b.set_points(xs)
         if args.autotune:
@@ -739,6 +741,7 @@ def run_batch(args, wl, rank, world):
             "data": "synthetic",
             "config": {"workload": wl["name"], "points_per_step_per_gpu": points, "items": len(items),
                        "precision": args.precision, "autotuned": bool(args.autotune),
+                       "owner_spread": bool(args.owner_spread),
                        "l2": "flushed between timed steps (512 MB write outside the step events)"},
             "gpu_launches": launches_timed, "clocks": clocks}
     real = 4 if args.precision == "fp32" else 8
@@ -988,6 +991,8 @@ def main():
                     help="plan workloads: spread the dense bins on the tensor cores (NFFT_OPT_TENSOR_SPREAD)")
     ap.add_argument("--tensor-interp", action="store_true",
                     help="plan workloads: interpolate the dense bins on the tensor cores (NFFT_OPT_TENSOR_INTERP)")
+    ap.add_argument("--owner-spread", action="store_true",
+                    help="batch workload: spread sparse bins by their cells' owners (NFFT_OPT_OWNER_SPREAD)")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip timing the plain FP64 form of the plan workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")

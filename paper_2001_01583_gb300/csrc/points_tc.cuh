@@ -261,30 +261,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
     for (int r = 0; r < call.nrhs && !failed; ++r) {
       int k = 0;          // chunks of this subproblem so far
       bool copy = true;   // the next fold starts the tile
+      // thread (p, i) stages tap i of point p of every chunk; its point's
+      // offsets, cell and index are loaded one chunk ahead (while the block
+      // builds the current chunk) and its value after the build, so the
+      // staging reads registers instead of waiting on global memory
+      const int sp_p = tid >> 3, sp_i = tid & 7;
+      const float sh = (float)(win.m - win.shift);
+      float pd[3] = {0.0f, 0.0f, 0.0f};
+      uint32_t ploc = 0;
+      int pperm = 0;
+      float2 pf = make_float2(0.0f, 0.0f);
+      auto fetch = [&](int start) {
+        if (start < sub.count && sp_p < sub.count - start) {
+          const int idx = sub.start + start + sp_p;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) pd[d] = a.pts.delta[d][idx];
+          ploc = a.pts.local[idx];
+          pperm = a.pts.perm[idx];
+        }
+      };
+      auto fetch_value = [&](int start) {
+        if (sp_i == 0 && start < sub.count && sp_p < sub.count - start) pf = f_in[(int64_t)r * it.M + pperm];
+      };
+      fetch(0);
+      fetch_value(0);
       for (int pb = 0; pb < sub.count; pb += kTcChunk, ++k) {
         const int nb = min(kTcChunk, sub.count - pb);
         const int buf = (int)(cc & 1u);
         // stage: thread (p, i) evaluates tap i of point p in each dimension
-        {
-          const int p = tid >> 3, i = tid & 7;
-          if (p < nb) {
-            const int idx = sub.start + pb + p;
-            const float sh = (float)(win.m - win.shift);
-            if (i < W) {
+        if (sp_p < nb) {
+          if (sp_i < W) {
 #pragma unroll
-              for (int d = 0; d < 3; ++d)
-                wts[p * S + d * W + i] = window_psi<float>(win, d, a.pts.delta[d][idx] + sh - (float)i);
-            }
-            if (i == 0) {
-              const uint32_t loc = a.pts.local[idx];
-              pos[p] = make_int4(unpack_local(loc, 3, 0), unpack_local(loc, 3, 1), unpack_local(loc, 3, 2), 0);
-              fv[p] = f_in[(int64_t)r * it.M + a.pts.perm[idx]];
-            }
-          } else if (i == 0) {
-            pos[p] = make_int4(-1024, -1024, -1024, 0);   // past the chunk: a zero column of A and row of B
-            fv[p] = make_float2(0.0f, 0.0f);
+            for (int d = 0; d < 3; ++d) wts[sp_p * S + d * W + sp_i] = window_psi<float>(win, d, pd[d] + sh - (float)sp_i);
           }
+          if (sp_i == 0) {
+            pos[sp_p] = make_int4(unpack_local(ploc, 3, 0), unpack_local(ploc, 3, 1), unpack_local(ploc, 3, 2), 0);
+            fv[sp_p] = pf;
+          }
+        } else if (sp_i == 0) {
+          pos[sp_p] = make_int4(-1024, -1024, -1024, 0);   // past the chunk: a zero column of A and row of B
+          fv[sp_p] = make_float2(0.0f, 0.0f);
         }
+        fetch(pb + kTcChunk);
         __syncthreads();
         // the MMAs that last read this buffer and this partial (chunk cc - 2)
         // must be done; a partial of this subproblem is then added to the tile
@@ -342,6 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
             tc_store_split(bHi + off, bLo + off, v);
           }
         }
+        fetch_value(pb + kTcChunk);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
