@@ -186,7 +186,14 @@ def _cpu_baseline(args, wl, rank, world):
 # hash to `sources`; otherwise the traffic is reported null.  Keyed by
 # (workload, stage); "scaled" says when a smaller case was captured and its
 # bytes scaled by the units processed.
-TRAFFIC = {}
+TRAFFIC = {
+    # the spreading launch of the largest configuration (N = 256^3, M = 3e7 clustered, 6 taps, autotuned),
+    # profiles/launches_largest_3d_n256_m3e7.md
+    ("picker", "spread"): {"bytes": 3587478272,
+                           "sources": "54ac0cea891ef93f18e44450327343cb1cfdf2ce5c3528abbbe2ec22395a5681"},
+    ("picker", "interp"): {"bytes": 2486656512,
+                           "sources": "54ac0cea891ef93f18e44450327343cb1cfdf2ce5c3528abbbe2ec22395a5681"},
+}
 TRAFFIC_SOURCES = ("points_planes.cuh", "points_tiled.cuh", "points_gm.cuh", "kernels.h", "common.cuh")
 
 
