@@ -288,6 +288,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
       for (int pb = 0; pb < sub.count; pb += kTcChunk, ++k) {
         const int nb = min(kTcChunk, sub.count - pb);
         const int buf = (int)(cc & 1u);
+        // the MMAs that last read this buffer and this partial (chunk cc - 2)
+        // must be done; chunks 2p and 2p + 1 accumulate into partial p & 1, so
+        // the wait completes pair (k - 3) / 2 at odd k >= 3, whose partial
+        // pair (k + 1) / 2 reuses from chunk k + 1 on: it is added to the tile
+        // now (the previous chunk's build is over: every thread passed its
+        // barrier, so the staging tables below are free as well)
+        bool ok = true;
+        if (cc >= 2) ok = tc_wait(bar_a[buf], ((cc - 2) >> 1) & 1u);
+        ok = __all_sync(0xffffffffu, ok);   // the fold's tensor-memory accesses are warp-wide
+        if (ok && k >= 3 && (k & 1)) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          tc_fold(tmem, warp, N, (uint32_t)(((k - 3) >> 1) & 1) * part_cols, sum_col, copy);
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        if (k >= 3 && (k & 1)) copy = false;
         // stage: thread (p, i) evaluates tap i of point p in each dimension
         if (sp_p < nb) {
           if (sp_i < W) {
@@ -303,23 +318,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_spread_tc(PointKernelArgs<flo
           fv[sp_p] = make_float2(0.0f, 0.0f);
         }
         fetch(pb + kTcChunk);
-        __syncthreads();
-        // the MMAs that last read this buffer and this partial (chunk cc - 2)
-        // must be done; a partial of this subproblem is then added to the tile
-        bool ok = true;
-        if (cc >= 2) ok = tc_wait(bar_a[buf], ((cc - 2) >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
           failed = true;
           break;
-        }
-        // chunks 2p and 2p + 1 accumulate into partial p & 1; the wait above
-        // (for chunk k - 2) completes pair (k - 3) / 2 at odd k >= 3, whose
-        // partial pair (k + 1) / 2 reuses from chunk k + 1 on
-        if (k >= 3 && (k & 1)) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          tc_fold(tmem, warp, N, (uint32_t)(((k - 3) >> 1) & 1) * part_cols, sum_col, copy);
-          copy = false;
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         // build A (rows of (z, y)) and B (rows of (x, re / im)) of the chunk:
         // item e < 1024: A row e & 127, points 4 (e >> 7) ..; then B
