@@ -132,14 +132,14 @@ const void* planes_kernel<float>(int taps, int warps, bool spread) { return plan
 template <>
 const void* planes_kernel<double>(int taps, int warps, bool spread) { return planes_kernel_f64(taps, warps, spread); }
 template <typename Real>
-size_t planes_table_bytes(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes(int taps, int bp, int np, int nw, const int* tile, bool spread);
 template <>
-size_t planes_table_bytes<float>(int taps, int bp, int np, int nw, const int* tile) {
-  return planes_table_bytes_f32(taps, bp, np, nw, tile);
+size_t planes_table_bytes<float>(int taps, int bp, int np, int nw, const int* tile, bool spread) {
+  return planes_table_bytes_f32(taps, bp, np, nw, tile, spread);
 }
 template <>
-size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* tile) {
-  return planes_table_bytes_f64(taps, bp, np, nw, tile);
+size_t planes_table_bytes<double>(int taps, int bp, int np, int nw, const int* tile, bool spread) {
+  return planes_table_bytes_f64(taps, bp, np, nw, tile, spread);
 }
 
 }  // namespace
@@ -419,8 +419,8 @@ int Engine::build_layout() {
       for (int t = 0; t < 3; ++t) tile[t] = bin[t] + c.taps - 1;
       const size_t wt = (size_t)tile[0] * tile[1] * choose_pitch(tile[2], c.taps, (int)csize) * csize;
       if (c.taps <= 16) return wt + 32768 <= budget;
-      const size_t tables = precision == NFFT_FP64 ? planes_table_bytes_f64(c.taps, 64, 1, 2, tile)
-                                                   : planes_table_bytes_f32(c.taps, 64, 1, 2, tile);
+      const size_t tables = precision == NFFT_FP64 ? planes_table_bytes_f64(c.taps, 64, 1, 2, tile, true)
+                                                   : planes_table_bytes_f32(c.taps, 64, 1, 2, tile, true);
       return wt + tables <= smem_optin;
     };
     bool planes = false;
@@ -917,7 +917,7 @@ int Engine::run_planes(const KClass& kc, PointKernelArgs<Real>& a, bool spread, 
   const size_t rows = (size_t)kc.tile[0] * kc.tile[1];
   const size_t tbytes = rows * (size_t)kc.pitch * csize;
   auto smem_of = [&](int nw, int np) {
-    return (size_t)np * tbytes + planes_table_bytes<Real>(W, 32 * nw, np, nw, kc.tile);
+    return (size_t)np * tbytes + planes_table_bytes<Real>(W, 32 * nw, np, nw, kc.tile, spread);
   };
   int np = 1;
   while (np < max_nrhs && smem_of(8, np + 1) <= smem_per_sm / 2) ++np;

@@ -125,8 +125,8 @@ const void* wpp_kernel_f64(int d, int taps, bool spread);
 constexpr int kMaxPlaneTaps = 26;   // widest window of the 3-D shared-tile kernels
 const void* planes_kernel_f32(int taps, int warps, bool spread);
 const void* planes_kernel_f64(int taps, int warps, bool spread);
-size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile);
-size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile, bool spread);
+size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile, bool spread);
 
 // 3-D spreading on the tensor cores (points_tc.cuh): FP32, taps 4, 6 or 8,
 // tiles of at most 128 (z, y) rows and 2 T2 <= kTcMaxColsHost real columns;

@@ -11,12 +11,12 @@ namespace gbnfft {
     return reinterpret_cast<const void*>(&k_interp_groups<W, R>);
 #define GBNFFT_PLANE_BYTES(W, R) \
   case W:                        \
-    return plane_table_bytes<W, R>(bp, np, nw, tile);
+    return plane_table_bytes<W, R>(bp, np, nw, tile, spread);
 
 const void* planes_kernel_f32_w18_22(int taps, int warps, bool spread);
-size_t planes_table_bytes_f32_w18_22(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes_f32_w18_22(int taps, int bp, int np, int nw, const int* tile, bool spread);
 const void* planes_kernel_f32_w24_26(int taps, int warps, bool spread);
-size_t planes_table_bytes_f32_w24_26(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes_f32_w24_26(int taps, int bp, int np, int nw, const int* tile, bool spread);
 
 const void* planes_spread_f32_uneven(int taps, int warps);
 
@@ -37,9 +37,9 @@ const void* planes_kernel_f32(int taps, int warps, bool spread) {
   }
 }
 
-size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile) {
-  if (taps >= 24) return planes_table_bytes_f32_w24_26(taps, bp, np, nw, tile);
-  if (taps >= 18) return planes_table_bytes_f32_w18_22(taps, bp, np, nw, tile);
+size_t planes_table_bytes_f32(int taps, int bp, int np, int nw, const int* tile, bool spread) {
+  if (taps >= 24) return planes_table_bytes_f32_w24_26(taps, bp, np, nw, tile, spread);
+  if (taps >= 18) return planes_table_bytes_f32_w18_22(taps, bp, np, nw, tile, spread);
   switch (taps) {
     GBNFFT_PLANE_TAPS_NARROW(GBNFFT_PLANE_BYTES, float)
     default:

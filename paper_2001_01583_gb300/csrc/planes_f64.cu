@@ -11,10 +11,10 @@ namespace gbnfft {
     return reinterpret_cast<const void*>(&k_interp_groups<W, R>);
 #define GBNFFT_PLANE_BYTES(W, R) \
   case W:                        \
-    return plane_table_bytes<W, R>(bp, np, nw, tile);
+    return plane_table_bytes<W, R>(bp, np, nw, tile, spread);
 
 const void* planes_kernel_f64_w18_20(int taps, int warps, bool spread);
-size_t planes_table_bytes_f64_w18_20(int taps, int bp, int np, int nw, const int* tile);
+size_t planes_table_bytes_f64_w18_20(int taps, int bp, int np, int nw, const int* tile, bool spread);
 
 const void* planes_spread_f64_uneven(int taps, int warps);
 
@@ -34,8 +34,8 @@ const void* planes_kernel_f64(int taps, int warps, bool spread) {
   }
 }
 
-size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile) {
-  if (taps >= 18) return planes_table_bytes_f64_w18_20(taps, bp, np, nw, tile);
+size_t planes_table_bytes_f64(int taps, int bp, int np, int nw, const int* tile, bool spread) {
+  if (taps >= 18) return planes_table_bytes_f64_w18_20(taps, bp, np, nw, tile, spread);
   switch (taps) {
     GBNFFT_PLANE_TAPS_NARROW(GBNFFT_PLANE_BYTES, double)
     default:

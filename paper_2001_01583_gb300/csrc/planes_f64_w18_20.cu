@@ -11,7 +11,7 @@ namespace gbnfft {
     return reinterpret_cast<const void*>(&k_interp_groups<W, R>);
 #define GBNFFT_PLANE_BYTES(W, R) \
   case W:                        \
-    return plane_table_bytes<W, R>(bp, np, nw, tile);
+    return plane_table_bytes<W, R>(bp, np, nw, tile, spread);
 
 const void* planes_kernel_f64_w18_20(int taps, int warps, bool spread) {
   if (spread) {
@@ -28,7 +28,7 @@ const void* planes_kernel_f64_w18_20(int taps, int warps, bool spread) {
   }
 }
 
-size_t planes_table_bytes_f64_w18_20(int taps, int bp, int np, int nw, const int* tile) {
+size_t planes_table_bytes_f64_w18_20(int taps, int bp, int np, int nw, const int* tile, bool spread) {
   switch (taps) {
     GBNFFT_PLANE_TAPS_W18_20(GBNFFT_PLANE_BYTES, double)
     default:

@@ -87,10 +87,10 @@ __host__ __device__ constexpr bool plane_flat_ok() {
   return sizeof(Real) == 4 && W == 6;
 }
 
-// Weight-row stride of both kernels (the flat layout needs W + W^2 floats).
+// Weight-row stride (the flat spreading layout needs W + W^2 floats).
 template <int W, typename Real>
-__host__ __device__ inline int plane_wt_stride(int) {
-  return plane_flat_ok<W, Real>() ? (3 * W > W + W * W ? 3 * W : W + W * W) : 3 * W;
+__host__ __device__ inline int plane_wt_stride(bool spread) {
+  return spread && plane_flat_ok<W, Real>() ? (3 * W > W + W * W ? 3 * W : W + W * W) : 3 * W;
 }
 
 // Shared layout after the tiles (bp points per batch, np right-hand sides):
@@ -98,8 +98,8 @@ __host__ __device__ inline int plane_wt_stride(int) {
 //   vt[np - 1][bp] complex (right-hand sides after the first) | jt[bp] int |
 //   gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
 template <int W, typename Real>
-__host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile) {
-  return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W, Real>(nw) * sizeof(Real) +
+__host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile, bool spread) {
+  return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W, Real>(spread) * sizeof(Real) +
          (size_t)(np - 1) * bp * 2 * sizeof(Real) + (size_t)(bp + 1) * sizeof(int) +
          (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) + (size_t)nw * 64 * sizeof(Real);
 }
@@ -119,14 +119,14 @@ struct PlaneSmem {
 
 template <int W, typename Real>
 __device__ __forceinline__ PlaneSmem<W, Real> plane_smem(unsigned char* raw, int np_max, int tile_elems, int bp,
-                                                         int nw, const GridGeom& g) {
+                                                         int nw, const GridGeom& g, bool spread) {
   using C = typename Cplx<Real>::type;
   PlaneSmem<W, Real> s;
   s.tile = reinterpret_cast<C*>(raw);
   const size_t rec_at = ((size_t)np_max * tile_elems * sizeof(C) + 15) & ~(size_t)15;
   s.rec = reinterpret_cast<PlaneRec<Real>*>(raw + rec_at);
   s.wt = reinterpret_cast<Real*>(s.rec + bp);
-  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * plane_wt_stride<W, Real>(nw));
+  s.vt = reinterpret_cast<C*>(s.wt + (size_t)bp * plane_wt_stride<W, Real>(spread));
   s.jt = reinterpret_cast<int*>(s.vt + (size_t)(np_max - 1) * bp);
   s.gz = reinterpret_cast<int64_t*>(s.jt + bp + (bp & 1));   // keep 8-byte alignment
   s.gy = s.gz + g.tile[0];
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
     C* grid = static_cast<C*>(it.grid);
     const int T1 = g.tile[1], T2 = g.tile[2];
     const int rows = g.tile[0] * T1;
-    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, NW, g);
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, NW, g, true);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
     for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
         __syncthreads();   // tile zeroed / previous batch no longer read
         if constexpr (FLAT) {
           if (np == 1) {
-            const int fstride = plane_wt_stride<W, Real>(NW);
+            const int fstride = plane_wt_stride<W, Real>(true);
             plane_stage_flat<W, NW>(a, s, it.win, f_in, it.M, sub.start + pb, nb, r0, T1, pitch, fstride);
             __syncthreads();
             spread_points_flat<W, NW>(s, nb, warp, lane, pitch, pstride, fstride);
@@ -728,129 +728,6 @@ __device__ __forceinline__ void interp_points_fast(const PlaneSmem<W, Real>& s, 
   }
 }
 
-// Stage a batch for flat interpolation (FP32, 6 taps): thread t handles point
-// first + t; its row holds wx[W], then the products wz(z) wy(y) at z W + y.
-template <int W>
-__device__ __forceinline__ void plane_stage_interp_flat(const PointKernelArgs<float>& a,
-                                                        const PlaneSmem<W, float>& s, const WindowDev& win,
-                                                        int first, int nb, int T1, int pitch, int stride) {
-  const int t = threadIdx.x;
-  if (t >= nb) return;
-  const int idx = first + t;
-  const uint32_t loc = a.pts.local[idx];
-  const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
-  s.jt[t] = a.pts.perm[idx];
-  PlaneRec<float> rec;
-  rec.off = (l0 * T1 + l1) * pitch + l2;
-  rec.z = l0;
-  rec.vx = 0.0f;
-  rec.vy = 0.0f;
-  float base[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) base[d] = a.pts.delta[d][idx] + (float)(win.m - win.shift);
-  float wz[W], wy[W];
-#pragma unroll
-  for (int i = 0; i < W; ++i) {
-    wz[i] = window_psi<float>(win, 0, base[0] - (float)i);
-    wy[i] = window_psi<float>(win, 1, base[1] - (float)i);
-  }
-  float* w = s.wt + (size_t)t * stride;
-#pragma unroll
-  for (int i = 0; i < W; ++i) w[i] = window_psi<float>(win, 2, base[2] - (float)i);
-#pragma unroll
-  for (int z = 0; z < W; ++z)
-#pragma unroll
-    for (int y = 0; y < W; ++y) w[W + z * W + y] = wz[z] * wy[y];
-  s.rec[t] = rec;
-}
-
-// Flat interpolation of a staged batch (FP32, 6 taps, one right-hand side):
-// a warp takes 4 points at a time, one after another; lane (ix, q) reads
-// cell ix of rows q, q + Q, ... of the point's W planes walked as one list of
-// W^2 rows (Q = 32 / W = 5 rows per pass: 8 passes, 90% of the lanes busy),
-// each weighted by its staged product wz wy; times wx that is the lane's
-// share of the point's value, and the transposed butterfly of
-// interp_points_fast reduces the 4 points' shares at once.
-template <int W>
-__device__ __forceinline__ void interp_points_flat(const PlaneSmem<W, float>& s, int nb, int warp, int nw,
-                                                   int lane, int pitch, int pstride, int stride, float2* out) {
-  constexpr int Q = 32 / W;
-  constexpr int R = W * W;
-  constexpr int KP = (R + Q - 1) / Q;
-  constexpr int PG = 4;
-  const int ix = lane % W, q = lane / W;
-  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile);
-  const uint32_t off_a = (uint32_t)__cvta_generic_to_shared(s.rec) + 8u;   // PlaneRec<float>::off
-  const uint32_t jt_a = (uint32_t)__cvta_generic_to_shared(s.jt);
-  const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
-  const uint32_t rowb = 4u * (uint32_t)stride;
-  uint32_t coff[KP], poff[KP];
-  bool ok[KP];
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    const int r = q + Q * k;
-    ok[k] = q < Q && r < R;
-    const int z = ok[k] ? r / W : 0, y = ok[k] ? r % W : 0;
-    coff[k] = 8u * (uint32_t)(z * pstride + y * pitch + ix);
-    poff[k] = 4u * (uint32_t)(W + (ok[k] ? r : 0));
-  }
-  const bool active = q < Q;
-  const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
-  for (int p0 = warp * PG; p0 < nb; p0 += nw * PG) {
-    float v[2 * PG];
-#pragma unroll
-    for (int g = 0; g < PG; ++g) {
-      const uint32_t pp = (uint32_t)min(p0 + g, nb - 1);   // past the batch: recomputed, not written
-      const uint32_t row = wt_a + rowb * pp;
-      const uint32_t base = tile_a + 8u * (uint32_t)lds_i1(off_a + 16u * pp);
-      float pw[KP];
-      float2 c[KP];
-#pragma unroll
-      for (int k = 0; k < KP; ++k) {
-        pw[k] = ok[k] ? lds_f1(row + poff[k]) : 0.0f;
-        c[k] = ok[k] ? lds_f2(base + coff[k]) : make_float2(0.0f, 0.0f);
-      }
-      float sr = 0.0f, si = 0.0f;
-#pragma unroll
-      for (int k = 0; k < KP; ++k) {
-        sr = fmaf(pw[k], c[k].x, sr);
-        si = fmaf(pw[k], c[k].y, si);
-      }
-      const float wx = active ? lds_f1(row + 4u * (uint32_t)ix) : 0.0f;
-      v[2 * g] = sr * wx;
-      v[2 * g + 1] = si * wx;
-    }
-    float a4[4], a2[2];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float send = b4 ? v[j] : v[4 + j];
-      const float keep = b4 ? v[4 + j] : v[j];
-      a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float send = b3 ? a4[j] : a4[2 + j];
-      const float keep = b3 ? a4[2 + j] : a4[j];
-      a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    float a1;
-    {
-      const float send = b2 ? a2[0] : a2[1];
-      const float keep = b2 ? a2[1] : a2[0];
-      a1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-    // lane l now holds value l >> 2: point l >> 3, real part when bit 2 is 0
-    const float im = __shfl_down_sync(0xffffffffu, a1, 4);
-    const int g = lane >> 3;
-    if ((lane & 7) == 0 && p0 + g < nb) {
-      const int j = lds_i1(jt_a + 4u * (uint32_t)(p0 + g));
-      out[j] = make_float2(a1, im);
-    }
-  }
-}
-
 // FP32 narrow windows: three blocks of 256 threads per SM (at most 85 registers)
 template <int W, typename Real>
 __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
@@ -869,8 +746,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
   // windows would halve the resident blocks): one point at a time per warp
   // in the spreading lane layout (conflict-free rows at the chosen pitch)
   constexpr bool FAST = sizeof(Real) == 4 && S::FULL && S::PASSES % 2 == 0 && W <= 8;
-  // FP32, 6 taps: the flat layout (rows do not fill a warp)
-  constexpr bool FLAT = plane_flat_ok<W, Real>();
   int lo, hi;
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
@@ -884,7 +759,7 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
     const int T1 = g.tile[1], T2 = g.tile[2];
     const int rows = g.tile[0] * T1;
     const int plane_stride = T1 * pitch;
-    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, nw, g);
+    const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, nw, g, false);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
     for (int t = 0; t < 3; ++t) origin[t] = bc[t] * g.bin[t] - it.win.m + it.win.shift;
@@ -915,15 +790,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
             __syncthreads();
             interp_points_fast<W, Real>(s, nb, warp, nw, lane, pitch, plane_stride,
                                         f_out + (int64_t)r0 * it.M);
-            continue;
-          }
-        }
-        if constexpr (FLAT) {
-          if (np == 1) {
-            const int fstride = plane_wt_stride<W, Real>(nw);
-            plane_stage_interp_flat<W>(a, s, it.win, sub.start + pb, nb, T1, pitch, fstride);
-            __syncthreads();
-            interp_points_flat<W>(s, nb, warp, nw, lane, pitch, plane_stride, fstride, f_out + (int64_t)r0 * it.M);
             continue;
           }
         }
