@@ -31,6 +31,17 @@ template <typename C> __device__ __forceinline__ C cmake(double re, double im);
 template <> __device__ __forceinline__ float2 cmake<float2>(double re, double im) { return make_float2((float)re, (float)im); }
 template <> __device__ __forceinline__ double2 cmake<double2>(double re, double im) { return make_double2(re, im); }
 
+// c + v w for a complex v and a real w: per component one round-to-nearest
+// fma (as fmaf / fma); in FP32 both components in one paired instruction
+// (FFMA2, sm_100 and later).
+__device__ __forceinline__ float2 cmad(float2 v, float w, float2 c) { return __ffma2_rn(v, make_float2(w, w), c); }
+__device__ __forceinline__ double2 cmad(double2 v, double w, double2 c) {
+  return make_double2(fma(v.x, w, c.x), fma(v.y, w, c.y));
+}
+// v w, per component one round-to-nearest product (FP32: FMUL2).
+__device__ __forceinline__ float2 cscale(float2 v, float w) { return __fmul2_rn(v, make_float2(w, w)); }
+__device__ __forceinline__ double2 cscale(double2 v, double w) { return make_double2(v.x * w, v.y * w); }
+
 // Window parameters, normalised so that psi(0) = 1 (the constant phi(0) is
 // moved into the FP64 scaling factors on the host).  The shape parameter
 // depends on sigma_t = n_t / N_t, so it is kept per dimension.

@@ -5,6 +5,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 namespace gbnfft {
 
@@ -1679,9 +1680,10 @@ int Engine::autotune(int reps, double* best_ms) {
     for (int b : {1024, 256, 4096})
       for (int P : Ps) cands.push_back(Cand{{b, 0, 0}, P});
   }
-  double best = 1e30;
-  Cand best_c = cands[0];
-  for (const Cand& c : cands) {
+  // layouts (bin edges, subproblem size) at the default block sizes
+  std::vector<std::pair<double, int>> ranked;
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    const Cand& c = cands[ci];
     if (st != NFFT_OK) break;
     for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? c.bin[t] : 0;
     max_sub_opt = c.P;
@@ -1691,21 +1693,26 @@ int Engine::autotune(int reps, double* best_ms) {
     if (reset_points() != NFFT_OK) continue;
     double ms = 0;
     if (time_transforms(reps, fin, fout, hin, hout, &ms) != NFFT_OK) continue;
-    if (ms < best) {
-      best = ms;
-      best_c = c;
-    }
+    ranked.emplace_back(ms, (int)ci);
   }
-  // warps per block for spreading and for interpolation, on the best layout
-  for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? best_c.bin[t] : 0;
-  max_sub_opt = best_c.P;
-  spread_threads_opt = interp_threads_opt = 0;
-  if (st == NFFT_OK) {
+  std::sort(ranked.begin(), ranked.end());
+  // threads per block for spreading and for interpolation, on each of the
+  // fastest layouts (a layout's rank can change with its block sizes)
+  double best = ranked.empty() ? 1e30 : ranked[0].first;
+  Cand best_c = ranked.empty() ? cands[0] : cands[ranked[0].second];
+  int best_sth = 0, best_ith = 0;
+  const size_t top = dmax >= 2 ? std::min<size_t>(ranked.size(), 3) : 0;
+  for (size_t k = 0; k < top && st == NFFT_OK; ++k) {
+    const Cand& c = cands[ranked[k].second];
+    for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? c.bin[t] : 0;
+    max_sub_opt = c.P;
+    spread_threads_opt = interp_threads_opt = 0;
     CK(cudaStreamSynchronize(stream));
-    st = build_layout();
-    if (st == NFFT_OK) st = reset_points();
-  }
-  if (st == NFFT_OK && dmax >= 2) {
+    if (build_layout() != NFFT_OK || reset_points() != NFFT_OK) {
+      cudaGetLastError();
+      continue;
+    }
+    double here = ranked[k].first;
     for (int pass = 0; pass < 2; ++pass) {
       int& opt = pass == 0 ? spread_threads_opt : interp_threads_opt;
       int keep = 0;
@@ -1717,14 +1724,29 @@ int Engine::autotune(int reps, double* best_ms) {
           cudaGetLastError();
           continue;
         }
-        if (ms < best) {
-          best = ms;
+        if (ms < here) {
+          here = ms;
           keep = th;
         }
       }
       opt = keep;
     }
-    drop_graphs();
+    if (here < best || k == 0) {
+      best = here;
+      best_c = c;
+      best_sth = spread_threads_opt;
+      best_ith = interp_threads_opt;
+    }
+  }
+  drop_graphs();
+  for (int t = 0; t < 3; ++t) bin_opt[t] = t < dmax ? best_c.bin[t] : 0;
+  max_sub_opt = best_c.P;
+  spread_threads_opt = best_sth;
+  interp_threads_opt = best_ith;
+  if (st == NFFT_OK) {
+    CK(cudaStreamSynchronize(stream));
+    st = build_layout();
+    if (st == NFFT_OK) st = reset_points();
   }
   // the sparse/dense split, for spreading and for interpolation: points of a
   // bin below which the grid-warp kernels take it (the automatic threshold

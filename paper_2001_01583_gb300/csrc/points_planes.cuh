@@ -96,12 +96,12 @@ __host__ __device__ inline int plane_wt_stride(bool spread) {
 // Shared layout after the tiles (bp points per batch, np right-hand sides):
 //   (16-byte aligned) rec[bp] PlaneRec | wt[bp][stride] Real |
 //   vt[np - 1][bp] complex (right-hand sides after the first) | jt[bp] int |
-//   gz[T0] gy[T1] gx[T2] int64 | red[nw][64] Real
+//   gz[T0] gy[T1] gx[T2] int64
 template <int W, typename Real>
 __host__ __device__ inline size_t plane_table_bytes(int bp, int np, int nw, const int* tile, bool spread) {
   return 16 + (size_t)bp * sizeof(PlaneRec<Real>) + (size_t)bp * plane_wt_stride<W, Real>(spread) * sizeof(Real) +
          (size_t)(np - 1) * bp * 2 * sizeof(Real) + (size_t)(bp + 1) * sizeof(int) +
-         (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t) + (size_t)nw * 64 * sizeof(Real);
+         (size_t)(tile[0] + tile[1] + tile[2]) * sizeof(int64_t);
 }
 
 template <int W, typename Real>
@@ -114,7 +114,6 @@ struct PlaneSmem {
   int64_t* gz;
   int64_t* gy;
   int64_t* gx;
-  Real* red;
 };
 
 template <int W, typename Real>
@@ -131,7 +130,6 @@ __device__ __forceinline__ PlaneSmem<W, Real> plane_smem(unsigned char* raw, int
   s.gz = reinterpret_cast<int64_t*>(s.jt + bp + (bp & 1));   // keep 8-byte alignment
   s.gy = s.gz + g.tile[0];
   s.gx = s.gy + g.tile[1];
-  s.red = reinterpret_cast<Real*>(s.gx + g.tile[2]);
   return s;
 }
 
@@ -179,10 +177,21 @@ __device__ __forceinline__ void plane_stage_batch(const PointKernelArgs<Real>& a
   for (int d = 0; d < 3; ++d) base[d] = a.pts.delta[d][idx] + (Real)(win.m - win.shift);
   if (NW == 0) {
     s.jt[t] = j;
+    if constexpr (sizeof(Real) == 4 && W % 2 == 0) {
+      // 8-byte stores (row stride 3W even, table 16-byte aligned)
+      float2* w2 = reinterpret_cast<float2*>(w);
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(win, d, base[d] - (Real)i);
+        for (int i = 0; i < W; i += 2)
+          w2[(d * W + i) / 2] = make_float2(window_psi<float>(win, d, base[d] - (float)i),
+                                            window_psi<float>(win, d, base[d] - (float)(i + 1)));
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int i = 0; i < W; ++i) w[d * W + i] = window_psi<Real>(win, d, base[d] - (Real)i);
+    }
   } else {
     using R = SpreadRow<W, (NW > 0 ? NW : 1)>;
     constexpr int NWs = NW > 0 ? NW : 1;
@@ -362,15 +371,14 @@ __device__ __forceinline__ void spread_points_fast(const PlaneSmem<W, Real>& s, 
 #pragma unroll
     for (int u = 0; u < R::TAPS; ++u) {
       const float wzx = wz[u] * wx;
-      const float vr = rc.x * wzx, vi = rc.y * wzx;
+      const float2 v = cscale(make_float2(rc.x, rc.y), wzx);
       const uint32_t au = a0 + uoff[u];
       float2 c[S::PASSES];
 #pragma unroll
       for (int k = 0; k < S::PASSES; ++k) c[k] = lds_f2(au + qoff[k]);
 #pragma unroll
       for (int k = 0; k < S::PASSES; ++k) {
-        c[k].x = fmaf(vr, wy[k], c[k].x);
-        c[k].y = fmaf(vi, wy[k], c[k].y);
+        c[k] = cmad(v, wy[k], c[k]);
         sts_f2(au + qoff[k], c[k]);
       }
     }
@@ -407,17 +415,26 @@ __device__ __forceinline__ void plane_stage_flat(const PointKernelArgs<float>& a
     wz[i] = window_psi<float>(win, 0, base[0] - (float)i);
     wy[i] = window_psi<float>(win, 1, base[1] - (float)i);
   }
-  float* w = s.wt + (size_t)t * stride;
+  // 8-byte stores (W even; the row stride W + W^2 is even and the table
+  // 16-byte aligned): a half warp's rows fall in distinct bank pairs
+  float2* w2 = reinterpret_cast<float2*>(s.wt + (size_t)t * stride);
 #pragma unroll
-  for (int i = 0; i < W; ++i) w[i] = window_psi<float>(win, 2, base[2] - (float)i);
+  for (int i = 0; i < W; i += 2)
+    w2[i / 2] = make_float2(window_psi<float>(win, 2, base[2] - (float)i),
+                            window_psi<float>(win, 2, base[2] - (float)(i + 1)));
 #pragma unroll
   for (int ww = 0; ww < NW; ++ww) {
     const int i0 = (ww - l0) & (NW - 1);
 #pragma unroll
     for (int u = 0; u < TAPS; ++u) {
-      const float z = wz[i0 + u * NW];
+      // wz[i0 + u NW] by selects (a runtime index would put wz in local memory)
+      float z = wz[u * NW];
 #pragma unroll
-      for (int y = 0; y < W; ++y) w[W + (ww * TAPS + u) * W + y] = z * wy[y];
+      for (int c = 1; c < NW; ++c)
+        if (i0 == c) z = wz[c + u * NW];
+      float2* row = w2 + (W + (ww * TAPS + u) * W) / 2;
+#pragma unroll
+      for (int y = 0; y < W; y += 2) row[y / 2] = __fmul2_rn(make_float2(z, z), make_float2(wy[y], wy[y + 1]));
     }
   }
   s.rec[t] = rec;
@@ -471,7 +488,7 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
 #pragma unroll
       for (int k = 0; k < KP; ++k) npw[k] = ok[k] ? lds_f1(row + poff[k]) : 0.0f;
     }
-    const float vr = rc.x * wx, vi = rc.y * wx;
+    const float2 v = cscale(make_float2(rc.x, rc.y), wx);
     const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);
     const uint32_t base = tile_a + 8u * (uint32_t)(__float_as_int(rc.z) + i0 * pstride);
     float2 c[KP];
@@ -481,8 +498,7 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       if (ok[k]) {
-        c[k].x = fmaf(vr, pw[k], c[k].x);
-        c[k].y = fmaf(vi, pw[k], c[k].y);
+        c[k] = cmad(v, pw[k], c[k]);
         sts_f2(base + coff[k], c[k]);
       }
     }
@@ -587,8 +603,10 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
 #pragma unroll
             for (int u = 0; u < R::TAPS; ++u) {
               if (!EVEN && i0 + u * NW >= W) break;
-              const Real wzx = wz[u] * wx;
-              const Real vr = vx * wzx, vi = vy * wzx;
+              C v;
+              v.x = vx;
+              v.y = vy;
+              v = cscale(v, wz[u] * wx);
               C* plane = tr + u * NW * pstride;
               C cell[S::PASSES];
 #pragma unroll
@@ -597,8 +615,7 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
 #pragma unroll
               for (int k = 0; k < S::PASSES; ++k) {
                 if (active && k * S::Q + q < W) {
-                  cell[k].x += vr * wy[k];
-                  cell[k].y += vi * wy[k];
+                  cell[k] = cmad(v, wy[k], cell[k]);
                   plane[k * qstride] = cell[k];
                 }
               }
@@ -674,28 +691,22 @@ __device__ __forceinline__ void interp_points_fast(const PlaneSmem<W, Real>& s, 
         wy[k + 1] = t.y;
       }
       const float wx = lds_f1(wx_a + ROW * pp);
-      float ur[S::PASSES], ui[S::PASSES];
+      float2 u[S::PASSES];
 #pragma unroll
-      for (int k = 0; k < S::PASSES; ++k) ur[k] = ui[k] = 0.0f;
+      for (int k = 0; k < S::PASSES; ++k) u[k] = make_float2(0.0f, 0.0f);
       uint32_t ad = tile_a + 8u * (uint32_t)off;
 #pragma unroll
       for (int iz = 0; iz < W; ++iz) {
 #pragma unroll
-        for (int k = 0; k < S::PASSES; ++k) {
-          const float2 c = lds_f2(ad + qoff[k]);
-          ur[k] = fmaf(wz[iz], c.x, ur[k]);
-          ui[k] = fmaf(wz[iz], c.y, ui[k]);
-        }
+        for (int k = 0; k < S::PASSES; ++k) u[k] = cmad(lds_f2(ad + qoff[k]), wz[iz], u[k]);
         ad += pb;
       }
-      float sr = 0.0f, si = 0.0f;
+      float2 sum = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int k = 0; k < S::PASSES; ++k) {
-        sr = fmaf(wy[k], ur[k], sr);
-        si = fmaf(wy[k], ui[k], si);
-      }
-      v[2 * g] = sr * wx;
-      v[2 * g + 1] = si * wx;
+      for (int k = 0; k < S::PASSES; ++k) sum = cmad(u[k], wy[k], sum);
+      const float2 sw = cscale(sum, wx);
+      v[2 * g] = sw.x;
+      v[2 * g + 1] = sw.y;
     }
     float a4[4], a2[2];
 #pragma unroll
@@ -815,21 +826,18 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
             Real ar = 0, ai = 0;
             if (mine) {
               const C* tr = s.tile + r * tile_elems + base;
+              C acc = cmake<C>(0.0, 0.0);
 #pragma unroll
               for (int iz = 0; iz < W; ++iz) {
-                Real pr = 0, pi = 0;
+                C p = cmake<C>(0.0, 0.0);
                 const C* pl = tr + iz * plane_stride;
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) {
-                  const C c = pl[iy * pitch];
-                  pr += c.x * wy[iy];
-                  pi += c.y * wy[iy];
-                }
-                ar += pr * wz[iz];
-                ai += pi * wz[iz];
+                for (int iy = 0; iy < W; ++iy) p = cmad(pl[iy * pitch], wy[iy], p);
+                acc = cmad(p, wz[iz], acc);
               }
-              ar *= wx;
-              ai *= wx;
+              acc = cscale(acc, wx);
+              ar = acc.x;
+              ai = acc.y;
             }
             if (S::POW2) {
 #pragma unroll
@@ -838,19 +846,18 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
                 ai += __shfl_xor_sync(0xffffffffu, ai, o);
               }
             } else {
-              Real* rw = s.red + warp * 64;
-              rw[lane] = ar;
-              rw[32 + lane] = ai;
-              __syncwarp();
-              if (mine && ix == 0) {
-                ar = 0;
-                ai = 0;
-                for (int k = 0; k < W; ++k) {
-                  ar += rw[grp * W + k];
-                  ai += rw[32 + grp * W + k];
+              // segmented sum over the group's W lanes: after the step of
+              // offset o lane ix holds the sum of lanes ix .. min(ix + 2o, W) - 1
+              // of its group, so lane ix = 0 ends with the whole group's
+#pragma unroll
+              for (int o = 1; o < W; o <<= 1) {
+                const Real tr = __shfl_down_sync(0xffffffffu, ar, o);
+                const Real ti = __shfl_down_sync(0xffffffffu, ai, o);
+                if (ix + o < W) {
+                  ar += tr;
+                  ai += ti;
                 }
               }
-              __syncwarp();
             }
             if (mine && ix == 0) f_out[(int64_t)(r0 + r) * it.M + s.jt[pp]] = cmake<C>(ar, ai);
           }
