@@ -455,15 +455,18 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
   const uint32_t rec_a = (uint32_t)__cvta_generic_to_shared(s.rec);
   const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
   const uint32_t rowb = 4u * (uint32_t)stride;
+  // A lane with no row in pass k (q = Q, or past the warp's R rows) shadows
+  // the pass's first row, Q k, which lane (ix, 0) updates in the same pass:
+  // it loads the same cell and weights and stores the same value, so every
+  // lane loads and stores unconditionally.
   uint32_t coff[KP], poff[KP];
-  bool ok[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
-    const int r = q + Q * k;
-    ok[k] = q < Q && r < R;
-    const int u = ok[k] ? r / W : 0, y = ok[k] ? r % W : 0;
+    const int r0 = q + Q * k;
+    const int r = (q < Q && r0 < R) ? r0 : Q * k;
+    const int u = r / W, y = r % W;
     coff[k] = 8u * (uint32_t)(u * NW * pstride + y * pitch + ix);
-    poff[k] = 4u * (uint32_t)(W + warp * R + (ok[k] ? r : 0));
+    poff[k] = 4u * (uint32_t)(W + warp * R + r);
   }
   const uint32_t wx_off = 4u * (uint32_t)ix;
   // the next point's record, column weight and products are loaded one point
@@ -473,7 +476,7 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
   float nwx = lds_f1(wt_a + wx_off);
   float npw[KP];
 #pragma unroll
-  for (int k = 0; k < KP; ++k) npw[k] = ok[k] ? lds_f1(wt_a + poff[k]) : 0.0f;
+  for (int k = 0; k < KP; ++k) npw[k] = lds_f1(wt_a + poff[k]);
   for (int pp = 0; pp < nb; ++pp) {
     const float4 rc = nrc;
     const float wx = nwx;
@@ -486,22 +489,16 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
       nrc = lds_f4(rec_a + 16u * pn);
       nwx = lds_f1(row + wx_off);
 #pragma unroll
-      for (int k = 0; k < KP; ++k) npw[k] = ok[k] ? lds_f1(row + poff[k]) : 0.0f;
+      for (int k = 0; k < KP; ++k) npw[k] = lds_f1(row + poff[k]);
     }
     const float2 v = cscale(make_float2(rc.x, rc.y), wx);
     const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);
     const uint32_t base = tile_a + 8u * (uint32_t)(__float_as_int(rc.z) + i0 * pstride);
     float2 c[KP];
 #pragma unroll
-    for (int k = 0; k < KP; ++k)
-      if (ok[k]) c[k] = lds_f2(base + coff[k]);
+    for (int k = 0; k < KP; ++k) c[k] = lds_f2(base + coff[k]);
 #pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      if (ok[k]) {
-        c[k] = cmad(v, pw[k], c[k]);
-        sts_f2(base + coff[k], c[k]);
-      }
-    }
+    for (int k = 0; k < KP; ++k) sts_f2(base + coff[k], cmad(v, pw[k], c[k]));
     __syncwarp();
   }
 }

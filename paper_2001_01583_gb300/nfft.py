@@ -66,11 +66,20 @@ class Plan:
 
     # -- helpers -----------------------------------------------------------------
     def _copy_stream(self):
-        """Host copies run on their own stream, ordered against the plan's
-        stream by events, so that they overlap kernels of earlier calls."""
+        """Host-to-device copies run on their own stream, ordered against the
+        plan's stream by events, so that they overlap kernels of earlier
+        calls."""
         if getattr(self, "_cs", None) is None:
             self._cs = torch.cuda.Stream(self.device)
         return self._cs
+
+    def _out_stream(self):
+        """Device-to-host copies of results run on a third stream: a result
+        waits for its own kernels only, and the next call's inputs (on the
+        copy stream) do not queue behind it."""
+        if getattr(self, "_os", None) is None:
+            self._os = torch.cuda.Stream(self.device)
+        return self._os
 
     def _to_device(self, t, dtype):
         if t.device.type != "cuda":
@@ -117,11 +126,11 @@ class Plan:
             res = out.view(dev.shape)
             ev = torch.cuda.Event()
             ev.record(self.stream)
-            cs = self._copy_stream()
-            cs.wait_event(ev)
-            with torch.cuda.stream(cs):
+            os_ = self._out_stream()
+            os_.wait_event(ev)
+            with torch.cuda.stream(os_):
                 res.copy_(dev, non_blocking=True)
-            dev.record_stream(cs)
+            dev.record_stream(os_)
         elif host:
             with torch.cuda.stream(self.stream):
                 res = dev.to("cpu")
@@ -190,8 +199,9 @@ class Plan:
     def sync(self):
         """Wait for the plan's stream and its host copies; raises NFFTError for
         a device-side error."""
-        if getattr(self, "_cs", None) is not None:
-            self._cs.synchronize()
+        for st in (getattr(self, "_cs", None), getattr(self, "_os", None)):
+            if st is not None:
+                st.synchronize()
         _lib.check(self._lib.nfft_sync(self._h), "nfft_sync")
 
     def set_option(self, option, value):

@@ -582,7 +582,8 @@ def test_host_buffers_end_to_end():
 def test_pinned_host_results_asynchronous():
     """Host inputs with pinned CPU `out` tensors: the results arrive on the
     plan's stream and equal the device path's (the forward bit for bit; the
-    adjoint up to the order of its tile flushes' atomic additions)."""
+    adjoint up to the order of its FP32 atomic additions, so within the FP32
+    bars of this file)."""
     N, M = (16, 16, 16), 3000
     x = inputs.uniform_points(M, 3, seed=91)
     f = inputs.complex_normal(M, seed=92, dtype=np.complex64)
@@ -598,7 +599,9 @@ def test_pinned_host_results_asynchronous():
         rb = p.forward(torch.from_numpy(fh).pin_memory(), out=ob)
         p.sync()
     assert ra.data_ptr() == oa.data_ptr() and rb.data_ptr() == ob.data_ptr()
-    _elementwise(oa.numpy(), a_dev.numpy(), 1e-6)
+    _elementwise(oa.numpy(), a_dev.numpy(), FP32_ELEM)
+    d = oa.numpy().astype(np.complex128) - a_dev.numpy()
+    assert np.linalg.norm(d) <= FP32_L2 * np.linalg.norm(a_dev.numpy())
     assert torch.equal(ob, b_dev)
 
 
