@@ -1660,7 +1660,7 @@ int Engine::autotune(int reps, double* best_ms) {
     int P;
   };
   std::vector<Cand> cands;
-  const int Ps[2] = {1024, 256};
+  const int Ps[3] = {1024, 256, 4096};
   if (dmax == 3 && (tensor_enabled || tensor_interp_enabled) && precision == NFFT_FP32_MIXED) {
     // tensor-core spreading: (z, y) rows of the tile within the MMA's 128,
     // x columns along the N dimension

@@ -150,6 +150,27 @@ __device__ __forceinline__ void plane_index_tables(const PlaneSmem<W, Real>& s, 
   }
 }
 
+// The tile rows a warp takes, e = first, first + step, ... over np tiles of
+// T0 x T1 rows: tile r, plane z and row y advanced by additions (no
+// divisions per row).
+struct TileRowWalk {
+  int r, z, y;
+  __device__ __forceinline__ TileRowWalk(int first, int T0, int T1) : r(0), z(0), y(first) { norm(T0, T1); }
+  __device__ __forceinline__ void norm(int T0, int T1) {
+    while (y >= T1) {
+      y -= T1;
+      if (++z == T0) {
+        z = 0;
+        ++r;
+      }
+    }
+  }
+  __device__ __forceinline__ void next(int step, int T0, int T1) {
+    y += step;
+    norm(T0, T1);
+  }
+};
+
 // Stage a batch: thread t handles point first + t.  NW > 0: the spreading
 // layout for NW warps (values of every right-hand side of the pass);
 // NW == 0: the interpolation layout (no values, the point's index instead);
@@ -534,7 +555,6 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
     const C* f_in = static_cast<const C*>(call.in);
     C* grid = static_cast<C*>(it.grid);
     const int T1 = g.tile[1], T2 = g.tile[2];
-    const int rows = g.tile[0] * T1;
     const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, BP, NW, g, true);
     int bc[kMaxDim], origin[kMaxDim];
     bin_coords(sub.bin, g, bc);
@@ -623,10 +643,9 @@ __global__ void __launch_bounds__(32 * NW) k_spread_planes(PointKernelArgs<Real>
       }
       __syncthreads();
       // flush the tile into the grid once: a warp per row, lanes along the row
-      for (int e = warp; e < np * rows; e += NW) {
-        const int r = e / rows;
-        const int row = e - r * rows;
-        const int z = row / T1, y = row - z * T1;
+      for (TileRowWalk w(warp, g.tile[0], T1); w.r < np; w.next(NW, g.tile[0], T1)) {
+        const int r = w.r, z = w.z, y = w.y;
+        const int row = z * T1 + y;
         const int64_t gb = (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
         const C* src = s.tile + r * tile_elems + row * pitch;
         for (int x = lane; x < T2; x += 32) {
@@ -765,7 +784,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
     C* f_out = static_cast<C*>(call.out);
     const C* grid_in = static_cast<const C*>(it.grid);
     const int T1 = g.tile[1], T2 = g.tile[2];
-    const int rows = g.tile[0] * T1;
     const int plane_stride = T1 * pitch;
     const PlaneSmem<W, Real> s = plane_smem<W, Real>(smem_raw, np_max, tile_elems, bp, nw, g, false);
     int bc[kMaxDim], origin[kMaxDim];
@@ -779,10 +797,9 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
       // load the tile with asynchronous global-to-shared copies: a warp per
       // row, lanes along it; every copy of the tile is in flight before the
       // block waits for them
-      for (int e = warp; e < np * rows; e += nw) {
-        const int r = e / rows;
-        const int row = e - r * rows;
-        const int z = row / T1, y = row - z * T1;
+      for (TileRowWalk w(warp, g.tile[0], T1); w.r < np; w.next(nw, g.tile[0], T1)) {
+        const int r = w.r, z = w.z, y = w.y;
+        const int row = z * T1 + y;
         const C* src = grid_in + (int64_t)(r0 + r) * g.grid_cells + s.gz[z] + s.gy[y];
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s.tile + r * tile_elems + row * pitch);
         for (int x = lane; x < T2; x += 32) cp_async_cell(dst + (uint32_t)(x * sizeof(C)), src + s.gx[x]);
