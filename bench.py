@@ -189,10 +189,10 @@ def _cpu_baseline(args, wl, rank, world):
 TRAFFIC = {
     # the spreading launch of the largest configuration (N = 256^3, M = 3e7 clustered, 6 taps, autotuned),
     # profiles/launches_largest_3d_n256_m3e7.md
-    ("picker", "spread"): {"bytes": 3549723904,
-                           "sources": "cdb0c47a92249c7e770f400133255fad3c20ee331549b2be3e5e8507ee521dd3"},
-    ("picker", "interp"): {"bytes": 2546517248,
-                           "sources": "cdb0c47a92249c7e770f400133255fad3c20ee331549b2be3e5e8507ee521dd3"},
+    ("picker", "spread"): {"bytes": 3531525632,
+                           "sources": "ca7a632ad3c3eb6b98c382508e5b8eab4c7b82514942b7ecf44282e5f0d7377d"},
+    ("picker", "interp"): {"bytes": 2632172032,
+                           "sources": "ca7a632ad3c3eb6b98c382508e5b8eab4c7b82514942b7ecf44282e5f0d7377d"},
 }
 TRAFFIC_SOURCES = ("points_planes.cuh", "points_tiled.cuh", "points_gm.cuh", "kernels.h", "common.cuh")
 

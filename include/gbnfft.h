@@ -131,13 +131,24 @@ typedef enum {
                                    keeps the plane kernels unless
                                    NFFT_OPT_TENSOR_INTERP is set.  0 (default): the
                                    plane-owner shared-memory kernel */
-  NFFT_OPT_TENSOR_INTERP = 14   /* the same conditions: 1 interpolates the dense
+  NFFT_OPT_TENSOR_INTERP = 14,  /* the same conditions: 1 interpolates the dense
                                    bins on the tensor cores (the chunk's points
                                    as the MMA's rows, the tile's (z, y) rows as
                                    its K; each point then sums its own x
                                    columns).  Takes the same bins as
                                    NFFT_OPT_TENSOR_SPREAD; either option alone
                                    or both.  0 (default): the plane kernels */
+  NFFT_OPT_PRUNED_FFT = 15      /* d = 3 plans of one item with N_0 < n_0: 1
+                                   (default) splits the FFT of Section 2 into the
+                                   1-D transforms along dimension 0 over the
+                                   whole grid and the 2-D transforms of
+                                   dimensions 1, 2 over the N_0 planes that hold
+                                   I_N (the adjoint transforms along 0 first and
+                                   then only the planes its crop reads; the
+                                   forward transforms the planes its padding
+                                   fills, the others being zero, then along 0):
+                                   1 + 2 N_0 / n_0 passes over the grid instead of
+                                   3.  0: one 3-D cuFFT over the whole grid */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */
@@ -181,6 +192,7 @@ typedef struct {
   int interp_block_threads;  /* the same for interpolation */
   int tensor_spread;         /* 1: dense bins are spread on the tensor cores (NFFT_OPT_TENSOR_SPREAD) */
   int tensor_interp;         /* 1: dense bins are interpolated on the tensor cores (NFFT_OPT_TENSOR_INTERP) */
+  int pruned_fft;            /* 1: the FFT runs as the pruned passes of NFFT_OPT_PRUNED_FFT */
 } nfft_plan_info;
 
 /* Create a plan (Section 2 parameters: bandwidth N, M points, oversampling

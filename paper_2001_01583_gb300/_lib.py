@@ -36,7 +36,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
 METHOD_AUTO, METHOD_TILED, METHOD_GLOBAL, METHOD_WARP, METHOD_GRID_WARP = 0, 1, 2, 3, 4
 (OPT_METHOD, OPT_BIN_0, OPT_BIN_1, OPT_BIN_2, OPT_MAX_SUBPROBLEM, OPT_RHS_CAPACITY, OPT_PROFILE, OPT_THREADS,
  OPT_SPREAD_THREADS, OPT_INTERP_THREADS, OPT_SPARSE_POINTS, OPT_SPARSE_POINTS_INTERP, OPT_OWNER_SPREAD,
- OPT_TENSOR_SPREAD, OPT_TENSOR_INTERP) = range(15)
+ OPT_TENSOR_SPREAD, OPT_TENSOR_INTERP, OPT_PRUNED_FFT) = range(16)
 STAGES = ("sort", "spread", "fft", "deconv", "pad", "ifft", "interp")
 
 
@@ -68,6 +68,7 @@ class PlanInfo(ctypes.Structure):
         ("interp_block_threads", ctypes.c_int),
         ("tensor_spread", ctypes.c_int),
         ("tensor_interp", ctypes.c_int),
+        ("pruned_fft", ctypes.c_int),
     ]
 
 

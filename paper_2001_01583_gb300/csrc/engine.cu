@@ -238,7 +238,7 @@ Engine::~Engine() {
   if (capture_stream) cudaStreamDestroy(capture_stream);
   release_layout();
   for (auto& fc : fclasses) {
-    for (auto& kv : fc.plans) cufftDestroy(kv.second);
+    destroy_fft_plans(fc);
     free_dev(fc.buf);
   }
   for (double* t : tables) cudaFree(t);
@@ -735,7 +735,83 @@ int Engine::fft_handle(FClass& fc, int batch, cufftHandle* out) {
   return NFFT_OK;
 }
 
+void Engine::destroy_fft_plans(FClass& fc) {
+  for (auto& kv : fc.plans) cufftDestroy(kv.second);
+  fc.plans.clear();
+  if (fc.prune_z) cufftDestroy(fc.prune_z);
+  if (fc.prune_yx) cufftDestroy(fc.prune_yx);
+  fc.prune_z = fc.prune_yx = 0;
+  fc.prune_built = false;
+}
+
+// The FFT of a single 3-D item split by dimension (NFFT_OPT_PRUNED_FFT): the
+// frequencies of I_N sit in the planes 0 .. N_0 / 2 - 1 and
+// n_0 - N_0 / 2 .. n_0 - 1 of dimension 0 (k < 0 wraps to k + n_0).
+bool Engine::fft_pruned(const FClass& fc) const {
+  return single && pruned_fft_opt && fc.d == 3 && !items.empty() && items[0].N[0] < fc.n[0];
+}
+
+int Engine::build_pruned(FClass& fc) {
+  if (fc.prune_built) return NFFT_OK;
+  const cufftType type = precision == NFFT_FP64 ? CUFFT_Z2Z : CUFFT_C2C;
+  const long long plane = fc.n[1] * fc.n[2];
+  long long nz[1] = {fc.n[0]};
+  long long nyx[2] = {fc.n[1], fc.n[2]};
+  size_t work = 0;
+  cufftHandle hz = 0, hyx = 0;
+  if (cufftCreate(&hz) != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
+  // lines along dimension 0: element stride n_1 n_2, one line per (y, x)
+  cufftResult r = cufftMakePlanMany64(hz, 1, nz, nz, plane, 1, nz, plane, 1, type, plane, &work);
+  if (r == CUFFT_SUCCESS && cufftCreate(&hyx) != CUFFT_SUCCESS) r = CUFFT_INTERNAL_ERROR;
+  // N_0 / 2 contiguous planes of n_1 x n_2
+  if (r == CUFFT_SUCCESS)
+    r = cufftMakePlanMany64(hyx, 2, nyx, nyx, 1, plane, nyx, 1, plane, type, items[0].N[0] / 2, &work);
+  if (r == CUFFT_SUCCESS && (cufftSetStream(hz, stream) != CUFFT_SUCCESS || cufftSetStream(hyx, stream) != CUFFT_SUCCESS))
+    r = CUFFT_INTERNAL_ERROR;
+  if (r != CUFFT_SUCCESS) {
+    if (hz) cufftDestroy(hz);
+    if (hyx) cufftDestroy(hyx);
+    return r == CUFFT_ALLOC_FAILED ? NFFT_ERR_OOM : NFFT_ERR_CUFFT;
+  }
+  fc.prune_z = hz;
+  fc.prune_yx = hyx;
+  fc.prune_built = true;
+  return NFFT_OK;
+}
+
 int Engine::run_fft(FClass& fc, int batch, int64_t grid_offset, int direction) {
+  if (fft_pruned(fc)) {
+    TRY(build_pruned(fc));
+    if (cufftSetStream(fc.prune_z, stream) != CUFFT_SUCCESS || cufftSetStream(fc.prune_yx, stream) != CUFFT_SUCCESS)
+      return NFFT_ERR_CUFFT;
+    const int64_t plane = fc.n[1] * fc.n[2];
+    const int64_t upper = (fc.n[0] - items[0].N[0] / 2) * plane;   // first plane of the k < 0 run
+    for (int b = 0; b < batch; ++b) {
+      const int64_t g0 = grid_offset + (int64_t)b * fc.cells;
+      cufftResult r = CUFFT_SUCCESS;
+      auto exec = [&](cufftHandle h, int64_t off) {
+        if (r != CUFFT_SUCCESS) return;
+        if (precision == NFFT_FP64) {
+          cufftDoubleComplex* g = static_cast<cufftDoubleComplex*>(fc.buf) + off;
+          r = cufftExecZ2Z(h, g, g, direction);
+        } else {
+          cufftComplex* g = static_cast<cufftComplex*>(fc.buf) + off;
+          r = cufftExecC2C(h, g, g, direction);
+        }
+      };
+      if (direction == CUFFT_FORWARD) {   // adjoint: every line along 0, then the kept planes
+        exec(fc.prune_z, g0);
+        exec(fc.prune_yx, g0);
+        exec(fc.prune_yx, g0 + upper);
+      } else {                            // forward: the filled planes, then every line along 0
+        exec(fc.prune_yx, g0);
+        exec(fc.prune_yx, g0 + upper);
+        exec(fc.prune_z, g0);
+      }
+      if (r != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
+    }
+    return NFFT_OK;
+  }
   cufftHandle h;
   TRY(fft_handle(fc, batch, &h));
   cufftResult r;
@@ -1473,6 +1549,10 @@ int Engine::set_option(int option, int64_t value) {
       if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
       (option == NFFT_OPT_TENSOR_SPREAD ? tensor_enabled : tensor_interp_enabled) = value != 0;
       break;
+    case NFFT_OPT_PRUNED_FFT:
+      if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
+      pruned_fft_opt = value != 0;
+      break;
     case NFFT_OPT_SPARSE_POINTS:
     case NFFT_OPT_SPARSE_POINTS_INTERP:
       if (value < -1 || value > (1 << 20)) return NFFT_ERR_INVALID_ARG;
@@ -1497,8 +1577,7 @@ int Engine::set_option(int option, int64_t value) {
       if (!single) return NFFT_ERR_UNSUPPORTED;   // a batch fixes its right-hand sides per item
       CK(cudaStreamSynchronize(stream));
       for (auto& fc : fclasses) {
-        for (auto& kv : fc.plans) cufftDestroy(kv.second);
-        fc.plans.clear();
+        destroy_fft_plans(fc);
         device_bytes -= (int64_t)fc.grids * fc.cells * (int64_t)csize;
         free_dev(fc.buf);
       }
@@ -1559,6 +1638,7 @@ int Engine::info(nfft_plan_info* out) const {
   out->interp_threads = interp_threads_opt;
   out->tensor_spread = kclasses.empty() ? 0 : (kclasses[0].tensor ? 1 : 0);
   out->tensor_interp = kclasses.empty() ? 0 : (kclasses[0].tensor_interp ? 1 : 0);
+  out->pruned_fft = (!fclasses.empty() && fft_pruned(fclasses[0])) ? 1 : 0;
   out->spread_block_threads = last_spread_threads;
   out->interp_block_threads = last_interp_threads;
   return NFFT_OK;

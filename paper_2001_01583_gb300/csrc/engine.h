@@ -54,6 +54,10 @@ struct FClass {
   void* buf = nullptr;
   std::map<int, cufftHandle> plans;
   bool owner_written = false;   // every grid of the class is written whole by the owner kernel
+  // pruned 3-D FFT (one item): 1-D along dimension 0 over the grid, 2-D over
+  // N_0 / 2 contiguous planes (applied to the two runs of planes holding I_N)
+  cufftHandle prune_z = 0, prune_yx = 0;
+  bool prune_built = false;
 };
 
 struct EventPair {
@@ -127,6 +131,9 @@ class Engine {
   template <typename Real> int ewald_impl(const void* q, double L, double alpha);
   template <typename Real> int ewald_forces_impl(const void* q, double L, double alpha, double* F);
   int run_fft(FClass& fc, int batch, int64_t grid_offset, int direction);
+  bool fft_pruned(const FClass& fc) const;
+  int build_pruned(FClass& fc);
+  void destroy_fft_plans(FClass& fc);
   int fft_handle(FClass& fc, int batch, cufftHandle* out);
   int blocks_per_sm(const void* fn, int threads, size_t smem);
   int stage_begin(int stage, EventPair* ev);
@@ -150,6 +157,7 @@ class Engine {
   bool owner_enabled = false;  // NFFT_OPT_OWNER_SPREAD
   bool tensor_enabled = false; // NFFT_OPT_TENSOR_SPREAD
   bool tensor_interp_enabled = false;  // NFFT_OPT_TENSOR_INTERP
+  bool pruned_fft_opt = true;           // NFFT_OPT_PRUNED_FFT
   int64_t kernel_launches = 0;   // this library's kernels launched so far (graph replays included)
   int64_t graph_launches[2] = {0, 0};
   int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP

@@ -219,7 +219,7 @@ class Plan:
                     owner_spread=inf.owner_spread, kernel_launches=inf.kernel_launches,
                     interp_threads=inf.interp_threads, spread_block_threads=inf.spread_block_threads,
                     interp_block_threads=inf.interp_block_threads, tensor_spread=inf.tensor_spread,
-                    tensor_interp=inf.tensor_interp)
+                    tensor_interp=inf.tensor_interp, pruned_fft=inf.pruned_fft)
 
     def autotune(self, reps=3):
         """Time candidate layouts on the points set and keep the fastest;
