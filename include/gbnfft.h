@@ -139,7 +139,7 @@ typedef enum {
                                    NFFT_OPT_TENSOR_SPREAD; either option alone
                                    or both.  0 (default): the plane kernels */
   NFFT_OPT_PRUNED_FFT = 15      /* d = 3 plans of one item with N_0 < n_0: 1
-                                   (default) splits the FFT of Section 2 into the
+                                   splits the FFT of Section 2 into the
                                    1-D transforms along dimension 0 over the
                                    whole grid and the 2-D transforms of
                                    dimensions 1, 2 over the N_0 planes that hold
@@ -148,7 +148,13 @@ typedef enum {
                                    forward transforms the planes its padding
                                    fills, the others being zero, then along 0):
                                    1 + 2 N_0 / n_0 passes over the grid instead of
-                                   3.  0: one 3-D cuFFT over the whole grid */
+                                   3.  0: one 3-D cuFFT over the whole grid.
+                                   -1 (default): automatic, the split form for
+                                   grids of at least 128 MiB (beyond the L2
+                                   cache; a smaller grid's 3-D cuFFT runs from
+                                   L2), and nfft_autotune times both forms and
+                                   keeps the faster (the option then reads 0
+                                   or 1 in effect) */
 } nfft_option;
 
 /* Stages timed when NFFT_OPT_PROFILE is on (index into nfft_stage_times). */

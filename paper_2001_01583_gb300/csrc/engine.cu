@@ -747,8 +747,14 @@ void Engine::destroy_fft_plans(FClass& fc) {
 // The FFT of a single 3-D item split by dimension (NFFT_OPT_PRUNED_FFT): the
 // frequencies of I_N sit in the planes 0 .. N_0 / 2 - 1 and
 // n_0 - N_0 / 2 .. n_0 - 1 of dimension 0 (k < 0 wraps to k + n_0).
+// Automatic choice: grids of at least 128 MiB (larger than the L2 cache);
+// a smaller grid's single 3-D cuFFT runs from L2 and beats three launches.
+constexpr double kPruneMinBytes = 134217728.0;
+
 bool Engine::fft_pruned(const FClass& fc) const {
-  return single && pruned_fft_opt && fc.d == 3 && !items.empty() && items[0].N[0] < fc.n[0];
+  if (!(single && fc.d == 3 && !items.empty() && items[0].N[0] < fc.n[0])) return false;
+  if (pruned_fft_mode >= 0) return pruned_fft_mode == 1;
+  return (double)fc.cells * (double)csize >= kPruneMinBytes;
 }
 
 int Engine::build_pruned(FClass& fc) {
@@ -1550,8 +1556,8 @@ int Engine::set_option(int option, int64_t value) {
       (option == NFFT_OPT_TENSOR_SPREAD ? tensor_enabled : tensor_interp_enabled) = value != 0;
       break;
     case NFFT_OPT_PRUNED_FFT:
-      if (value != 0 && value != 1) return NFFT_ERR_INVALID_ARG;
-      pruned_fft_opt = value != 0;
+      if (value < -1 || value > 1) return NFFT_ERR_INVALID_ARG;
+      pruned_fft_mode = (int)value;
       break;
     case NFFT_OPT_SPARSE_POINTS:
     case NFFT_OPT_SPARSE_POINTS_INTERP:
@@ -1858,6 +1864,38 @@ int Engine::autotune(int reps, double* best_ms) {
       if (st == NFFT_OK) st = reset_points();
     }
     drop_graphs();
+  }
+  // the pruned against the full 3-D FFT (automatic mode only): the faster
+  // stays, and the other form's cuFFT plans are released
+  if (st == NFFT_OK && pruned_fft_mode < 0 && single && !fclasses.empty()) {
+    FClass& fc = fclasses[item_fclass[0]];
+    const int auto_mode = fft_pruned(fc) ? 1 : 0;
+    pruned_fft_mode = 1;
+    if (fft_pruned(fc)) {
+      double t[2] = {1e30, 1e30};
+      for (int mode = 0; mode < 2; ++mode) {
+        pruned_fft_mode = mode;
+        if (time_transforms(reps, fin, fout, hin, hout, &t[mode]) != NFFT_OK) {
+          cudaGetLastError();
+          t[mode] = 1e30;
+        }
+      }
+      pruned_fft_mode = t[1] <= t[0] ? 1 : 0;
+      if (t[pruned_fft_mode] >= 1e30) pruned_fft_mode = auto_mode;
+      best = std::min(best, t[pruned_fft_mode]);
+      CK(cudaStreamSynchronize(stream));
+      if (pruned_fft_mode == 1) {
+        for (auto& kv : fc.plans) cufftDestroy(kv.second);
+        fc.plans.clear();
+      } else {
+        if (fc.prune_z) cufftDestroy(fc.prune_z);
+        if (fc.prune_yx) cufftDestroy(fc.prune_yx);
+        fc.prune_z = fc.prune_yx = 0;
+        fc.prune_built = false;
+      }
+    } else {
+      pruned_fft_mode = -1;   // not applicable (sigma = 1 along dimension 0)
+    }
   }
   CK(cudaStreamSynchronize(stream));
   for (void* p : owned) cudaFree(p);

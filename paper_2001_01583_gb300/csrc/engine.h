@@ -157,7 +157,7 @@ class Engine {
   bool owner_enabled = false;  // NFFT_OPT_OWNER_SPREAD
   bool tensor_enabled = false; // NFFT_OPT_TENSOR_SPREAD
   bool tensor_interp_enabled = false;  // NFFT_OPT_TENSOR_INTERP
-  bool pruned_fft_opt = true;           // NFFT_OPT_PRUNED_FFT
+  int pruned_fft_mode = -1;             // NFFT_OPT_PRUNED_FFT: -1 automatic, 0 never, 1 always
   int64_t kernel_launches = 0;   // this library's kernels launched so far (graph replays included)
   int64_t graph_launches[2] = {0, 0};
   int sparse_interp_opt = 0;   // NFFT_OPT_SPARSE_POINTS_INTERP

@@ -94,12 +94,29 @@ def test_pruned_fft_against_oracle_and_full_fft(N, sigma, precision):
 
 
 def test_pruned_fft_only_where_it_applies():
-    """Two dimensions keep the full cuFFT; so does sigma = 1 (no plane
-    outside I_N)."""
-    from paper_2001_01583_gb300 import Plan
+    """The automatic choice takes the split form for grids beyond the L2
+    cache only; forced on, it still needs three dimensions and planes outside
+    I_N (sigma = 1 has none); the autotuner keeps one of the two forms."""
+    from paper_2001_01583_gb300 import Plan, _lib
+    with Plan((16, 16, 16), 100, 2.0, 3, "kaiser_bessel", "fp32") as p:
+        assert p.info()["pruned_fft"] == 0          # a 32^3 grid: the 3-D cuFFT
+        p.set_option(_lib.OPT_PRUNED_FFT, 1)
+        assert p.info()["pruned_fft"] == 1
+    with Plan((256, 256, 256), 100, 2.0, 3, "kaiser_bessel", "fp32") as p:
+        assert p.info()["pruned_fft"] == 1          # a 512^3 grid, 1 GiB
     with Plan((16, 16), 100, 2.0, 3, "kaiser_bessel", "fp32") as p:
+        p.set_option(_lib.OPT_PRUNED_FFT, 1)
         assert p.info()["pruned_fft"] == 0
     with Plan((16, 16, 16), 100, 1.0, 3, "kaiser_bessel", "fp32") as p:
+        p.set_option(_lib.OPT_PRUNED_FFT, 1)
         assert p.info()["pruned_fft"] == 0
-    with Plan((16, 16, 16), 100, 2.0, 3, "kaiser_bessel", "fp32") as p:
-        assert p.info()["pruned_fft"] == 1
+    x = inputs.uniform_points(20000, 3, seed=304)
+    with Plan((64, 64, 64), 20000, 2.0, 3, "kaiser_bessel", "fp32") as p:
+        p.set_points(torch.from_numpy(x).cuda())
+        p.autotune(reps=2)
+        assert p.info()["pruned_fft"] in (0, 1)
+        f = torch.from_numpy(inputs.complex_normal(20000, seed=305)).to(torch.complex64).cuda()
+        a = p.adjoint(f).cpu().numpy().astype(np.complex128)
+        p.sync()
+    sa = S.adjoint(x, f.cpu().numpy().astype(np.complex128), (64, 64, 64), 2.0, 3, S.KAISER_BESSEL)
+    _elementwise(a, sa, FP32_ELEM)
