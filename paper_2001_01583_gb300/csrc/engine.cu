@@ -1179,6 +1179,7 @@ int Engine::set_points_impl(const double* x_override) {
   s.total_bins = total_bins;
   s.x_override = x_override;
   s.err = err_flag;
+  s.single_d = items.size() == 1 ? items[0].geom.d : 0;
   EventPair ev{};
   TRY(stage_begin(NFFT_STAGE_SORT, &ev));
   CK(cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)std::max(total_bins, 1), stream));

@@ -23,6 +23,7 @@ struct SortArgs {
   int total_bins;
   const double* x_override;       // single item: points of this call (else items[i].x)
   int* err;                       // bit 0: non-finite coordinate
+  int single_d;                   // one item: its dimension (the kernels' one-item form); 0 otherwise
 };
 // Cell and global bin of every point, and its rank inside its bin.
 template <typename Real>

@@ -477,14 +477,16 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
   const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
   const uint32_t rowb = 4u * (uint32_t)stride;
   // A lane with no row in pass k (q = Q, or past the warp's R rows) shadows
-  // the pass's first row, Q k, which lane (ix, 0) updates in the same pass:
-  // it loads the same cell and weights and stores the same value, so every
-  // lane loads and stores unconditionally.
+  // the pass's last row, min(Q k + Q - 1, R - 1), which lane (ix, q') of the
+  // same pass updates: it loads the same cell and weights and stores the
+  // same value, so every lane loads and stores unconditionally.  The last
+  // row's lanes sit in the upper half of the warp with the idle ones, so a
+  // pass touches no more distinct addresses per half warp than before.
   uint32_t coff[KP], poff[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     const int r0 = q + Q * k;
-    const int r = (q < Q && r0 < R) ? r0 : Q * k;
+    const int r = (q < Q && r0 < R) ? r0 : min(Q * k + Q - 1, R - 1);
     const int u = r / W, y = r % W;
     coff[k] = 8u * (uint32_t)(u * NW * pstride + y * pitch + ix);
     poff[k] = 4u * (uint32_t)(W + warp * R + r);

@@ -192,6 +192,121 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortArgs s, const int*
   }
 }
 
+// The two point passes for one item of dimension D (single plans): the
+// item's geometry is held in registers, and every coordinate of a thread's
+// points is loaded before any is reduced (no item search, no reload of the
+// item's fields per point).
+template <int D>
+struct OneItem {
+  const double* x;
+  int64_t poff;
+  int boff;
+  int n[D], bw[D], nb[D];
+  __device__ __forceinline__ explicit OneItem(const SortArgs& s) {
+    const ItemDev& it = s.items[0];
+    x = s.x_override ? s.x_override : it.x;
+    poff = it.point_offset;
+    boff = it.bin_offset;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      n[t] = it.geom.n[t];
+      bw[t] = it.geom.bin[t];
+      nb[t] = it.geom.nbins[t];
+    }
+  }
+};
+
+template <typename Real, int D>
+__global__ void __launch_bounds__(kSortThreads) k_bin_count_one(SortArgs s, int* __restrict__ bin_count,
+                                                                int2* __restrict__ bin_rank) {
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortPer) + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const OneItem<D> one(s);
+  double v[kSortPer][D];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+#pragma unroll
+    for (int t = 0; t < D; ++t) v[k][t] = gidx < s.total_points ? one.x[(gidx - one.poff) * D + t] : 0.0;
+  }
+  int bin[kSortPer];
+  bool any_bad = false;
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    int local = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      double c0 = v[k][t];
+      if (!isfinite(c0)) {
+        any_bad = true;
+        c0 = 0.0;
+      }
+      int c;
+      Real dl;
+      reduce_coord<Real>(c0, one.n[t], c, dl);
+      local = local * one.nb[t] + c / one.bw[t];
+    }
+    bin[k] = gidx < s.total_points ? one.boff + local : -1;
+  }
+  if (any_bad) atomicOr(s.err, 1);
+  unsigned peers[kSortPer];
+  int got[kSortPer];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    peers[k] = __match_any_sync(0xffffffffu, bin[k]);
+    got[k] = 0;
+    if (bin[k] >= 0 && lane == __ffs(peers[k]) - 1) got[k] = atomicAdd(&bin_count[bin[k]], __popc(peers[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int first = __shfl_sync(peers[k], got[k], __ffs(peers[k]) - 1);
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    if (bin[k] >= 0) bin_rank[gidx] = make_int2(bin[k], first + __popc(peers[k] & ((1u << lane) - 1u)));
+  }
+}
+
+template <typename Real, int D>
+__global__ void __launch_bounds__(kSortThreads) k_scatter_one(SortArgs s, const int* __restrict__ bin_start,
+                                                              const int2* __restrict__ bin_rank, int* __restrict__ perm,
+                                                              uint32_t* __restrict__ local, Real* d0, Real* d1, Real* d2) {
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortPer) + threadIdx.x;
+  Real* dst[3] = {d0, d1, d2};
+  const OneItem<D> one(s);
+  int2 br[kSortPer];
+  double v[kSortPer][D];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    const bool in = gidx < s.total_points;
+    br[k] = in ? bin_rank[gidx] : make_int2(-1, 0);
+#pragma unroll
+    for (int t = 0; t < D; ++t) v[k][t] = in ? one.x[(gidx - one.poff) * D + t] : 0.0;
+  }
+  int pos[kSortPer];
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) pos[k] = br[k].x >= 0 ? bin_start[br[k].x] + br[k].y : -1;
+  constexpr int bits = D == 1 ? 32 : (D == 2 ? 16 : 10);
+#pragma unroll
+  for (int k = 0; k < kSortPer; ++k) {
+    if (pos[k] < 0) continue;
+    const int64_t gidx = base + (int64_t)k * kSortThreads;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      const double c0 = isfinite(v[k][t]) ? v[k][t] : 0.0;
+      int c;
+      Real dl;
+      reduce_coord<Real>(c0, one.n[t], c, dl);
+      const uint32_t lc = (uint32_t)(c % one.bw[t]);
+      packed |= (D == 1) ? lc : (lc << (bits * t));
+      dst[t][pos[k]] = dl;
+    }
+    perm[pos[k]] = (int)(gidx - one.poff);
+    local[pos[k]] = packed;
+  }
+}
+
 // Exclusive scan of n ints with one block of 1024 threads: each thread scans a
 // contiguous chunk sequentially, the chunk totals are scanned in shared memory.
 // Used for the per-tile partial sums of the multi-block scan below.
@@ -314,8 +429,13 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <typename Real>
 cudaError_t launch_bin_count(const SortArgs& s, int* bin_count, int2* bin_rank, cudaStream_t st) {
   if (s.total_points == 0) return cudaSuccess;
-  k_bin_count<Real><<<blocks_for(s.total_points, kSortThreads * kSortPer), kSortThreads, 0, st>>>(s, bin_count,
-                                                                                                  bin_rank);
+  const unsigned blocks = blocks_for(s.total_points, kSortThreads * kSortPer);
+  switch (s.single_d) {
+    case 1: k_bin_count_one<Real, 1><<<blocks, kSortThreads, 0, st>>>(s, bin_count, bin_rank); break;
+    case 2: k_bin_count_one<Real, 2><<<blocks, kSortThreads, 0, st>>>(s, bin_count, bin_rank); break;
+    case 3: k_bin_count_one<Real, 3><<<blocks, kSortThreads, 0, st>>>(s, bin_count, bin_rank); break;
+    default: k_bin_count<Real><<<blocks, kSortThreads, 0, st>>>(s, bin_count, bin_rank);
+  }
   return cudaGetLastError();
 }
 
@@ -344,8 +464,24 @@ template <typename Real>
 cudaError_t launch_scatter(const SortArgs& s, const int* bin_start, const int2* bin_rank, int* perm, uint32_t* local,
                            Real* const* delta, cudaStream_t st) {
   if (s.total_points == 0) return cudaSuccess;
-  k_scatter<Real><<<blocks_for(s.total_points, kSortThreads * kSortPer), kSortThreads, 0, st>>>(
-      s, bin_start, bin_rank, perm, local, delta[0], delta[1], delta[2]);
+  const unsigned blocks = blocks_for(s.total_points, kSortThreads * kSortPer);
+  switch (s.single_d) {
+    case 1:
+      k_scatter_one<Real, 1><<<blocks, kSortThreads, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0], delta[1],
+                                                              delta[2]);
+      break;
+    case 2:
+      k_scatter_one<Real, 2><<<blocks, kSortThreads, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0], delta[1],
+                                                              delta[2]);
+      break;
+    case 3:
+      k_scatter_one<Real, 3><<<blocks, kSortThreads, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0], delta[1],
+                                                              delta[2]);
+      break;
+    default:
+      k_scatter<Real><<<blocks, kSortThreads, 0, st>>>(s, bin_start, bin_rank, perm, local, delta[0], delta[1],
+                                                       delta[2]);
+  }
   return cudaGetLastError();
 }
 
