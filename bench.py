@@ -189,10 +189,10 @@ def _cpu_baseline(args, wl, rank, world):
 TRAFFIC = {
     # the spreading launch of the largest configuration (N = 256^3, M = 3e7 clustered, 6 taps, autotuned),
     # profiles/launches_largest_3d_n256_m3e7.md
-    ("picker", "spread"): {"bytes": 3531525632,
-                           "sources": "ca7a632ad3c3eb6b98c382508e5b8eab4c7b82514942b7ecf44282e5f0d7377d"},
-    ("picker", "interp"): {"bytes": 2632172032,
-                           "sources": "ca7a632ad3c3eb6b98c382508e5b8eab4c7b82514942b7ecf44282e5f0d7377d"},
+    ("picker", "spread"): {"bytes": 3529425152,
+                           "sources": "a95258a40660f0a65a2d121fda5c1cc004234825b3ea4935eeb5e5d6399ad5bd"},
+    ("picker", "interp"): {"bytes": 2632852480,
+                           "sources": "a95258a40660f0a65a2d121fda5c1cc004234825b3ea4935eeb5e5d6399ad5bd"},
 }
 TRAFFIC_SOURCES = ("points_planes.cuh", "points_tiled.cuh", "points_gm.cuh", "kernels.h", "common.cuh")
 
