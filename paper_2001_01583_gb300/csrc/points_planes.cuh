@@ -415,15 +415,19 @@ __device__ __forceinline__ void plane_stage_flat(const PointKernelArgs<float>& a
                                                  const WindowDev& win, const float2* f_in, int64_t M, int first,
                                                  int nb, int r0, int T1, int pitch, int stride) {
   constexpr int TAPS = W / NW;
+  static_assert(NW <= 2, "the flat record holds one tile offset per warp");
   const int t = threadIdx.x;
   if (t >= nb) return;
   const int idx = first + t;
   const int j = a.pts.perm[idx];
   const uint32_t loc = a.pts.local[idx];
   const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
+  // the record's two offsets: the tile cell of the first plane warp 0 and
+  // warp 1 own (tap (w - l0) mod NW)
   PlaneRec<float> rec;
-  rec.off = (l0 * T1 + l1) * pitch + l2;
-  rec.z = l0;
+  const int off = (l0 * T1 + l1) * pitch + l2;
+  rec.off = off + ((0 - l0) & (NW - 1)) * T1 * pitch;
+  rec.z = off + ((1 - l0) & (NW - 1)) * T1 * pitch;
   const float2 v0 = f_in[(int64_t)r0 * M + j];
   rec.vx = v0.x;
   rec.vy = v0.y;
@@ -500,6 +504,7 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
   float npw[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) npw[k] = lds_f1(wt_a + poff[k]);
+#pragma unroll 2
   for (int pp = 0; pp < nb; ++pp) {
     const float4 rc = nrc;
     const float wx = nwx;
@@ -515,8 +520,7 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
       for (int k = 0; k < KP; ++k) npw[k] = lds_f1(row + poff[k]);
     }
     const float2 v = cscale(make_float2(rc.x, rc.y), wx);
-    const int i0 = (warp - __float_as_int(rc.w)) & (NW - 1);
-    const uint32_t base = tile_a + 8u * (uint32_t)(__float_as_int(rc.z) + i0 * pstride);
+    const uint32_t base = tile_a + 8u * (uint32_t)(warp == 0 ? __float_as_int(rc.z) : __float_as_int(rc.w));
     float2 c[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) c[k] = lds_f2(base + coff[k]);
