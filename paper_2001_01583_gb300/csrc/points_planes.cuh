@@ -79,18 +79,44 @@ struct SpreadRow {
 // plane's 6 rows evenly (per plane a pass of 5 rows and one of 1: 56% of the
 // lanes busy), and warps that divide the taps: each warp walks its planes'
 // rows as one list (the flat layout), so a pass can finish one plane and
-// start the next (90% busy).  Staged per point: wx | the products
-// wz(plane) wy(row) of every warp's rows, warp-major.  Wider windows would
-// need too many per-lane pass offsets in registers.
+// start the next (90% busy).  Wider windows would need too many per-lane
+// pass offsets in registers.
 template <int W, typename Real>
 __host__ __device__ constexpr bool plane_flat_ok() {
   return sizeof(Real) == 4 && W == 6;
 }
 
-// Weight-row stride (the flat spreading layout needs W + W^2 floats).
+// The flat layout's shape for NW warps: lane (ix, q) takes rows q, q + Q, ...
+// of the warp's R rows in KP passes.  A lane with no row in pass k (q = Q, or
+// past R) shadows the pass's last row, min(Q k + Q - 1, R - 1).  Staged per
+// point: for each warp and lane row q, the KP products wz(plane) wy(row) of
+// its passes side by side (one 16-byte load per lane per point), then wx.
+template <int W, int NW>
+struct FlatShape {
+  static constexpr int TAPS = W / NW;
+  static constexpr int Q = 32 / W;
+  static constexpr int R = TAPS * W;
+  static constexpr int KP = (R + Q - 1) / Q;
+  static constexpr int PW = Q * KP;                 // products per warp
+  static constexpr int WX = NW * PW;                // where wx starts
+  // row stride: a multiple of 4 floats, and an odd number of 16-byte units,
+  // so that 8 consecutive rows' 16-byte stores fall in distinct banks
+  static constexpr int S4 = (WX + W + 3) / 4;
+  static constexpr int STRIDE = 4 * (S4 % 2 ? S4 : S4 + 1);
+  __host__ __device__ static constexpr int row(int q, int k) {
+    return (q < Q && q + Q * k < R) ? q + Q * k : (Q * k + Q - 1 < R - 1 ? Q * k + Q - 1 : R - 1);
+  }
+};
+
+// Weight-row stride (the flat spreading layout: FlatShape's, for 1 or 2 warps).
 template <int W, typename Real>
 __host__ __device__ inline int plane_wt_stride(bool spread) {
-  return spread && plane_flat_ok<W, Real>() ? (3 * W > W + W * W ? 3 * W : W + W * W) : 3 * W;
+  if (spread && plane_flat_ok<W, Real>()) {
+    constexpr int a = FlatShape<W, 1>::STRIDE, b = FlatShape<W, 2>::STRIDE;
+    constexpr int f = a > b ? a : b;
+    return f > 3 * W ? f : 3 * W;
+  }
+  return 3 * W;
 }
 
 // Shared layout after the tiles (bp points per batch, np right-hand sides):
@@ -408,14 +434,13 @@ __device__ __forceinline__ void spread_points_fast(const PlaneSmem<W, Real>& s, 
 }
 
 // Stage a batch in the flat layout (FP32, one right-hand side): thread t
-// handles point first + t; its row holds wx[W], then for warp w = 0..NW-1
-// the products wz(tap (w - z0) mod NW + u NW) wy(y) at u W + y, u < W / NW.
+// handles point first + t; its row holds FlatShape's products, then wx.
 template <int W, int NW>
 __device__ __forceinline__ void plane_stage_flat(const PointKernelArgs<float>& a, const PlaneSmem<W, float>& s,
                                                  const WindowDev& win, const float2* f_in, int64_t M, int first,
                                                  int nb, int r0, int T1, int pitch, int stride) {
-  constexpr int TAPS = W / NW;
   static_assert(NW <= 2, "the flat record holds one tile offset per warp");
+  static_assert(FlatShape<W, NW>::KP % 4 == 0, "a lane's products are whole 16-byte units");
   const int t = threadIdx.x;
   if (t >= nb) return;
   const int idx = first + t;
@@ -440,62 +465,68 @@ __device__ __forceinline__ void plane_stage_flat(const PointKernelArgs<float>& a
     wz[i] = window_psi<float>(win, 0, base[0] - (float)i);
     wy[i] = window_psi<float>(win, 1, base[1] - (float)i);
   }
-  // 8-byte stores (W even; the row stride W + W^2 is even and the table
-  // 16-byte aligned): a half warp's rows fall in distinct bank pairs
-  float2* w2 = reinterpret_cast<float2*>(s.wt + (size_t)t * stride);
-#pragma unroll
-  for (int i = 0; i < W; i += 2)
-    w2[i / 2] = make_float2(window_psi<float>(win, 2, base[2] - (float)i),
-                            window_psi<float>(win, 2, base[2] - (float)(i + 1)));
+  // products first (16-byte stores: the row stride is an odd number of
+  // 16-byte units and the table 16-byte aligned), then wx
+  using F = FlatShape<W, NW>;
+  float* w = s.wt + (size_t)t * stride;
 #pragma unroll
   for (int ww = 0; ww < NW; ++ww) {
     const int i0 = (ww - l0) & (NW - 1);
 #pragma unroll
-    for (int u = 0; u < TAPS; ++u) {
-      // wz[i0 + u NW] by selects (a runtime index would put wz in local memory)
-      float z = wz[u * NW];
+    for (int q = 0; q < F::Q; ++q) {
+      float pk[F::KP];
 #pragma unroll
-      for (int c = 1; c < NW; ++c)
-        if (i0 == c) z = wz[c + u * NW];
-      float2* row = w2 + (W + (ww * TAPS + u) * W) / 2;
+      for (int k = 0; k < F::KP; ++k) {
+        const int r = F::row(q, k), u = r / W, y = r % W;
+        // wz[i0 + u NW] by selects (a runtime index would put wz in local memory)
+        float z = wz[u * NW];
 #pragma unroll
-      for (int y = 0; y < W; y += 2) row[y / 2] = __fmul2_rn(make_float2(z, z), make_float2(wy[y], wy[y + 1]));
+        for (int c = 1; c < NW; ++c)
+          if (i0 == c) z = wz[c + u * NW];
+        pk[k] = z * wy[y];
+      }
+#pragma unroll
+      for (int k = 0; k < F::KP; k += 4)
+        *reinterpret_cast<float4*>(w + ww * F::PW + q * F::KP + k) = make_float4(pk[k], pk[k + 1], pk[k + 2], pk[k + 3]);
     }
   }
+#pragma unroll
+  for (int i = 0; i < W; i += 2)
+    *reinterpret_cast<float2*>(w + F::WX + i) = make_float2(window_psi<float>(win, 2, base[2] - (float)i),
+                                                            window_psi<float>(win, 2, base[2] - (float)(i + 1)));
   s.rec[t] = rec;
 }
 
 // The plane-owner loop over a batch staged in the flat layout: lane (ix, q)
-// takes the rows q, q + Q, ... (Q = 32 / W) of the warp's TAPS planes walked
-// as one list of TAPS W rows, column ix.
+// takes the rows q, q + Q, ... (Q = 32 / W) of the warp's W / NW planes
+// walked as one list of rows, column ix.
 template <int W, int NW>
 __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s, int nb, int warp, int lane,
                                                    int pitch, int pstride, int stride) {
-  constexpr int TAPS = W / NW;
-  constexpr int Q = 32 / W;
-  constexpr int R = TAPS * W;                  // rows of a point this warp updates
-  constexpr int KP = (R + Q - 1) / Q;          // passes
+  using F = FlatShape<W, NW>;
+  constexpr int Q = F::Q, KP = F::KP;
   const int ix = lane % W, q = lane / W;
   const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile);
   const uint32_t rec_a = (uint32_t)__cvta_generic_to_shared(s.rec);
   const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
   const uint32_t rowb = 4u * (uint32_t)stride;
-  // A lane with no row in pass k (q = Q, or past the warp's R rows) shadows
-  // the pass's last row, min(Q k + Q - 1, R - 1), which lane (ix, q') of the
-  // same pass updates: it loads the same cell and weights and stores the
-  // same value, so every lane loads and stores unconditionally.  The last
-  // row's lanes sit in the upper half of the warp with the idle ones, so a
-  // pass touches no more distinct addresses per half warp than before.
-  uint32_t coff[KP], poff[KP];
+  // Every lane loads and stores unconditionally: one with no row in pass k
+  // shadows the pass's last row (FlatShape::row), which a lane of the same
+  // pass updates, so it loads the same cell and weights and stores the same
+  // value.  The last row's lanes sit in the upper half of the warp with the
+  // idle ones, so a pass touches no more distinct addresses per half warp
+  // than the rows themselves.
+  uint32_t coff[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
-    const int r0 = q + Q * k;
-    const int r = (q < Q && r0 < R) ? r0 : min(Q * k + Q - 1, R - 1);
+    const int r = F::row(q, k);
     const int u = r / W, y = r % W;
     coff[k] = 8u * (uint32_t)(u * NW * pstride + y * pitch + ix);
-    poff[k] = 4u * (uint32_t)(W + warp * R + r);
   }
-  const uint32_t wx_off = 4u * (uint32_t)ix;
+  // this lane's KP products (lanes q = Q read row q = Q - 1's, whose shadow
+  // rows are theirs) and its column weight
+  const uint32_t poff = 4u * (uint32_t)(warp * F::PW + (q < Q ? q : Q - 1) * KP);
+  const uint32_t wx_off = 4u * (uint32_t)(F::WX + ix);
   // the next point's record, column weight and products are loaded one point
   // ahead; a point's cells are all loaded before any is written back (the
   // passes touch distinct cells)
@@ -503,7 +534,13 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
   float nwx = lds_f1(wt_a + wx_off);
   float npw[KP];
 #pragma unroll
-  for (int k = 0; k < KP; ++k) npw[k] = lds_f1(wt_a + poff[k]);
+  for (int k = 0; k < KP; k += 4) {
+    const float4 t4 = lds_f4(wt_a + poff + 4u * k);
+    npw[k] = t4.x;
+    npw[k + 1] = t4.y;
+    npw[k + 2] = t4.z;
+    npw[k + 3] = t4.w;
+  }
 #pragma unroll 2
   for (int pp = 0; pp < nb; ++pp) {
     const float4 rc = nrc;
@@ -517,7 +554,13 @@ __device__ __forceinline__ void spread_points_flat(const PlaneSmem<W, float>& s,
       nrc = lds_f4(rec_a + 16u * pn);
       nwx = lds_f1(row + wx_off);
 #pragma unroll
-      for (int k = 0; k < KP; ++k) npw[k] = lds_f1(row + poff[k]);
+      for (int k = 0; k < KP; k += 4) {
+        const float4 t4 = lds_f4(row + poff + 4u * k);
+        npw[k] = t4.x;
+        npw[k + 1] = t4.y;
+        npw[k + 2] = t4.z;
+        npw[k + 3] = t4.w;
+      }
     }
     const float2 v = cscale(make_float2(rc.x, rc.y), wx);
     const uint32_t base = tile_a + 8u * (uint32_t)(warp == 0 ? __float_as_int(rc.z) : __float_as_int(rc.w));
