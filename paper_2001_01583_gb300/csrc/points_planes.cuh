@@ -108,11 +108,11 @@ struct FlatShape {
   }
 };
 
-// Weight-row stride (the flat layouts of both kernels: FlatShape's, for 1 or
-// 2 spreading warps and for interpolation's one warp per point).
+// Weight-row stride (the flat spreading layout: FlatShape's, for 1 or 2
+// warps; interpolation keeps 3W).
 template <int W, typename Real>
-__host__ __device__ inline int plane_wt_stride(bool /*spread*/) {
-  if (plane_flat_ok<W, Real>()) {
+__host__ __device__ inline int plane_wt_stride(bool spread) {
+  if (spread && plane_flat_ok<W, Real>()) {
     constexpr int a = FlatShape<W, 1>::STRIDE, b = FlatShape<W, 2>::STRIDE;
     constexpr int f = a > b ? a : b;
     return f > 3 * W ? f : 3 * W;
@@ -815,116 +815,6 @@ __device__ __forceinline__ void interp_points_fast(const PlaneSmem<W, Real>& s, 
   }
 }
 
-// Stage a batch for flat interpolation (FP32, 6 taps, one right-hand side):
-// thread t handles point first + t; its row holds, for each lane row q and
-// pass k of FlatShape<W, 1> (one warp walks all W^2 rows of the point), the
-// product wz wy of row q + Q k, zero where the pass has no such row, then wx.
-template <int W>
-__device__ __forceinline__ void plane_stage_interp_flat(const PointKernelArgs<float>& a,
-                                                        const PlaneSmem<W, float>& s, const WindowDev& win,
-                                                        int first, int nb, int T1, int pitch, int stride) {
-  using F = FlatShape<W, 1>;
-  static_assert(F::KP % 4 == 0, "a lane's products are whole 16-byte units");
-  const int t = threadIdx.x;
-  if (t >= nb) return;
-  const int idx = first + t;
-  const uint32_t loc = a.pts.local[idx];
-  const int l0 = unpack_local(loc, 3, 0), l1 = unpack_local(loc, 3, 1), l2 = unpack_local(loc, 3, 2);
-  s.jt[t] = a.pts.perm[idx];
-  PlaneRec<float> rec;
-  rec.off = (l0 * T1 + l1) * pitch + l2;
-  rec.z = l0;
-  rec.vx = 0.0f;
-  rec.vy = 0.0f;
-  float base[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) base[d] = a.pts.delta[d][idx] + (float)(win.m - win.shift);
-  float wz[W], wy[W];
-#pragma unroll
-  for (int i = 0; i < W; ++i) {
-    wz[i] = window_psi<float>(win, 0, base[0] - (float)i);
-    wy[i] = window_psi<float>(win, 1, base[1] - (float)i);
-  }
-  float* w = s.wt + (size_t)t * stride;
-#pragma unroll
-  for (int q = 0; q < F::Q; ++q) {
-    float pk[F::KP];
-#pragma unroll
-    for (int k = 0; k < F::KP; ++k) {
-      const int r = q + F::Q * k;
-      pk[k] = r < F::R ? wz[r / W] * wy[r % W] : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < F::KP; k += 4)
-      *reinterpret_cast<float4*>(w + q * F::KP + k) = make_float4(pk[k], pk[k + 1], pk[k + 2], pk[k + 3]);
-  }
-#pragma unroll
-  for (int i = 0; i < W; i += 2)
-    *reinterpret_cast<float2*>(w + F::WX + i) = make_float2(window_psi<float>(win, 2, base[2] - (float)i),
-                                                            window_psi<float>(win, 2, base[2] - (float)(i + 1)));
-  s.rec[t] = rec;
-}
-
-// Flat interpolation of a staged batch (FP32, 6 taps, one right-hand side):
-// a warp takes 4 points at a time; lane (ix, q) reads cell ix of rows q,
-// q + Q, ... of the point's W planes walked as one list of W^2 rows (8
-// passes of 5 rows), weighted by the staged products (one 16-byte load per
-// 4 passes), and times wx that is its share of the point's value; the
-// butterfly reduces the 4 points.  A lane with no row in a pass reads the
-// pass's last row's cell with a zero product (lanes q = Q: a zero wx), so
-// the loads run unpredicated and add nothing.
-template <int W>
-__device__ __forceinline__ void interp_points_flat(const PlaneSmem<W, float>& s, int nb, int warp, int nw,
-                                                   int lane, int pitch, int pstride, int stride, float2* out) {
-  using F = FlatShape<W, 1>;
-  constexpr int Q = F::Q, KP = F::KP;
-  constexpr int PG = 4;
-  const int ix = lane % W, q = lane / W;
-  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile);
-  const uint32_t off_a = (uint32_t)__cvta_generic_to_shared(s.rec) + 8u;   // PlaneRec<float>::off
-  const uint32_t jt_a = (uint32_t)__cvta_generic_to_shared(s.jt);
-  const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
-  const uint32_t rowb = 4u * (uint32_t)stride;
-  uint32_t coff[KP];
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    const int r = F::row(q, k);
-    coff[k] = 8u * (uint32_t)((r / W) * pstride + (r % W) * pitch + ix);
-  }
-  const uint32_t poff = 4u * (uint32_t)((q < Q ? q : Q - 1) * KP);
-  const uint32_t wx_off = 4u * (uint32_t)(F::WX + ix);
-  const bool idle = q >= Q;
-  for (int p0 = warp * PG; p0 < nb; p0 += nw * PG) {
-    float v[2 * PG];
-#pragma unroll
-    for (int g = 0; g < PG; ++g) {
-      const uint32_t pp = (uint32_t)min(p0 + g, nb - 1);   // past the batch: recomputed, not written
-      const uint32_t row = wt_a + rowb * pp;
-      const uint32_t base = tile_a + 8u * (uint32_t)lds_i1(off_a + 16u * pp);
-      float pw[KP];
-#pragma unroll
-      for (int k = 0; k < KP; k += 4) {
-        const float4 t4 = lds_f4(row + poff + 4u * k);
-        pw[k] = t4.x;
-        pw[k + 1] = t4.y;
-        pw[k + 2] = t4.z;
-        pw[k + 3] = t4.w;
-      }
-      float2 c[KP];
-#pragma unroll
-      for (int k = 0; k < KP; ++k) c[k] = lds_f2(base + coff[k]);
-      float2 sum = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int k = 0; k < KP; ++k) sum = cmad(c[k], pw[k], sum);
-      const float wx = idle ? 0.0f : lds_f1(row + wx_off);
-      const float2 sw = cscale(sum, wx);
-      v[2 * g] = sw.x;
-      v[2 * g + 1] = sw.y;
-    }
-    butterfly4_store(v, lane, p0, nb, jt_a, out);
-  }
-}
-
 // FP32 narrow windows: three blocks of 256 threads per SM (at most 85 registers)
 template <int W, typename Real>
 __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
@@ -943,9 +833,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
   // windows would halve the resident blocks): one point at a time per warp
   // in the spreading lane layout (conflict-free rows at the chosen pitch)
   constexpr bool FAST = sizeof(Real) == 4 && S::FULL && S::PASSES % 2 == 0 && W <= 8;
-  // FP32, 6 taps (rows that do not fill a warp): the flat layout, one warp
-  // per point walking its W^2 rows
-  constexpr bool FLAT = plane_flat_ok<W, Real>();
   int lo, hi;
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
@@ -988,15 +875,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
             __syncthreads();
             interp_points_fast<W, Real>(s, nb, warp, nw, lane, pitch, plane_stride,
                                         f_out + (int64_t)r0 * it.M);
-            continue;
-          }
-        }
-        if constexpr (FLAT) {
-          if (np == 1) {
-            const int fstride = plane_wt_stride<W, Real>(false);
-            plane_stage_interp_flat<W>(a, s, it.win, sub.start + pb, nb, T1, pitch, fstride);
-            __syncthreads();
-            interp_points_flat<W>(s, nb, warp, nw, lane, pitch, plane_stride, fstride, f_out + (int64_t)r0 * it.M);
             continue;
           }
         }
