@@ -189,10 +189,10 @@ def _cpu_baseline(args, wl, rank, world):
 TRAFFIC = {
     # the spreading launch of the largest configuration (N = 256^3, M = 3e7 clustered, 6 taps, autotuned),
     # profiles/launches_largest_3d_n256_m3e7.md
-    ("picker", "spread"): {"bytes": 3529425152,
-                           "sources": "a95258a40660f0a65a2d121fda5c1cc004234825b3ea4935eeb5e5d6399ad5bd"},
-    ("picker", "interp"): {"bytes": 2632852480,
-                           "sources": "a95258a40660f0a65a2d121fda5c1cc004234825b3ea4935eeb5e5d6399ad5bd"},
+    ("picker", "spread"): {"bytes": 3527202816,
+                           "sources": "c81048f3d0ca6b3a5813d50ac739fc51ee0a70e1ac58ed1c01567ad4a6423b23"},
+    ("picker", "interp"): {"bytes": 2631691520,
+                           "sources": "c81048f3d0ca6b3a5813d50ac739fc51ee0a70e1ac58ed1c01567ad4a6423b23"},
 }
 TRAFFIC_SOURCES = ("points_planes.cuh", "points_tiled.cuh", "points_gm.cuh", "kernels.h", "common.cuh")
 
