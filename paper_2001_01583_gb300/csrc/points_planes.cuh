@@ -815,68 +815,6 @@ __device__ __forceinline__ void interp_points_fast(const PlaneSmem<W, Real>& s, 
   }
 }
 
-// Interpolation of a staged batch for one right-hand side in FP32 with 6
-// taps (rows that do not fill a warp): the column-per-lane form (W lanes per
-// point, each summing column ix of the point's W x W rows) on 32-bit shared
-// addresses, the row offsets held in registers.  A lane without a point of
-// its own reads point 0 of the batch with a zero column weight, so every
-// load runs unpredicated; a segmented shuffle sum finishes each point.
-template <int W>
-__device__ __forceinline__ void interp_points_cols(const PlaneSmem<W, float>& s, int nb, int warp, int nw, int lane,
-                                                   int pitch, int pstride, float2* out) {
-  using S = PlaneShape<W>;
-  static_assert(W % 2 == 0, "weight rows of 3W floats are read in 8-byte pairs");
-  const int grp = lane / W, ix = lane % W;
-  const bool active = grp < S::PPW;
-  const uint32_t tile_a = (uint32_t)__cvta_generic_to_shared(s.tile) + 8u * (uint32_t)ix;
-  const uint32_t off_a = (uint32_t)__cvta_generic_to_shared(s.rec) + 8u;   // PlaneRec<float>::off
-  const uint32_t wt_a = (uint32_t)__cvta_generic_to_shared(s.wt);
-  const uint32_t jt_a = (uint32_t)__cvta_generic_to_shared(s.jt);
-  const uint32_t pb = 8u * (uint32_t)pstride;
-  uint32_t rowo[W];
-#pragma unroll
-  for (int iy = 0; iy < W; ++iy) rowo[iy] = 8u * (uint32_t)(iy * pitch);
-  for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
-    const int pp = p0 + grp;
-    const bool mine = active && pp < nb;
-    const uint32_t q = mine ? (uint32_t)pp : 0u;
-    const uint32_t row = wt_a + 4u * (uint32_t)(3 * W) * q;
-    float wz[W], wy[W];
-#pragma unroll
-    for (int i = 0; i < W; i += 2) {
-      const float2 z2 = lds_f2(row + 4u * (uint32_t)i);
-      const float2 y2 = lds_f2(row + 4u * (uint32_t)(W + i));
-      wz[i] = z2.x;
-      wz[i + 1] = z2.y;
-      wy[i] = y2.x;
-      wy[i + 1] = y2.y;
-    }
-    const float wx = mine ? lds_f1(row + 4u * (uint32_t)(2 * W + ix)) : 0.0f;
-    const uint32_t a0 = tile_a + 8u * (uint32_t)lds_i1(off_a + 16u * q);
-    float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int iz = 0; iz < W; ++iz) {
-      const uint32_t ap = a0 + (uint32_t)iz * pb;
-      float2 pz = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int iy = 0; iy < W; ++iy) pz = cmad(lds_f2(ap + rowo[iy]), wy[iy], pz);
-      acc = cmad(pz, wz[iz], acc);
-    }
-    acc = cscale(acc, wx);
-    // segmented sum over the group's W lanes (lane ix = 0 ends with it)
-#pragma unroll
-    for (int o = 1; o < W; o <<= 1) {
-      const float tr = __shfl_down_sync(0xffffffffu, acc.x, o);
-      const float ti = __shfl_down_sync(0xffffffffu, acc.y, o);
-      if (ix + o < W) {
-        acc.x += tr;
-        acc.y += ti;
-      }
-    }
-    if (mine && ix == 0) out[lds_i1(jt_a + 4u * (uint32_t)pp)] = acc;
-  }
-}
-
 // FP32 narrow windows: three blocks of 256 threads per SM (at most 85 registers)
 template <int W, typename Real>
 __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_interp_groups(PointKernelArgs<Real> a, WppLayout lay) {
@@ -895,8 +833,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
   // windows would halve the resident blocks): one point at a time per warp
   // in the spreading lane layout (conflict-free rows at the chosen pitch)
   constexpr bool FAST = sizeof(Real) == 4 && S::FULL && S::PASSES % 2 == 0 && W <= 8;
-  // FP32, 6 taps: the column-per-lane form on 32-bit shared addresses
-  constexpr bool COLS = sizeof(Real) == 4 && !FAST && W == 6;
   int lo, hi;
   launch_subs(a, lo, hi);
   for (int sp = lo + blockIdx.x; sp < hi; sp += gridDim.x) {
@@ -944,12 +880,6 @@ __global__ void __launch_bounds__(256, (W <= 8 && sizeof(Real) == 4) ? 3 : 1) k_
         }
         plane_stage_batch<W, 0, Real>(a, s, it.win, nullptr, it.M, sub.start + pb, nb, r0, 0, bp, T1, pitch, 3 * W);
         __syncthreads();
-        if constexpr (COLS) {
-          if (np == 1) {
-            interp_points_cols<W>(s, nb, warp, nw, lane, pitch, plane_stride, f_out + (int64_t)r0 * it.M);
-            continue;
-          }
-        }
         for (int p0 = warp * S::PPW; p0 < nb; p0 += nw * S::PPW) {
           const int pp = p0 + grp;
           const bool mine = active && pp < nb;
